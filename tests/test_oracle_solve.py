@@ -1,0 +1,220 @@
+"""Pins for the oracle's A.P, solve and observables (CPU only).
+
+Independent checks: closed forms for one and two dipoles, dense LU (a library
+solve) against the oracle's BiCGSTAB, the FFT embedding against the direct sum
+and against a larger grid, the optical theorem, C_sca from integrating |f|^2
+over the sphere of directions, energy conservation, symmetry of A, and the
+DDSCAT guide's own worked example (RCTGLPRSM, Appendix "w000r000ori.avg").
+"""
+import math
+
+import numpy as np
+import pytest
+
+from dda_inputs import targets as tg
+from dda_inputs import workloads as W
+from oracle import dda, mie
+
+
+def test_single_dipole_closed_form():
+    """N = 1: A = 1/alpha, P = alpha E, C_ext = 4 pi k Im(alpha),
+    C_abs = 4 pi k |alpha|^2 [-Im(1/alpha) - (2/3) k^3]."""
+    occ = np.ones((1, 1, 1), np.uint8)
+    m, kd = 1.7 + 0.3j, 0.4
+    r = dda.solve_target(occ, occ, [m], kd, [1, 0, 0], [0, 1, 0], [0, 1, 0], "CM",
+                         operator="dense")
+    a = dda.polarizability("CM", m, kd)
+    g = math.pi * dda.effective_radius(1) ** 2
+    assert abs(r["P"][0][0, 1] - a) < 1e-15
+    assert abs(r["Qext"][0] - 4 * math.pi * kd * a.imag / g) < 1e-14
+    cabs = 4 * math.pi * kd * abs(a) ** 2 * (-np.imag(1 / a) - 2 / 3 * kd ** 3)
+    assert abs(r["Qabs"][0] - cabs / g) < 1e-14
+
+
+@pytest.mark.parametrize("method", ["CM", "FCD"])
+def test_dipole_pair_closed_form(method):
+    """Two dipoles one lattice step apart along x, field along z: by symmetry
+    P1 = P2 = P z with (1/alpha - G_zz) P = E (E in phase at both sites for
+    khat = y).  G_zz(r along x) = (k^2 + d^2/dz^2) g at distance 1."""
+    occ = np.ones((1, 1, 2), np.uint8)
+    m, kd = 1.5 + 0.1j, 0.7
+    kh, e = np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0])
+    r = dda.solve_target(occ, occ, [m], kd, kh, [0, 0, 1], e, method, npol=1,
+                         operator="dense")
+    if method == "CM":
+        gzz = np.exp(1j * kd) * (kd * kd - 1 + 1j * kd)   # e^{ikr}/r^3[(kr)^2 - (1-ikr)]
+    else:
+        g, g1, _ = dda.filtered_scalar_green(np.array([1.0]), kd)
+        gzz = (kd * kd * g + g1)[0]                     # k^2 g + g'/r, transverse
+    a = dda.polarizability(method, m, kd)
+    P = 1.0 / (1.0 / a - gzz)
+    assert np.allclose(r["P"][0][:, 2], P, rtol=1e-13)
+    assert np.allclose(r["P"][0][:, :2], 0, atol=1e-15)
+
+
+def test_matrix_is_complex_symmetric():
+    w = W.two_material_brick(3, 4, 2)
+    flat, pos = dda.site_positions(w.occ)
+    ainv = dda.site_alpha_inverse(w.comp.reshape(-1)[flat], w.m, "FCD", 0.5)
+    A = dda.dense_matrix(pos, ainv, 0.5, "FCD")
+    assert np.allclose(A, A.T, atol=1e-15)
+
+
+@pytest.mark.parametrize("method", dda.METHODS)
+def test_bicgstab_matches_dense_lu(method):
+    w = W.two_material_brick(5, 4, 6, method=method)
+    kw = dict(method=method, dirs=w.dirs)
+    d = dda.solve_target(w.occ, w.comp, w.m, w.kd, w.khat[0], w.yhat[0], w.e01[0],
+                         operator="dense", **kw)
+    b = dda.solve_target(w.occ, w.comp, w.m, w.kd, w.khat[0], w.yhat[0], w.e01[0],
+                         operator="direct", tol=1e-12, **kw)
+    for l in range(2):
+        err = np.linalg.norm(d["P"][l] - b["P"][l]) / np.linalg.norm(d["P"][l])
+        assert err < 1e-10
+        assert abs(d["Qext"][l] - b["Qext"][l]) < 1e-10 * abs(d["Qext"][l])
+
+
+@pytest.mark.parametrize("method", ["LDR", "FCD"])
+@pytest.mark.parametrize("dims", [(6, 10, 12), (7, 5, 9), (1, 1, 5), (3, 1, 1)])
+def test_fft_embedding_equals_direct_sum(method, dims):
+    nx, ny, nz = dims
+    occ, comp = tg.ellipsoid(nx, ny, nz, nx + 0.8, ny + 0.8, nz + 0.8)
+    flat, pos = dda.site_positions(occ)
+    kd = 0.45
+    ainv = dda.site_alpha_inverse(comp.reshape(-1)[flat], [1.6 + 0.2j], method, kd,
+                                  [1, 0, 0], [0, 1, 0])
+    P = W.random_polarization(occ, seed=11)[0]
+    ref = dda.matvec_direct(dda.box_to_sites(P, flat), pos, ainv, kd, method)
+    ainv_box = np.zeros(occ.size, np.complex128)
+    ainv_box[flat] = ainv
+    for grid in (None, (2 * nx + 3, 2 * ny + 1, 2 * nz + 5)):
+        op = dda.FFTOperator(occ, ainv_box.reshape(occ.shape), kd, method, grid)
+        got = dda.box_to_sites(op(P), flat)
+        assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_fft_grid_too_small_is_refused():
+    occ, _ = tg.rect_prism(4, 4, 4)
+    with pytest.raises(ValueError):
+        dda.FFTOperator(occ, np.ones(occ.shape, np.complex128), 0.3, "LDR", (6, 8, 8))
+
+
+@pytest.mark.parametrize("method", dda.METHODS)
+def test_optical_theorem(method):
+    """C_ext = (4 pi / k^2) Im f_ll(0): the forward amplitude and the
+    extinction sum are computed by different routines."""
+    w = W.small_ellipsoid(6, 5, 7, kd=0.5, method=method, n_orient=3, seed=4)
+    for i in range(3):
+        r = dda.solve_target(w.occ, w.comp, w.m, w.kd, w.khat[i], w.yhat[i], w.e01[i],
+                             method, dirs=w.dirs, tol=1e-12)
+        g = math.pi * dda.effective_radius(w.n_dipoles) ** 2
+        for l in range(2):
+            cext = 4 * math.pi / w.kd ** 2 * r["famp"][0, l, l].imag
+            assert abs(cext / g - r["Qext"][l]) < 1e-10 * abs(r["Qext"][l])
+
+
+def _sphere_quadrature(nt=48, nph=96):
+    x, wt = np.polynomial.legendre.leggauss(nt)
+    th = np.arccos(x)
+    ph = (np.arange(nph) + 0.5) * 2 * math.pi / nph
+    dirs = np.array([(t, p) for t in th for p in ph])
+    wts = np.array([a * 2 * math.pi / nph for a in wt for _ in ph])
+    return dirs, wts
+
+
+@pytest.mark.parametrize("method", ["LDR", "FCD"])
+def test_qsca_equals_integral_of_scattered_intensity(method):
+    """C_sca = (1/k^2) int sum_m |f_ml|^2 dOmega must equal C_ext - C_abs (the
+    guide's Q_sca = Q_ext - Q_abs); this ties P, the f_ml convention and the
+    C_abs weight together."""
+    w = W.small_ellipsoid(5, 6, 4, m=1.8 + 0.4j, kd=0.6, method=method, n_orient=2)
+    dirs, wts = _sphere_quadrature()
+    r = dda.solve_target(w.occ, w.comp, w.m, w.kd, w.khat[1], w.yhat[1], w.e01[1],
+                         method, dirs=dirs, tol=1e-12)
+    g = math.pi * dda.effective_radius(w.n_dipoles) ** 2
+    f = r["famp"][1:]
+    for l in range(2):
+        csca = float(np.sum(wts * np.sum(np.abs(f[:, :, l]) ** 2, axis=1))) / w.kd ** 2
+        assert abs(csca / g - r["Qsca"][l]) < 1e-8 * r["Qsca"][l]
+
+
+@pytest.mark.parametrize("method", dda.METHODS)
+def test_lossless_target_absorbs_nothing(method):
+    w = W.small_ellipsoid(5, 5, 6, m=1.6, kd=0.5, method=method)
+    r = dda.solve_target(w.occ, w.comp, w.m, w.kd, w.khat[0], w.yhat[0], w.e01[0],
+                         method, tol=1e-12)
+    for l in range(2):
+        assert abs(r["Qabs"][l]) < 1e-10 * r["Qext"][l]
+        assert r["Qsca"][l] > 0
+
+
+def test_reciprocity_of_amplitudes():
+    """A = A^T implies f(-k_i <- -k_s) relations; the simplest consequence:
+    e_b . P^{(a)}(k_a) summed with incident phase of b equals the same with a
+    and b swapped (E_b^T A^{-1} E_a = E_a^T A^{-1} E_b)."""
+    w = W.two_material_brick(4, 3, 5)
+    flat, pos = dda.site_positions(w.occ)
+    kd = w.kd
+    ka, ea = np.array([0.6, 0.8, 0.0]), np.array([0.0, 0.0, 1.0])
+    kb, eb = np.array([0.0, 0.6, -0.8]), np.array([1.0, 0.0, 0.0])
+    ainv = dda.site_alpha_inverse(w.comp.reshape(-1)[flat], w.m, "CM", kd)
+    A = dda.dense_matrix(pos, ainv, kd, "CM")
+    Ea = dda.incident_field(pos, kd, ka, ea).reshape(-1)
+    Eb = dda.incident_field(pos, kd, kb, eb).reshape(-1)
+    Pa = np.linalg.solve(A, Ea)
+    Pb = np.linalg.solve(A, Eb)
+    assert abs(Eb @ Pa - Ea @ Pb) < 1e-12 * abs(Eb @ Pa)
+
+
+def test_rayleigh_limit_single_dipole_matches_small_sphere_mie():
+    """x -> 0: Q_abs -> 4 x Im[(m^2-1)/(m^2+2)] for both Mie and one dipole."""
+    m, x = 1.5 + 0.1j, 1e-3
+    ray = 4 * x * np.imag((m * m - 1) / (m * m + 2))
+    assert abs(mie.mie_q(m, x)[1] / ray - 1) < 1e-4
+    occ = np.ones((1, 1, 1), np.uint8)
+    kd = x / dda.effective_radius(1)
+    r = dda.solve_target(occ, occ, [m], kd, [1, 0, 0], [0, 1, 0], [0, 1, 0], "LDR",
+                         operator="dense")
+    assert abs(r["Qabs"][0] / ray - 1) < 1e-4
+
+
+@pytest.mark.slow
+def test_dda_converges_to_mie_as_lattice_refines():
+    """Sphere, m = 1.33+0.01i, x = 1: the DDA error falls as N grows
+    (the guide's Figs. 1-2 show the same convergence)."""
+    m, x = 1.33 + 0.01j, 1.0
+    qe_mie = mie.mie_q(m, x)[0]
+    errs = []
+    for n in (6, 10, 16):
+        occ, comp = tg.sphere(n)
+        N = int(occ.sum())
+        kd = x / dda.effective_radius(N)
+        r = dda.solve_target(occ, comp, [m], kd, [1, 0, 0], [0, 1, 0], [0, 1, 0], "LDR",
+                             tol=1e-10)
+        errs.append(abs(np.mean(r["Qext"]) / qe_mie - 1))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.02
+
+
+def test_guide_worked_example_rctglprsm():
+    """RCTGLPRSM 16x32x32 Au brick of the guide's Appendix (w000r000ori.avg):
+    N = 16384, k d = 0.19635, m = 0.9656 + 1.8628i, k along x_TF, e = y, z.
+    The guide used GKDLDR; LATTDR (what the oracle has) is expected within ~1%
+    (the guide's Fig. 6 shows the two agree for |m| k d < 0.5).  Printed:
+    Q_ext 3.6134, Q_abs 1.4308, Q_sca 2.1827, S_11(0) 75.115, S_11(180) 18.591."""
+    occ, comp = tg.rect_prism(16, 32, 32)
+    assert int(occ.sum()) == 16384
+    kd = 3.093665 * 0.06346821
+    m = 0.9656 + 1.8628j
+    assert abs(abs(m) * kd - 0.4120) < 5e-5
+    dirs = np.array([(math.pi, 0.0)])
+    r = dda.solve_target(occ, comp, [m], kd, [1, 0, 0], [0, 1, 0], [0, 1, 0], "LDR",
+                         tol=1e-7, dirs=dirs)
+    qext, qabs = np.mean(r["Qext"]), np.mean(r["Qabs"])
+    assert abs(qext / 3.6134 - 1) < 0.01
+    assert abs(qabs / 1.4308 - 1) < 0.01
+    assert abs((qext - qabs) / 2.1827 - 1) < 0.01
+    f = r["famp"]
+    s11 = 0.5 * np.sum(np.abs(f) ** 2, axis=(1, 2))
+    assert abs(s11[0] / 75.115 - 1) < 0.02
+    assert abs(s11[1] / 18.591 - 1) < 0.02
