@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the DDA solve on the sphere-64^3 workload.
+
+Workload: sphere on a 64^3 lattice (N = 137,376 dipoles, FFT grid 128^3),
+m = 1.5 + 0.02i, x = 2 pi a_eff / lambda = 5, LATTDR polarizability, incidence
+along x with both polarizations (2 right-hand sides), tolerance 1e-8 on the
+FP64 relative residual.  A step is one complete solve of both polarizations
+(every BiCGSTAB iteration, the FP64 refinement residuals, the final FP64 true
+residual and the cross sections and forward amplitudes), FFT-convolution
+matvec in complex FP32 inside FP64 iterative refinement.  The plain FP64
+solve is timed beside it on the same GPU and both are checked for equal
+Q_ext (relative difference <= 1e-6).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle
+(numpy FFT-convolution BiCGSTAB in FP64) on bounded samples of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "dipole*iters/s"
+UNIT = "dipole*iterations/s"
+WORKLOAD = "sphere64^3 N=137376, m=1.5+0.02i, x=5, LDR, 2 pol, tol 1e-8"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(pw), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes of the five matvec passes (per right-hand side)
+# ---------------------------------------------------------------------------
+def pass_bytes(box, grid, s):
+    nx, ny, nz = box
+    Lx, Ly, Lz = grid
+    nbox = nx * ny * nz
+    rows_x = 3 * nz * ny * Lx          # spectral rows after the x pass
+    full_yz = 3 * nz * Ly * Lx         # after the y pass
+    per_rhs = {
+        "x_fwd": s * (3 * nbox + rows_x),
+        "y_fwd": s * (rows_x + full_yz),
+        "z_mul": s * (2 * full_yz),
+        "y_inv": s * (full_yz + rows_x),
+        "x_inv": s * (rows_x + 3 * nbox + 3 * nbox) + nbox,   # + composition bytes
+    }
+    H = (Lx // 2 + 1) * (Ly // 2 + 1) * (Lz // 2 + 1)
+    per_launch = {"z_mul": 6 * H * s}    # the Green transform octant, read once
+    return per_rhs, per_launch
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    for f in ("matvec.cu", "fft_core.cuh", "dda_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1305_6497_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel, workload):
+    """Per-RHS DRAM traffic of `kernel` from the committed ncu summary, or None
+    if it was taken on a different version of the kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = _source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#"):
+            k, w, sha, per_rhs = parts[:4]
+            if k == kernel and w == workload and sha == src:
+                return float(per_rhs)
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(w, iters=3):
+    """The oracle's FFT-convolution BiCGSTAB (FP64) on the workload, stopped
+    after `iters` iterations of one polarization; returns (dipole*iters/s, s)."""
+    import numpy as np
+    from oracle import dda as O
+    flat, pos = O.site_positions(w.occ)
+    e1, _ = O.polarization_pair(w.khat[0], w.e01[0])
+    ainv = O.site_alpha_inverse(w.comp.reshape(-1)[flat], w.m, w.method, w.kd, w.khat[0], e1)
+    E = O.incident_field(pos, w.kd, w.khat[0], e1)
+    t0 = time.perf_counter()
+    ainv_box = np.zeros(w.occ.size, np.complex128)
+    ainv_box[flat] = ainv
+    op = O.FFTOperator(w.occ, ainv_box.reshape(w.occ.shape), w.kd, w.method)
+
+    def mv(x):
+        return O.box_to_sites(op(O.sites_to_box(x.reshape(-1, 3), flat, w.occ.shape)),
+                              flat).reshape(-1)
+    t1 = time.perf_counter()
+    _, it, _ = O.bicgstab(mv, E.reshape(-1), 1e-30, iters)
+    t2 = time.perf_counter()
+    N = len(flat)
+    return N * it / (t2 - t1), (t2 - t1), (t1 - t0), it
+
+
+def run_reference(args, rank, world):
+    from dda_inputs import workloads as W
+    if rank != 0:
+        return 0
+    w = W.c2_sphere64()
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(w, 1)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt, _, it = oracle_sample(w, 2)
+        vals.append(v)
+        times.append(dt)
+    value = sum(w.n_dipoles * 2 for _ in times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": w.n_dipoles},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "2 BiCGSTAB iterations of one polarization per step "
+                                   "(numpy FFT convolution, FP64, single-threaded)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from dda_inputs import workloads as W
+    from paper_1305_6497_gb300 import binding as B
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = W.c2_sphere64()
+    N = w.n_dipoles
+    R = w.n_rhs
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    kw = dict(yhat=w.yhat, npol=2, tol=w.tol, max_iter=5000, dirs=None, want_famp=True)
+    t = B.Target(w.occ, w.comp, w.m, method=w.method)
+    grid = t.grid
+    # warm-up (includes the one-time Green-tensor transform build)
+    setup = t.solve(w.kd, w.khat, w.e01, precision="fp32_refined", want_P=False, **kw)
+    for _ in range(max(0, args.warmup - 1)):
+        t.solve(w.kd, w.khat, w.e01, precision="fp32_refined", want_P=False, **kw)
+
+    # ---- timed region: refined FP32 ----
+    clocks = ClockSampler(local_rank)
+    step_ms, iters, launches = [], [], 0
+    kern_ms, kern_calls = {}, {}
+    fp32_rhs_mv = fp64_rhs_mv = 0
+    qext = None
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    l0 = B.dda_launch_count()
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                       # evict L2 between steps
+        torch.cuda.synchronize()
+        out = t.solve(w.kd, w.khat, w.e01, precision="fp32_refined", want_P=False,
+                      profile=True, **kw)
+        step_ms.append(out["t_solve_ms"])
+        iters.append(int(np.sum(out["iters"])))
+        fp32_rhs_mv += out["matvecs"] - out["matvecs_fp64"]
+        fp64_rhs_mv += out["matvecs_fp64"]
+        for k, v in out["kernel_ms"].items():
+            kern_ms[k] = kern_ms.get(k, 0.0) + v
+            kern_calls[k] = kern_calls.get(k, 0) + out["kernel_calls"][k]
+        qext = out["Qext"]
+        resid = out["resid"]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = B.dda_launch_count() - l0
+    clk = clocks.stop()
+    barrier()
+
+    dev_s = sum(step_ms) / 1e3
+    value_local = N * sum(iters) / dev_s
+    solves_local = R * args.steps / dev_s
+
+    # ---- plain FP64 on the same GPU (fewer steps: it is ~10x slower) ----
+    k64 = max(1, min(args.steps, 3))
+    ms64, it64 = [], []
+    for _ in range(k64):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        o64 = t.solve(w.kd, w.khat, w.e01, precision="fp64", want_P=False, **kw)
+        ms64.append(o64["t_solve_ms"])
+        it64.append(int(np.sum(o64["iters"])))
+    q64 = o64["Qext"]
+    qerr = float(np.max(np.abs(qext / q64 - 1)))
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e_ms = []
+    h2d = int(w.occ.nbytes + w.comp.nbytes)
+    d2h = R * N * 3 * 16
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        te = B.Target(w.occ, w.comp, w.m, method=w.method)
+        oe = te.solve(w.kd, w.khat, w.e01, precision="fp32_refined", want_P=True, **kw)
+        te.close()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        e2e_iters = int(np.sum(oe["iters"]))
+    t.close()
+
+    # ---- roofline of the dominant pass ----
+    per_rhs, per_launch = pass_bytes(w.shape, grid, 8)
+    dom = max(("fp32", p) for p in B.PASSES if kern_ms.get(("fp32", p), 0) > 0)
+    dom = max(((kern_ms[("fp32", p)], p) for p in B.PASSES))[1]
+    tms = kern_ms[("fp32", dom)]
+    ncall = kern_calls[("fp32", dom)]
+    alg = per_rhs[dom] * fp32_rhs_mv + per_launch.get(dom, 0) * ncall
+    achieved = alg / (tms / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic_rhs = _ncu_traffic(dom, "sphere64")
+    share = {f"{p}": round(kern_ms[("fp32", p)] / sum(step_ms), 4) for p in B.PASSES}
+    share.update({f"{p}_fp64": round(kern_ms[("fp64", p)] / sum(step_ms), 4)
+                  for p in B.PASSES})
+
+    # ---- aggregate over ranks (replicas) ----
+    tot = {"iters": float(sum(iters)), "dev_s": dev_s, "wall_s": t_wall}
+    if world > 1:
+        import torch.distributed as dist
+        v = torch.tensor([tot["iters"], dev_s, t_wall], dtype=torch.float64)
+        s_it = v.clone()
+        dist.all_reduce(s_it, op=dist.ReduceOp.SUM)
+        m_t = v.clone()
+        dist.all_reduce(m_t, op=dist.ReduceOp.MAX)
+        tot = {"iters": s_it[0].item(), "dev_s": m_t[1].item(), "wall_s": m_t[2].item()}
+    if rank != 0:
+        return 0
+    value = N * tot["iters"] / tot["dev_s"]
+    cpu = None
+    if world == 1 or rank == 0:
+        v_cpu, dt_cpu, setup_cpu, it_cpu = oracle_sample(w, 3)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{it_cpu} BiCGSTAB iterations of one polarization of this workload "
+                         f"(numpy FFT convolution, FP64, single-threaded; {dt_cpu:.1f} s, "
+                         f"setup {setup_cpu:.1f} s excluded)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot["dev_s"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 inner / c128 refinement", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "box": list(w.shape), "grid": list(grid),
+                   "rhs": R, "precision": "fp32_refined", "tol": w.tol,
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "solves_per_s": R * args.steps * world / tot["dev_s"],
+        "latency_ms": {"p50": statistics.median(step_ms),
+                       "p99": sorted(step_ms)[min(len(step_ms) - 1,
+                                                   int(math.ceil(0.99 * len(step_ms))) - 1)]},
+        "iters_per_rhs": sum(iters) / (R * args.steps),
+        "fp64_vs_refined": {
+            "fp64_ms_per_solve_batch": statistics.mean(ms64),
+            "fp64_dipole_iters_per_s": N * sum(it64) / (sum(ms64) / 1e3),
+            "fp64_iters_per_rhs": sum(it64) / (R * k64),
+            "refined_speedup": statistics.mean(ms64) / statistics.mean(step_ms),
+            "qext_rel_diff": qerr, "qext": [float(q) for q in qext],
+            "resid_refined": [float(r) for r in resid]},
+        "setup_ms": setup["t_setup_ms"],
+        "roofline": {"bound": "hbm", "kernel": f"k_fft_{dom} (fp32)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_rhs": per_rhs[dom],
+                     "traffic": None if traffic_rhs is None else traffic_rhs,
+                     "share_of_step": share},
+        "cpu_baseline": cpu,
+        "e2e": {"value": N * e2e_iters / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": statistics.mean(e2e_ms),
+                "includes": "target create (occupancy upload, Green-tensor transform), "
+                            "solve, P download, destroy"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

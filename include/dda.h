@@ -1,0 +1,194 @@
+/*
+ * dda.h -- C ABI of the GB300 discrete-dipole-approximation (DDA) solver.
+ *
+ * The library solves A P = E (the DDSCAT 7.3 guide, Sec. "Choice of Iterative
+ * Algorithm", eq. AP=E) for N polarizable points on a cubic lattice: E is the
+ * incident field at the occupied sites, P the unknown dipole moments and A the
+ * 3N x 3N interaction matrix, (A P)_j = alpha_j^{-1} P_j - sum_{l != j}
+ * G(r_j - r_l) P_l.  The product A.P is evaluated as a zero-padded 3-D FFT
+ * convolution of the three polarization components with the six unique
+ * components of the lattice Green tensor (Sec. "Choice of FFT Algorithm"), on
+ * the GPU, and the system is solved by BiCGSTAB (the PIM method behind the
+ * guide's PBCGST option).
+ *
+ * Conventions (all calls):
+ *  - Lattice units: d = 1; "kd" is k d with k the wavenumber in the ambient
+ *    medium; refractive indices m are relative to the ambient medium (Sec.
+ *    "Application to Targets in Dielectric Media").
+ *  - A target box is nx * ny * nz sites; site (ix, iy, iz) has flat index
+ *    ix + nx*(iy + ny*iz) and sits at r = (ix - (nx-1)/2, iy - (ny-1)/2,
+ *    iz - (nz-1)/2) (origin at the box centre).  Vectors over the N occupied
+ *    sites are stored in flat-index order.
+ *  - Complex numbers are two consecutive doubles (re, im).
+ *  - Every pointer argument is a HOST pointer unless stated; the library copies
+ *    what it needs and never keeps a caller's pointer after the call returns.
+ *  - No call throws; each returns a dda_status.  dda_last_error() gives a
+ *    human-readable detail for the calling thread's last failing call.
+ *  - One dda_target must not be used from two threads at once; distinct
+ *    targets may be used concurrently (each call runs on its own stream).
+ *  - Without a usable CUDA device every compute call returns DDA_ERR_CUDA;
+ *    there is no CPU fallback.
+ */
+#ifndef DDA_H
+#define DDA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DDA_OK = 0,
+  DDA_ERR_INVALID_ARG = 1, /* a size, pointer or option is out of range        */
+  DDA_ERR_OOM = 2,         /* device allocation failed (nothing is leaked)     */
+  DDA_ERR_CUDA = 3,        /* CUDA error, or no device                         */
+  DDA_ERR_NOCONV = 4,      /* max_iter reached; outputs hold the last iterate  */
+  DDA_ERR_BREAKDOWN = 5,   /* BiCGSTAB breakdown (rho or omega ~ 0, or NaN)     */
+  DDA_ERR_TIMEOUT = 6      /* a bounded device wait ran out                    */
+} dda_status;
+
+/* Polarizability prescriptions (Sec. "Choice of DDA Method").
+ *  CM : Clausius-Mossotti alpha_CM = 3/(4 pi) (m^2-1)/(m^2+2) with the
+ *       radiative-reaction correction alpha = alpha_CM / (1 - (2/3) i (kd)^3 alpha_CM).
+ *  LDR: LATTDR, alpha = alpha_CM / {1 + alpha_CM [(b1 + m^2 b2 + m^2 b3 S)(kd)^2
+ *       - (2/3) i (kd)^3]}, S = sum_j (khat_j e_j)^2, with the Draine & Goodman
+ *       (1993) coefficients; depends on each incident direction and polarization.
+ *  FCD: FLTRCD, alpha = alpha_CM / {1 - alpha_CM [(4/3)(kd)^2 + (2/(3 pi))
+ *       ln((pi-kd)/(pi+kd)) (kd)^3 + (2/3) i (kd)^3]} (Sec. "Filtered Coupled
+ *       Dipole", read with the sign and (kd)^3 factor that make a lossless
+ *       material absorb nothing), and the interaction tensor is the filtered one,
+ *       (k^2 + grad grad) of the outgoing Green function with spatial
+ *       frequencies above pi/d removed.  CM and LDR use the point-dipole tensor
+ *       G(r) P = e^{ikr}/r^3 {k^2 r^2 (rhat x P) x rhat + (1-ikr)[3 rhat(rhat.P) - P]}. */
+typedef enum { DDA_POL_CM = 0, DDA_POL_LDR = 1, DDA_POL_FCD = 2 } dda_pol_method;
+
+/* Arithmetic of the solve.
+ *  FP64        : every step in FP64.
+ *  FP32        : FFT convolution and Krylov vectors in complex FP32, inner
+ *                products and norms accumulated in FP64; the reported residual
+ *                is still the FP64 true residual of the result.
+ *  FP32_REFINED: FP64 iterative refinement around FP32 inner BiCGSTAB solves:
+ *                r = E - A P in FP64, solve A d = r in FP32 to inner_tol,
+ *                P += d in FP64, until ||E - A P|| / ||E|| <= tol (the guide's
+ *                single/double precision discussion, Sec. "Single vs. Double
+ *                Precision", motivates keeping the accuracy-critical parts in FP64). */
+typedef enum {
+  DDA_PREC_FP64 = 0,
+  DDA_PREC_FP32 = 1,
+  DDA_PREC_FP32_REFINED = 2
+} dda_precision;
+
+typedef struct dda_target dda_target; /* opaque, library-owned */
+
+/* Create a target from an occupancy grid.
+ *  occ : nx*ny*nz bytes, nonzero = occupied site.
+ *  comp: nx*ny*nz bytes, composition 1..ncomp at occupied sites (ignored
+ *        elsewhere); NULL means composition 1 everywhere.
+ *  m   : ncomp complex refractive indices (interleaved re, im), relative to the
+ *        ambient medium (Sec. "Target Geometry: The Target Frame": a target is the list of
+ *        occupied sites with their composition).
+ *  out : receives the new target; freed with dda_target_destroy.
+ * Limits: 1 <= nx, ny, nz <= 4096, 1 <= ncomp <= 255, at least one occupied
+ * site.  Device memory for the target (composition grid, site list) is
+ * allocated here; the Green-tensor transform is built on the first solve or
+ * matvec for a given (kd, method) and kept until the next different one. */
+dda_status dda_target_create(int nx, int ny, int nz, const uint8_t* occ,
+                             const uint8_t* comp, int ncomp, const double* m,
+                             dda_target** out);
+
+/* Select the polarizability prescription used by later solves (default LDR). */
+dda_status dda_set_polarizability(dda_target* t, dda_pol_method method);
+
+/* y = A x for one incident wave (the hot loop's operator, eq. AP=E).
+ *  kd        : k d (> 0, < pi for FCD).
+ *  khat, e   : incident direction [3] and polarization [3][2] (only LDR reads
+ *              them; may be NULL otherwise).
+ *  x, y      : [N][3][2] on the occupied sites in flat-index order (host).
+ *  precision : DDA_PREC_FP64 or DDA_PREC_FP32 (FP32_REFINED acts as FP32). */
+dda_status dda_matvec(dda_target* t, double kd, const double* khat, const double* e,
+                      const double* x, double* y, dda_precision precision);
+
+typedef struct {
+  double kd;             /* k d in the ambient medium                           */
+  int n_inc;             /* number of incident directions (orientations) >= 1   */
+  const double* khat;    /* [n_inc][3] unit propagation vectors, target frame   */
+  const double* yhat;    /* [n_inc][3] Lab-Frame y axis in the target frame, for
+                            the scattering basis; NULL = normalized Re(e01)    */
+  const double* e01;     /* [n_inc][3][2] first polarization (normalized by the
+                            library); e02 = khat x conj(e01)                    */
+  int npol;              /* 1 or 2 polarizations per direction                  */
+  double tol;            /* stop when ||E - A P|| / ||E|| <= tol (FP64)          */
+  int max_iter;          /* cap on BiCGSTAB iterations per RHS (all sweeps)     */
+  dda_precision precision;
+  double inner_tol;      /* FP32_REFINED inner tolerance; <= 0 selects 1e-4     */
+  int n_dirs;            /* scattering directions besides forward (>= 0)        */
+  const double* dirs;    /* [n_dirs][2] (theta_s, phi_s) radians in the Lab Frame
+                            (x_LF = khat, y_LF = yhat): n = x cos(theta) +
+                            y sin(theta) cos(phi) + z sin(theta) sin(phi)       */
+  const double* P0;      /* optional warm start [n_inc*npol][N][3][2] or NULL   */
+  int profile;           /* nonzero: time each FFT-matvec pass with CUDA events   */
+} dda_solve_params;
+
+/* Results.  Every array is caller-allocated HOST memory; a NULL pointer means
+ * "not requested".  Right-hand side index rhs = inc*npol + pol. */
+typedef struct {
+  double* P;       /* [n_rhs][N][3][2] dipole moments (|E_0| = 1)                  */
+  double* Qext;    /* [n_rhs] extinction efficiency C_ext / (pi a_eff^2)           */
+  double* Qabs;    /* [n_rhs] absorption efficiency                                 */
+  double* Qsca;    /* [n_rhs] Q_ext - Q_abs                                         */
+  double* famp;    /* [n_inc][n_dirs+1][2 (m)][npol (l)][2] scattering amplitudes
+                      f_ml (Sec. "Scattering by Finite Targets: The Mueller Matrix", eq. f_ml_def);
+                      direction 0 is forward                                         */
+  int* iters;      /* [n_rhs] BiCGSTAB iterations (inner iterations when refined)   */
+  double* resid;   /* [n_rhs] final FP64 true relative residual ||E - A P|| / ||E||  */
+  int* sweeps;     /* [n_rhs] FP64 refinement sweeps (1 when not refined)           */
+  double t_setup_ms;   /* Green-tensor transform build in this call (0 if cached) */
+  double t_solve_ms;   /* solve, observables and copies (device events)           */
+  int64_t matvecs;     /* RHS-matvecs executed (FP32 + FP64)                      */
+  int64_t matvecs_fp64;
+  /* with params->profile: device time (ms) and launch count of the five matvec
+     passes, [precision 0 = FP32, 1 = FP64][pass: x fwd, y fwd, z fwd+multiply+
+     inverse, y inv, x inv + diagonal], summed over the call                       */
+  double kernel_ms[10];
+  int64_t kernel_calls[10];
+  int64_t launches;    /* CUDA kernels this call launched                          */
+} dda_solve_result;
+
+/* Solve A P = E for every incident direction and polarization of params as one
+ * batch of right-hand sides (they share A unless the polarizability is LDR,
+ * where only alpha differs per RHS), then compute Q_ext, Q_abs (Sec. "What
+ * Does It Calculate?"; Q = C / (pi a_eff^2), a_eff = (3N/4pi)^(1/3) d) and
+ * f_ml for the forward direction and params->dirs.  Returns DDA_ERR_NOCONV if
+ * some RHS did not reach tol within max_iter (results hold the last iterate). */
+dda_status dda_solve(dda_target* t, const dda_solve_params* params,
+                     dda_solve_result* result);
+
+/* Free a target and all its device memory.  NULL is ignored. */
+void dda_target_destroy(dda_target* t);
+
+/* Static string for a status code. */
+const char* dda_status_string(dda_status s);
+
+/* Detail of the calling thread's last failing call ("" if none). */
+const char* dda_last_error(void);
+
+/* Kernels launched by this library since the process started (all threads). */
+int64_t dda_launch_count(void);
+
+/* Number of occupied sites N of a target (-1 for NULL). */
+int64_t dda_target_num_dipoles(const dda_target* t);
+
+/* Upper bound on the device bytes dda_solve(t, params, ...) allocates beyond
+ * what the target already holds (admission control); -1 on bad arguments. */
+int64_t dda_solve_hbm_bytes(const dda_target* t, const dda_solve_params* params);
+
+/* FFT grid chosen for a target: the smallest 2^a 3^b 5^c lengths >= 2n-1 per
+ * axis (Sec. "Choice of FFT Algorithm": the guide's GPFA grid sizes). */
+dda_status dda_target_grid(const dda_target* t, int* Lx, int* Ly, int* Lz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDA_H */

@@ -11,7 +11,7 @@ Gaussian units (the guide follows Draine 1988).
 
 Contents, each citing the passage it follows:
   site_positions           -- targets as lists of occupied lattice sites (Sec.
-                              "Target Generation", x = [(i,j,k) + x0] d)
+                              "Target Geometry: The Target Frame")
   alpha_cm / polarizability -- Clausius-Mossotti, CM with radiative reaction,
                               LATTDR and FLTRCD (Sec. "Choice of DDA Method")
   incident_field           -- E_inc,j = e exp(i k khat.r_j) (Sec. "Incident
@@ -23,7 +23,7 @@ Contents, each citing the passage it follows:
   bicgstab                 -- BiCGSTAB (van der Vorst 1992), the PIM method the
                               guide's PBCGST option runs (Sec. "Choice of
                               Iterative Algorithm")
-  cross_sections           -- Q_ext, Q_abs, Q_sca (Sec. "Scattering ...")
+  cross_sections           -- Q_ext, Q_abs, Q_sca (Sec. "What Does It Calculate?")
   scattering_amplitudes    -- f_ml (eq. f_ml_def)
 
 Readings where the guide is silent or garbled are stated at each function and
@@ -66,7 +66,7 @@ def site_positions(occ: np.ndarray):
 
 
 def effective_radius(n_dipoles: int) -> float:
-    """a_eff = (3 V / 4 pi)^(1/3) with V = N d^3 (Sec. "Target Size ...")."""
+    """a_eff = (3 V / 4 pi)^(1/3) with V = N d^3 (Sec. "Applicability of the DDA")."""
     return (3.0 * n_dipoles / (4.0 * math.pi)) ** (1.0 / 3.0)
 
 
@@ -372,7 +372,7 @@ def cross_sections(P: np.ndarray, E: np.ndarray, ainv: np.ndarray, kd: float):
 
     C_ext = 4 pi k sum_j Im(E_inc,j^* . P_j)
     C_abs = 4 pi k sum_j |P_j|^2 [-Im(1/alpha_j) - (2/3) k^3]     (scalar alpha)
-    Q = C / (pi a_eff^2), Q_sca = Q_ext - Q_abs (Sec. "What Does DDSCAT
+    Q = C / (pi a_eff^2), Q_sca = Q_ext - Q_abs (Sec. "What Does It
     Calculate?": Q_ext = Q_sca + Q_abs).
     """
     k = float(kd)
@@ -390,7 +390,7 @@ def scattering_frame(khat, yhat, theta, phi):
     """(n_s, theta_hat, phi_hat) in TF coordinates for a Lab-Frame direction.
 
     The Lab Frame has x_LF = khat and y_LF = yhat; n_s = x cos(theta) +
-    y sin(theta) cos(phi) + z sin(theta) sin(phi) (Sec. "Scattering Directions",
+    y sin(theta) cos(phi) + z sin(theta) sin(phi) (Sec. "Scattering Directions", "Isolated Finite Targets",
     LFRAME), theta_hat = dn/dtheta, phi_hat = (dn/dphi)/sin(theta).
     """
     x = np.asarray(khat, dtype=np.float64)

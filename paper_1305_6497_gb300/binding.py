@@ -1,0 +1,256 @@
+"""ctypes binding of libdda.so (include/dda.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and converts
+numpy arrays to the plain pointers and sizes of the C ABI; all computation
+happens in the CUDA library.  Importing this module loads libdda.so and raises
+if it is missing -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdda.so")
+
+DDA_OK, DDA_ERR_INVALID_ARG, DDA_ERR_OOM, DDA_ERR_CUDA, DDA_ERR_NOCONV, \
+    DDA_ERR_BREAKDOWN, DDA_ERR_TIMEOUT = range(7)
+POL = {"CM": 0, "LDR": 1, "FCD": 2}
+PREC = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
+
+_dp = ct.POINTER(ct.c_double)
+_ip = ct.POINTER(ct.c_int)
+
+
+class SolveParams(ct.Structure):
+    _fields_ = [("kd", ct.c_double), ("n_inc", ct.c_int), ("khat", _dp), ("yhat", _dp),
+                ("e01", _dp), ("npol", ct.c_int), ("tol", ct.c_double),
+                ("max_iter", ct.c_int), ("precision", ct.c_int), ("inner_tol", ct.c_double),
+                ("n_dirs", ct.c_int), ("dirs", _dp), ("P0", _dp), ("profile", ct.c_int)]
+
+
+class SolveResult(ct.Structure):
+    _fields_ = [("P", _dp), ("Qext", _dp), ("Qabs", _dp), ("Qsca", _dp), ("famp", _dp),
+                ("iters", _ip), ("resid", _dp), ("sweeps", _ip),
+                ("t_setup_ms", ct.c_double), ("t_solve_ms", ct.c_double),
+                ("matvecs", ct.c_int64), ("matvecs_fp64", ct.c_int64),
+                ("kernel_ms", ct.c_double * 10), ("kernel_calls", ct.c_int64 * 10),
+                ("launches", ct.c_int64)]
+
+PASSES = ("x_fwd", "y_fwd", "z_mul", "y_inv", "x_inv")
+
+
+class DDAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ct.CDLL(LIB_PATH)
+    vp = ct.c_void_p
+    lib.dda_target_create.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p,
+                                      ct.c_int, _dp, ct.POINTER(vp)]
+    lib.dda_target_create.restype = ct.c_int
+    lib.dda_set_polarizability.argtypes = [vp, ct.c_int]
+    lib.dda_set_polarizability.restype = ct.c_int
+    lib.dda_matvec.argtypes = [vp, ct.c_double, _dp, _dp, _dp, _dp, ct.c_int]
+    lib.dda_matvec.restype = ct.c_int
+    lib.dda_solve.argtypes = [vp, ct.POINTER(SolveParams), ct.POINTER(SolveResult)]
+    lib.dda_solve.restype = ct.c_int
+    lib.dda_target_destroy.argtypes = [vp]
+    lib.dda_target_destroy.restype = None
+    lib.dda_status_string.argtypes = [ct.c_int]
+    lib.dda_status_string.restype = ct.c_char_p
+    lib.dda_last_error.argtypes = []
+    lib.dda_last_error.restype = ct.c_char_p
+    lib.dda_target_num_dipoles.argtypes = [vp]
+    lib.dda_target_num_dipoles.restype = ct.c_int64
+    lib.dda_solve_hbm_bytes.argtypes = [vp, ct.POINTER(SolveParams)]
+    lib.dda_solve_hbm_bytes.restype = ct.c_int64
+    lib.dda_target_grid.argtypes = [vp, _ip, _ip, _ip]
+    lib.dda_target_grid.restype = ct.c_int
+    lib.dda_launch_count.argtypes = []
+    lib.dda_launch_count.restype = ct.c_int64
+    return lib
+
+
+lib = _load()
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _check(status, allow=()):
+    if status != DDA_OK and status not in allow:
+        raise DDAError(status, f"{lib.dda_status_string(status).decode()}: "
+                               f"{lib.dda_last_error().decode()}")
+    return status
+
+
+def dda_status_string(status: int) -> str:
+    return lib.dda_status_string(status).decode()
+
+
+def dda_last_error() -> str:
+    return lib.dda_last_error().decode()
+
+
+def dda_launch_count() -> int:
+    return int(lib.dda_launch_count())
+
+
+def dda_target_create(occ: np.ndarray, comp: np.ndarray | None, m) -> int:
+    """occ/comp: (nz, ny, nx) arrays; m: complex refractive indices.  Returns a handle."""
+    occ = np.ascontiguousarray(occ, dtype=np.uint8)
+    nz, ny, nx = occ.shape
+    if comp is not None:
+        comp = np.ascontiguousarray(comp, dtype=np.uint8)
+    mm = np.ascontiguousarray(np.array(m, dtype=np.complex128).view(np.float64))
+    h = ct.c_void_p()
+    _check(lib.dda_target_create(nx, ny, nz, occ.ctypes.data,
+                                 None if comp is None else comp.ctypes.data,
+                                 len(m), _ptr(mm), ct.byref(h)))
+    return h.value
+
+
+def dda_set_polarizability(h, method: str) -> None:
+    _check(lib.dda_set_polarizability(h, POL[method]))
+
+
+def dda_target_destroy(h) -> None:
+    lib.dda_target_destroy(h)
+
+
+def dda_target_num_dipoles(h) -> int:
+    return int(lib.dda_target_num_dipoles(h))
+
+
+def dda_target_grid(h):
+    a, b, c = ct.c_int(), ct.c_int(), ct.c_int()
+    _check(lib.dda_target_grid(h, ct.byref(a), ct.byref(b), ct.byref(c)))
+    return a.value, b.value, c.value
+
+
+def dda_matvec(h, kd: float, x: np.ndarray, khat=None, e=None, precision="fp64") -> np.ndarray:
+    """y = A x; x: [N, 3] complex on the occupied sites (flat-index order)."""
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    y = np.empty_like(x)
+    kh = None if khat is None else np.ascontiguousarray(khat, dtype=np.float64)
+    ee = None if e is None else np.ascontiguousarray(np.asarray(e, np.complex128).view(np.float64))
+    _check(lib.dda_matvec(h, float(kd), _ptr(kh), _ptr(ee), _ptr(x.view(np.float64)),
+                          _ptr(y.view(np.float64)), PREC[precision]))
+    return y
+
+
+def _params(kd, khat, e01, yhat, npol, tol, max_iter, precision, inner_tol, dirs, P0,
+            profile=False):
+    keep = []
+
+    def arr(a, dtype=np.float64):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dtype)
+        keep.append(a)
+        return a
+
+    khat = arr(np.atleast_2d(khat))
+    n_inc = khat.shape[0]
+    e = arr(np.atleast_2d(np.asarray(e01, np.complex128)), np.complex128)
+    yh = arr(None if yhat is None else np.atleast_2d(yhat))
+    d = arr(None if dirs is None or len(dirs) == 0 else np.asarray(dirs).reshape(-1, 2))
+    p0 = arr(None if P0 is None else np.asarray(P0, np.complex128), np.complex128)
+    prm = SolveParams(kd=float(kd), n_inc=n_inc, khat=_ptr(khat), yhat=_ptr(yh),
+                      e01=_ptr(e.view(np.float64)), npol=int(npol), tol=float(tol),
+                      max_iter=int(max_iter), precision=PREC[precision],
+                      inner_tol=float(inner_tol), n_dirs=0 if d is None else d.shape[0],
+                      dirs=_ptr(d), P0=None if p0 is None else _ptr(p0.view(np.float64)),
+                      profile=1 if profile else 0)
+    return prm, keep, n_inc
+
+
+def dda_solve_hbm_bytes(h, kd, khat, e01, npol=2, precision="fp64", dirs=None) -> int:
+    prm, keep, _ = _params(kd, khat, e01, None, npol, 1e-8, 1, precision, 0.0, dirs, None)
+    return int(lib.dda_solve_hbm_bytes(h, ct.byref(prm)))
+
+
+def dda_solve(h, kd, khat, e01, yhat=None, npol=2, tol=1e-8, max_iter=2000,
+              precision="fp64", inner_tol=0.0, dirs=None, P0=None, want_P=True,
+              want_famp=True, raise_on_noconv=False, profile=False) -> dict:
+    """Solve for every incidence x polarization.  Returns a dict of numpy arrays."""
+    prm, keep, n_inc = _params(kd, khat, e01, yhat, npol, tol, max_iter, precision,
+                               inner_tol, dirs, P0, profile)
+    N = dda_target_num_dipoles(h)
+    R = n_inc * npol
+    D = prm.n_dirs + 1
+    out = dict(P=np.empty((R, N, 3), np.complex128) if want_P else None,
+               Qext=np.empty(R), Qabs=np.empty(R), Qsca=np.empty(R),
+               famp=np.empty((n_inc, D, 2, npol), np.complex128) if want_famp else None,
+               iters=np.empty(R, np.int32), resid=np.empty(R), sweeps=np.empty(R, np.int32))
+    res = SolveResult(
+        P=None if out["P"] is None else _ptr(out["P"].view(np.float64)),
+        Qext=_ptr(out["Qext"]), Qabs=_ptr(out["Qabs"]), Qsca=_ptr(out["Qsca"]),
+        famp=None if out["famp"] is None else _ptr(out["famp"].view(np.float64)),
+        iters=out["iters"].ctypes.data_as(_ip), resid=_ptr(out["resid"]),
+        sweeps=out["sweeps"].ctypes.data_as(_ip))
+    st = lib.dda_solve(h, ct.byref(prm), ct.byref(res))
+    allow = () if raise_on_noconv else (DDA_ERR_NOCONV,)
+    _check(st, allow)
+    out["status"] = st
+    out["t_setup_ms"] = res.t_setup_ms
+    out["t_solve_ms"] = res.t_solve_ms
+    out["matvecs"] = res.matvecs
+    out["matvecs_fp64"] = res.matvecs_fp64
+    out["launches"] = res.launches
+    if profile:
+        out["kernel_ms"] = {(p, PASSES[i]): res.kernel_ms[5 * k + i]
+                            for k, p in enumerate(("fp32", "fp64")) for i in range(5)}
+        out["kernel_calls"] = {(p, PASSES[i]): res.kernel_calls[5 * k + i]
+                               for k, p in enumerate(("fp32", "fp64")) for i in range(5)}
+    return out
+
+
+class Target:
+    """Owning wrapper around a dda_target handle."""
+
+    def __init__(self, occ, comp=None, m=(1.5 + 0j,), method="LDR"):
+        self.h = dda_target_create(occ, comp, list(m))
+        self.shape = tuple(np.asarray(occ).shape[::-1])
+        dda_set_polarizability(self.h, method)
+
+    def close(self):
+        if self.h:
+            dda_target_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_dipoles(self):
+        return dda_target_num_dipoles(self.h)
+
+    @property
+    def grid(self):
+        return dda_target_grid(self.h)
+
+    def set_polarizability(self, method):
+        dda_set_polarizability(self.h, method)
+
+    def matvec(self, kd, x, khat=None, e=None, precision="fp64"):
+        return dda_matvec(self.h, kd, x, khat, e, precision)
+
+    def solve(self, kd, khat, e01, **kw):
+        return dda_solve(self.h, kd, khat, e01, **kw)
+
+    def hbm_bytes(self, kd, khat, e01, **kw):
+        return dda_solve_hbm_bytes(self.h, kd, khat, e01, **kw)

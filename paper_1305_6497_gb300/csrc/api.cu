@@ -1,0 +1,1046 @@
+// C ABI of the DDA library: targets, the Green-tensor transform cache, the
+// BiCGSTAB drivers (FP64, FP32, FP32 with FP64 refinement) and observables.
+// See include/dda.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dda.h"
+#include "dda_ops.h"
+
+using namespace dda;
+using cd = std::complex<double>;
+
+#include <atomic>
+static std::atomic<long long> g_launches{0};
+void dda::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long dda::launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static dda_status fail(dda_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+struct CudaFail {
+  cudaError_t e;
+  const char* what;
+};
+
+#define CK(expr)                                                   \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) throw CudaFail{_e, #expr};              \
+  } while (0)
+
+static dda_status from_cuda(const CudaFail& f) {
+  cudaGetLastError();  // clear sticky-free errors
+  std::string msg = std::string(f.what) + ": " + cudaGetErrorString(f.e);
+  if (f.e == cudaErrorMemoryAllocation) return fail(DDA_ERR_OOM, msg);
+  return fail(DDA_ERR_CUDA, msg);
+}
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void ensure(size_t n) {
+    if (n <= bytes) return;
+    release();
+    if (n == 0) return;
+    CK(cudaMalloc(&p, n));
+    bytes = n;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename X> X* as() const { return reinterpret_cast<X*>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// FFT plans (Stockham radix sequence and twiddles, host side)
+// ---------------------------------------------------------------------------
+static bool is_smooth(int n) {
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+// smallest 2^a 3^b 5^c >= m (the guide's GPFA lengths)
+static int smooth_at_least(int m) {
+  int n = std::max(1, m);
+  while (!is_smooth(n)) ++n;
+  return n;
+}
+
+static std::vector<int> factor_radices(int L) {
+  int a = 0, n = L;
+  while (n % 2 == 0) { n /= 2; ++a; }
+  std::vector<int> r;
+  // powers of two: radix 8 as long as no single 2 is left over
+  int e8 = a / 3, rem = a % 3;
+  if (rem == 1 && e8 >= 1) { e8 -= 1; r.push_back(4); r.push_back(4); }
+  else if (rem == 1) r.push_back(2);
+  else if (rem == 2) r.push_back(4);
+  for (int i = 0; i < e8; ++i) r.insert(r.begin(), 8);
+  while (n % 3 == 0) { n /= 3; r.push_back(3); }
+  while (n % 5 == 0) { n /= 5; r.push_back(5); }
+  return r;
+}
+
+// In-place plan: stage t has radix rs[t], block B_t = L / (rs[0]...rs[t-1]) and
+// twiddles exp(-2 pi i j m / B_t), j < B_t/rs[t], m = 1..rs[t]-1.  Also returns
+// which frequency ends up at each position after the forward (decimation in
+// frequency) transform: position sum_t m_t S_t holds sum_t m_t N_t with
+// S_t = B_t/rs[t] and N_t = rs[0]...rs[t-1].
+static AxisPlan make_plan(int L, std::vector<long double>& twr, std::vector<long double>& twi,
+                          std::vector<int>& k_at) {
+  AxisPlan P{};
+  P.L = L;
+  std::vector<int> rs = factor_radices(L);
+  P.nstage = (int)rs.size();
+  int B = L, off = 0;
+  twr.clear(); twi.clear();
+  const long double two_pi = 6.283185307179586476925286766559L;
+  std::vector<int> S(P.nstage), Nt(P.nstage);
+  int nprod = 1;
+  for (int t = 0; t < P.nstage; ++t) {
+    const int R = rs[t];
+    const int Sp = B / R;
+    P.radix[t] = R;
+    P.blk[t] = B;
+    P.tw_off[t] = off;
+    for (int j = 0; j < Sp; ++j)
+      for (int m = 1; m < R; ++m) {
+        const long long num = ((long long)j * m) % (long long)B;
+        const long double ang = -two_pi * (long double)num / (long double)B;
+        twr.push_back(cosl(ang));
+        twi.push_back(sinl(ang));
+      }
+    off += Sp * (R - 1);
+    S[t] = Sp;
+    Nt[t] = nprod;
+    nprod *= R;
+    B = Sp;
+  }
+  P.tw_len = off;
+  k_at.assign(L, 0);
+  for (int pos = 0; pos < L; ++pos) {
+    int q = pos, k = 0;
+    for (int t = 0; t < P.nstage; ++t) {
+      const int m = q / S[t];
+      q -= m * S[t];
+      k += m * Nt[t];
+    }
+    k_at[pos] = k;
+  }
+  return P;
+}
+
+// ---------------------------------------------------------------------------
+// target
+// ---------------------------------------------------------------------------
+struct Workspace {
+  int R = 0;
+  // FP64
+  DevBuf b64, x64, r64, rh64, p64, v64, s64, t64, scr64;
+  // FP32
+  DevBuf x32, r32, rh32, p32, v32, s32, t32, scr32, b32;
+  DevBuf partials, ks, active, active_outer, norms, sums;
+  DevBuf pol, ph, ainv64, ainv32, wabs, fph, sitebuf;
+  void release_all() {
+    for (DevBuf* b : {&b64, &x64, &r64, &rh64, &p64, &v64, &s64, &t64, &scr64, &x32, &r32,
+                      &rh32, &p32, &v32, &s32, &t32, &scr32, &b32, &partials, &ks, &active,
+                      &active_outer, &norms, &sums, &pol, &ph, &ainv64, &ainv32, &wabs, &fph,
+                      &sitebuf})
+      b->release();
+  }
+};
+
+// Per-pass CUDA-event timing of the matvec kernels (enabled per solve).
+struct Profiler {
+  bool on = false;
+  bool created = false;
+  cudaEvent_t ev[3][kMatvecPasses + 1];
+  double ms[2][kMatvecPasses];
+  long long calls[2][kMatvecPasses];
+  void reset() {
+    for (int p = 0; p < 2; ++p)
+      for (int i = 0; i < kMatvecPasses; ++i) { ms[p][i] = 0.0; calls[p][i] = 0; }
+  }
+  void create() {
+    if (created) return;
+    for (auto& set : ev)
+      for (auto& e : set) CK(cudaEventCreate(&e));
+    created = true;
+  }
+  void destroy() {
+    if (!created) return;
+    for (auto& set : ev)
+      for (auto& e : set) cudaEventDestroy(e);
+    created = false;
+  }
+  const cudaEvent_t* set(int k) const { return on ? ev[k] : nullptr; }
+  // after a synchronize: add the pass times of event set k to precision slot p
+  void harvest(int p, int k) {
+    if (!on) return;
+    for (int i = 0; i < kMatvecPasses; ++i) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, ev[k][i], ev[k][i + 1]));
+      ms[p][i] += t;
+      calls[p][i] += 1;
+    }
+  }
+};
+
+struct dda_target {
+  int nx = 0, ny = 0, nz = 0;
+  int64_t nbox = 0, N = 0;
+  int ncomp = 0;
+  std::vector<cd> m;
+  dda_pol_method method = DDA_POL_LDR;
+  int Lx = 0, Ly = 0, Lz = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  DevBuf comp, site, tw64, tw32, perm;  // perm: k_at x|y|z, then pos x|y|z
+  AxisPlan px{}, py{}, pz{};
+  int twoff[3] = {0, 0, 0};
+  // Green transform cache
+  bool have_green = false;
+  double green_kd = 0.0;
+  int green_filtered = -1;
+  DevBuf g64, g32;
+  MatvecLaunch L32{}, L64{};
+  bool kernels_configured = false;
+  Workspace ws;
+  Profiler prof;
+};
+
+static int64_t octant_size(const dda_target* t) {
+  return (int64_t)(t->Lx / 2 + 1) * (t->Ly / 2 + 1) * (t->Lz / 2 + 1);
+}
+
+template <typename T>
+static OpView<T> make_view(const dda_target* t, const void* ghat, const void* ainv,
+                           const void* tw) {
+  OpView<T> v{};
+  v.nx = t->nx; v.ny = t->ny; v.nz = t->nz;
+  v.Lx = t->Lx; v.Ly = t->Ly; v.Lz = t->Lz;
+  v.Hx = t->Lx / 2 + 1; v.Hy = t->Ly / 2 + 1; v.Hz = t->Lz / 2 + 1;
+  v.nbox = t->nbox;
+  v.comp = t->comp.as<uint8_t>();
+  v.ghat = reinterpret_cast<const cplx_t<T>*>(ghat);
+  v.ainv = reinterpret_cast<const cplx_t<T>*>(ainv);
+  v.ncomp1 = t->ncomp + 1;
+  const cplx_t<T>* tb = reinterpret_cast<const cplx_t<T>*>(tw);
+  v.twx = tb + t->twoff[0];
+  v.twy = tb + t->twoff[1];
+  v.twz = tb + t->twoff[2];
+  const int* pm = t->perm.as<int>();
+  v.kx_at = pm;
+  v.ky_at = pm + t->Lx;
+  v.kz_at = pm + t->Lx + t->Ly;
+  v.px = t->px; v.py = t->py; v.pz = t->pz;
+  return v;
+}
+
+static void build_green(dda_target* t, double kd, int filtered) {
+  if (t->have_green && t->green_kd == kd && t->green_filtered == filtered) return;
+  const int64_t M = (int64_t)t->Lx * t->Ly * t->Lz;
+  const int64_t H = octant_size(t);
+  t->have_green = false;
+  DevBuf full, tmp;
+  try {
+    full.ensure(sizeof(double2) * 6 * M);
+    tmp.ensure(sizeof(double2) * 6 * M);
+    t->g64.ensure(sizeof(double2) * 6 * H);
+    t->g32.ensure(sizeof(float2) * 6 * H);
+    CK(launch_green_fill(t->nx, t->ny, t->nz, t->Lx, t->Ly, t->Lz, kd, filtered,
+                         full.as<double2>(), t->stream));
+    // the full grid seen as a "box" of 2 RHS x 3 components: nothing is pruned
+    OpView<double> op = make_view<double>(t, nullptr, nullptr, t->tw64.p);
+    op.nx = t->Lx; op.ny = t->Ly; op.nz = t->Lz;
+    op.nbox = M;
+    op.comp = nullptr;
+    MatvecLaunch L = plan_matvec<double>(op);
+    CK(configure_matvec_kernels<double>(L));
+    CK(launch_fft3d_full(op, L, 6, full.as<double2>(), tmp.as<double2>(), t->stream));
+    const int* pos = t->perm.as<int>() + (t->Lx + t->Ly + t->Lz);
+    CK(launch_green_octant(t->Lx, t->Ly, t->Lz, pos, pos + t->Lx, pos + t->Lx + t->Ly,
+                           tmp.as<double2>(), t->g64.as<double2>(), t->g32.as<float2>(),
+                           t->stream));
+    CK(cudaStreamSynchronize(t->stream));
+  } catch (...) {
+    full.release();
+    tmp.release();
+    throw;
+  }
+  full.release();
+  tmp.release();
+  t->have_green = true;
+  t->green_kd = kd;
+  t->green_filtered = filtered;
+}
+
+// ---------------------------------------------------------------------------
+// polarizabilities and incident-wave tables (host, FP64)
+// ---------------------------------------------------------------------------
+static const double kLdrB1 = -1.8915316, kLdrB2 = 0.1648469, kLdrB3 = -1.7700004;
+
+static cd alpha_of(dda_pol_method meth, cd m, double kd, const double* khat, const cd* e) {
+  const double pi = 3.14159265358979323846;
+  const cd m2 = m * m;
+  const cd a0 = 3.0 / (4.0 * pi) * (m2 - 1.0) / (m2 + 2.0);
+  const cd I(0.0, 1.0);
+  const double k3 = kd * kd * kd;
+  if (meth == DDA_POL_CM) return a0 / (1.0 - (2.0 / 3.0) * I * k3 * a0);
+  if (meth == DDA_POL_LDR) {
+    double S = 0.0, en = 0.0;
+    for (int c = 0; c < 3; ++c) en += std::norm(e[c]);
+    for (int c = 0; c < 3; ++c) S += khat[c] * khat[c] * std::norm(e[c]) / en;
+    return a0 / (1.0 + a0 * ((kLdrB1 + m2 * kLdrB2 + m2 * kLdrB3 * S) * kd * kd -
+                             (2.0 / 3.0) * I * k3));
+  }
+  const double lg = std::log((pi - kd) / (pi + kd));
+  return a0 / (1.0 - a0 * ((4.0 / 3.0) * kd * kd + (2.0 / (3.0 * pi)) * lg * k3 +
+                           (2.0 / 3.0) * I * k3));
+}
+
+struct Incidence {
+  double khat[3];
+  double yhat[3];
+  cd e[2][3];  // e01, e02
+};
+
+static dda_status make_incidence(const dda_solve_params* p, int i, Incidence& inc) {
+  const double* k = p->khat + 3 * i;
+  double kn = std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+  if (!(kn > 0.0) || !std::isfinite(kn)) return fail(DDA_ERR_INVALID_ARG, "khat is zero");
+  for (int c = 0; c < 3; ++c) inc.khat[c] = k[c] / kn;
+  double en = 0.0;
+  cd e1[3];
+  for (int c = 0; c < 3; ++c) {
+    e1[c] = cd(p->e01[6 * i + 2 * c], p->e01[6 * i + 2 * c + 1]);
+    en += std::norm(e1[c]);
+  }
+  if (!(en > 0.0) || !std::isfinite(en)) return fail(DDA_ERR_INVALID_ARG, "e01 is zero");
+  en = std::sqrt(en);
+  for (int c = 0; c < 3; ++c) e1[c] /= en;
+  // e01 must be transverse
+  cd ke = 0.0;
+  for (int c = 0; c < 3; ++c) ke += inc.khat[c] * e1[c];
+  if (std::abs(ke) > 1e-6) return fail(DDA_ERR_INVALID_ARG, "e01 is not perpendicular to khat");
+  const double* x = inc.khat;
+  cd c1[3] = {std::conj(e1[0]), std::conj(e1[1]), std::conj(e1[2])};
+  cd e2[3] = {x[1] * c1[2] - x[2] * c1[1], x[2] * c1[0] - x[0] * c1[2],
+              x[0] * c1[1] - x[1] * c1[0]};
+  for (int c = 0; c < 3; ++c) { inc.e[0][c] = e1[c]; inc.e[1][c] = e2[c]; }
+  double y[3];
+  if (p->yhat) {
+    for (int c = 0; c < 3; ++c) y[c] = p->yhat[3 * i + c];
+  } else {
+    for (int c = 0; c < 3; ++c) y[c] = e1[c].real();
+    double yn = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+    if (yn < 1e-12)
+      for (int c = 0; c < 3; ++c) y[c] = e1[c].imag();
+  }
+  // orthonormalize y against khat
+  double d = y[0] * x[0] + y[1] * x[1] + y[2] * x[2];
+  for (int c = 0; c < 3; ++c) y[c] -= d * x[c];
+  double yn = std::sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+  if (!(yn > 1e-9)) return fail(DDA_ERR_INVALID_ARG, "yhat is parallel to khat");
+  for (int c = 0; c < 3; ++c) inc.yhat[c] = y[c] / yn;
+  return DDA_OK;
+}
+
+// per-axis phase table exp(i s kd u (i - (n-1)/2)) for i < n
+static void axis_phase(int n, double kd, double u, double sgn, std::vector<double2>& out) {
+  for (int i = 0; i < n; ++i) {
+    const double arg = sgn * kd * u * (i - 0.5 * (n - 1));
+    out.push_back(make_double2(std::cos(arg), std::sin(arg)));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// BiCGSTAB driver, R RHS in lockstep on the device.  Returns the number of
+// iterations per RHS through `its` and the status per RHS.
+// ---------------------------------------------------------------------------
+template <typename T> struct Vecs {
+  cplx_t<T>*b, *x, *r, *rh, *p, *v, *s, *t, *scr;
+};
+
+template <typename T>
+static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R,
+                     const Vecs<T>& V, bool x_nonzero, double tol, int max_iter,
+                     std::vector<int>& its, std::vector<int>& status, int64_t& matvecs) {
+  Workspace& w = t->ws;
+  const int64_t n = 3 * t->nbox;
+  const int nblk = reduce_blocks(n);
+  double* part = w.partials.as<double>();
+  KState* ks = w.ks.as<KState>();
+  int* act = w.active.as<int>();
+  cudaStream_t st = t->stream;
+  if (x_nonzero) {
+    CK(launch_matvec<T>(op, L, R, V.x, V.s, V.scr, nullptr, st));
+    matvecs += R;
+    CK(launch_bicg_init<T>(n, R, V.b, V.s, V.r, V.rh, V.p, V.v, part, st));
+  } else {
+    CK(launch_bicg_init<T>(n, R, V.b, nullptr, V.r, V.rh, V.p, V.v, part, st));
+  }
+  CK(launch_state_init(R, nblk, part, ks, act, tol, max_iter, st));
+  std::vector<int> hact(R);
+  CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int nact = 0;
+  for (int a : hact) nact += a;
+  int iter = 0;
+  while (nact > 0 && iter < max_iter) {
+    CK(launch_update_p<T>(n, R, V.r, V.p, V.v, ks, act, st));
+    CK(launch_matvec<T>(op, L, R, V.p, V.v, V.scr, act, st, t->prof.set(0)));
+    CK(launch_dot_rhat_v<T>(n, R, V.rh, V.v, part, act, st));
+    CK(launch_scalar_alpha(R, nblk, part, ks, act, st));
+    CK(launch_update_s<T>(n, R, V.r, V.v, V.s, ks, act, st));
+    CK(launch_matvec<T>(op, L, R, V.s, V.t, V.scr, act, st, t->prof.set(1)));
+    CK(launch_dot_ts<T>(n, R, V.t, V.s, part, act, st));
+    CK(launch_scalar_omega(R, nblk, part, ks, act, st));
+    CK(launch_update_xr<T>(n, R, V.x, V.r, V.p, V.s, V.t, V.rh, part, ks, act, st));
+    CK(launch_scalar_rho(R, nblk, part, ks, act, st));
+    matvecs += 2 * (int64_t)nact;
+    CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    t->prof.harvest(sizeof(T) == 4 ? 0 : 1, 0);
+    t->prof.harvest(sizeof(T) == 4 ? 0 : 1, 1);
+    nact = 0;
+    for (int a : hact) nact += a;
+    ++iter;
+  }
+  std::vector<KState> hks(R);
+  CK(cudaMemcpyAsync(hks.data(), ks, sizeof(KState) * R, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  its.resize(R);
+  status.resize(R);
+  for (int r = 0; r < R; ++r) {
+    its[r] = hks[r].iters;
+    status[r] = hks[r].status == KS_RUN ? KS_NOCONV : hks[r].status;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// workspace sizing
+// ---------------------------------------------------------------------------
+static int64_t workspace_bytes(const dda_target* t, int R, dda_precision prec, int ndir) {
+  const int64_t nv = 3 * t->nbox * (int64_t)R;
+  const int64_t ns = 3 * (int64_t)t->nz * t->Ly * t->Lx * R;
+  int64_t b = 0;
+  const bool f32 = prec != DDA_PREC_FP64;
+  // FP64: b, x, r (+ the 5 Krylov vectors and scratch if FP64 solve)
+  b += 3 * nv * 16;
+  if (!f32) b += 5 * nv * 16;
+  b += ns * 16;  // FP64 scratch (final/true residual matvec)
+  if (f32) b += 8 * nv * 8 + ns * 8;
+  const int nblk = reduce_blocks(3 * t->nbox);
+  b += (int64_t)std::max(4 * R, 6 * R * (ndir + 1)) * nblk * 8;
+  b += (int64_t)R * (sizeof(KState) + 64) + (int64_t)R * (t->nx + t->ny + t->nz + 8) * 16;
+  b += (int64_t)(ndir + 1) * (t->nx + t->ny + t->nz) * 16 + t->N * (int64_t)R * 48;
+  return b;
+}
+
+static void ensure_workspace(dda_target* t, int R, dda_precision prec, int ndir) {
+  Workspace& w = t->ws;
+  const int64_t nv = 3 * t->nbox * (int64_t)R;
+  const int64_t ns = 3 * (int64_t)t->nz * t->Ly * t->Lx * R;
+  const bool f32 = prec != DDA_PREC_FP64;
+  w.b64.ensure(nv * 16); w.x64.ensure(nv * 16); w.r64.ensure(nv * 16);
+  w.scr64.ensure(ns * 16);
+  if (!f32) {
+    w.rh64.ensure(nv * 16); w.p64.ensure(nv * 16); w.v64.ensure(nv * 16);
+    w.s64.ensure(nv * 16); w.t64.ensure(nv * 16);
+  } else {
+    w.x32.ensure(nv * 8); w.r32.ensure(nv * 8); w.rh32.ensure(nv * 8); w.p32.ensure(nv * 8);
+    w.v32.ensure(nv * 8); w.s32.ensure(nv * 8); w.t32.ensure(nv * 8); w.b32.ensure(nv * 8);
+    w.scr32.ensure(ns * 8);
+  }
+  const int nblk = reduce_blocks(3 * t->nbox);
+  w.partials.ensure((size_t)std::max(4 * R, 6 * R * (ndir + 1)) * nblk * 8);
+  w.ks.ensure(sizeof(KState) * R);
+  w.active.ensure(sizeof(int) * R);
+  w.active_outer.ensure(sizeof(int) * R);
+  w.norms.ensure(sizeof(double) * R);
+  w.sums.ensure(sizeof(double) * 6 * (size_t)std::max(R, R * (ndir + 1)));
+  w.pol.ensure(sizeof(double2) * 3 * R);
+  w.ph.ensure(sizeof(double2) * (size_t)R * (t->nx + t->ny + t->nz));
+  w.ainv64.ensure(sizeof(double2) * (size_t)R * (t->ncomp + 1));
+  w.ainv32.ensure(sizeof(float2) * (size_t)R * (t->ncomp + 1));
+  w.wabs.ensure(sizeof(double) * (size_t)R * (t->ncomp + 1));
+  w.fph.ensure(sizeof(double2) * (size_t)(ndir + 1) * (t->nx + t->ny + t->nz));
+  w.sitebuf.ensure(sizeof(double2) * 3 * (size_t)t->N * R);
+  w.R = R;
+}
+
+static void configure(dda_target* t) {
+  if (t->kernels_configured) return;
+  OpView<float> v32 = make_view<float>(t, t->g32.p, nullptr, t->tw32.p);
+  OpView<double> v64 = make_view<double>(t, t->g64.p, nullptr, t->tw64.p);
+  t->L32 = plan_matvec<float>(v32);
+  t->L64 = plan_matvec<double>(v64);
+  CK(configure_matvec_kernels<float>(t->L32));
+  CK(configure_matvec_kernels<double>(t->L64));
+  t->kernels_configured = true;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* dda_status_string(dda_status s) {
+  switch (s) {
+    case DDA_OK: return "ok";
+    case DDA_ERR_INVALID_ARG: return "invalid argument";
+    case DDA_ERR_OOM: return "out of device memory";
+    case DDA_ERR_CUDA: return "CUDA error";
+    case DDA_ERR_NOCONV: return "not converged";
+    case DDA_ERR_BREAKDOWN: return "BiCGSTAB breakdown";
+    case DDA_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* dda_last_error(void) { return g_last_error.c_str(); }
+
+int64_t dda_launch_count(void) { return (int64_t)launch_count(); }
+
+int64_t dda_target_num_dipoles(const dda_target* t) { return t ? t->N : -1; }
+
+dda_status dda_target_grid(const dda_target* t, int* Lx, int* Ly, int* Lz) {
+  if (!t || !Lx || !Ly || !Lz) return fail(DDA_ERR_INVALID_ARG, "null argument");
+  *Lx = t->Lx; *Ly = t->Ly; *Lz = t->Lz;
+  return DDA_OK;
+}
+
+void dda_target_destroy(dda_target* t) {
+  if (!t) return;
+  cudaSetDevice(t->device);
+  if (t->stream) cudaStreamSynchronize(t->stream);
+  t->ws.release_all();
+  t->comp.release(); t->site.release(); t->tw64.release(); t->tw32.release();
+  t->perm.release();
+  t->g64.release(); t->g32.release();
+  t->prof.destroy();
+  if (t->ev0) cudaEventDestroy(t->ev0);
+  if (t->ev1) cudaEventDestroy(t->ev1);
+  if (t->stream) cudaStreamDestroy(t->stream);
+  delete t;
+}
+
+dda_status dda_target_create(int nx, int ny, int nz, const uint8_t* occ, const uint8_t* comp,
+                             int ncomp, const double* m, dda_target** out) {
+  g_last_error.clear();
+  if (!out) return fail(DDA_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 1024 || ny > 1024 || nz > 1024)
+    return fail(DDA_ERR_INVALID_ARG, "box dimensions must be in 1..1024");
+  if (!occ) return fail(DDA_ERR_INVALID_ARG, "occ is NULL");
+  if (ncomp < 1 || ncomp > 255 || !m) return fail(DDA_ERR_INVALID_ARG, "ncomp must be 1..255 with m");
+  const int64_t nbox = (int64_t)nx * ny * nz;
+  std::vector<uint8_t> cgrid(nbox);
+  std::vector<int64_t> sites;
+  for (int64_t i = 0; i < nbox; ++i) {
+    if (occ[i]) {
+      const int c = comp ? comp[i] : 1;
+      if (c < 1 || c > ncomp) return fail(DDA_ERR_INVALID_ARG, "composition out of 1..ncomp");
+      cgrid[i] = (uint8_t)c;
+      sites.push_back(i);
+    } else {
+      cgrid[i] = 0;
+    }
+  }
+  if (sites.empty()) return fail(DDA_ERR_INVALID_ARG, "target has no occupied site");
+  for (int c = 0; c < 2 * ncomp; ++c)
+    if (!std::isfinite(m[c])) return fail(DDA_ERR_INVALID_ARG, "refractive index not finite");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(DDA_ERR_CUDA, "no CUDA device");
+  }
+  dda_target* t = new dda_target();
+  try {
+    CK(cudaGetDevice(&t->device));
+    t->nx = nx; t->ny = ny; t->nz = nz;
+    t->nbox = nbox;
+    t->N = (int64_t)sites.size();
+    t->ncomp = ncomp;
+    for (int c = 0; c < ncomp; ++c) t->m.push_back(cd(m[2 * c], m[2 * c + 1]));
+    t->Lx = smooth_at_least(2 * nx - 1);
+    t->Ly = smooth_at_least(2 * ny - 1);
+    t->Lz = smooth_at_least(2 * nz - 1);
+    CK(cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreate(&t->ev0));
+    CK(cudaEventCreate(&t->ev1));
+    t->comp.ensure(nbox);
+    CK(cudaMemcpy(t->comp.p, cgrid.data(), nbox, cudaMemcpyHostToDevice));
+    t->site.ensure(sizeof(int64_t) * sites.size());
+    CK(cudaMemcpy(t->site.p, sites.data(), sizeof(int64_t) * sites.size(),
+                  cudaMemcpyHostToDevice));
+    // plans and twiddles for the three axes, one table per precision
+    std::vector<double2> t64;
+    std::vector<float2> t32;
+    std::vector<int> kat;
+    const int Ls[3] = {t->Lx, t->Ly, t->Lz};
+    AxisPlan* ps[3] = {&t->px, &t->py, &t->pz};
+    std::vector<int> posall;
+    for (int a = 0; a < 3; ++a) {
+      std::vector<long double> wr, wi;
+      std::vector<int> ka;
+      *ps[a] = make_plan(Ls[a], wr, wi, ka);
+      std::vector<int> pa(Ls[a]);
+      for (int q = 0; q < Ls[a]; ++q) pa[ka[q]] = q;
+      kat.insert(kat.end(), ka.begin(), ka.end());
+      posall.insert(posall.end(), pa.begin(), pa.end());
+      t->twoff[a] = (int)t64.size();
+      for (size_t i = 0; i < wr.size(); ++i) {
+        t64.push_back(make_double2((double)wr[i], (double)wi[i]));
+        t32.push_back(make_float2((float)wr[i], (float)wi[i]));
+      }
+    }
+    if (t64.empty()) { t64.push_back(make_double2(1, 0)); t32.push_back(make_float2(1, 0)); }
+    t->tw64.ensure(sizeof(double2) * t64.size());
+    t->tw32.ensure(sizeof(float2) * t32.size());
+    CK(cudaMemcpy(t->tw64.p, t64.data(), sizeof(double2) * t64.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t->tw32.p, t32.data(), sizeof(float2) * t32.size(), cudaMemcpyHostToDevice));
+    kat.insert(kat.end(), posall.begin(), posall.end());
+    t->perm.ensure(sizeof(int) * kat.size());
+    CK(cudaMemcpy(t->perm.p, kat.data(), sizeof(int) * kat.size(), cudaMemcpyHostToDevice));
+  } catch (const CudaFail& f) {
+    dda_status s = from_cuda(f);
+    dda_target_destroy(t);
+    return s;
+  }
+  *out = t;
+  return DDA_OK;
+}
+
+dda_status dda_set_polarizability(dda_target* t, dda_pol_method method) {
+  if (!t) return fail(DDA_ERR_INVALID_ARG, "target is NULL");
+  if (method != DDA_POL_CM && method != DDA_POL_LDR && method != DDA_POL_FCD)
+    return fail(DDA_ERR_INVALID_ARG, "unknown polarizability method");
+  t->method = method;
+  return DDA_OK;
+}
+
+int64_t dda_solve_hbm_bytes(const dda_target* t, const dda_solve_params* p) {
+  if (!t || !p || p->n_inc < 1 || (p->npol != 1 && p->npol != 2) || p->n_dirs < 0) return -1;
+  const int R = p->n_inc * p->npol;
+  int64_t b = workspace_bytes(t, R, p->precision, p->n_dirs);
+  const int filtered = t->method == DDA_POL_FCD ? 1 : 0;
+  if (!(t->have_green && t->green_kd == p->kd && t->green_filtered == filtered)) {
+    const int64_t M = (int64_t)t->Lx * t->Ly * t->Lz;
+    b += 2 * 6 * M * 16;  // transient setup grids
+  }
+  return b;
+}
+
+static dda_status check_kd(const dda_target* t, double kd) {
+  if (!(kd > 0.0) || !std::isfinite(kd)) return fail(DDA_ERR_INVALID_ARG, "kd must be > 0");
+  if (t->method == DDA_POL_FCD && !(kd < 3.14159265358979323846))
+    return fail(DDA_ERR_INVALID_ARG, "FCD needs kd < pi");
+  return DDA_OK;
+}
+
+dda_status dda_matvec(dda_target* t, double kd, const double* khat, const double* e,
+                      const double* x, double* y, dda_precision precision) {
+  g_last_error.clear();
+  if (!t || !x || !y) return fail(DDA_ERR_INVALID_ARG, "null argument");
+  dda_status s = check_kd(t, kd);
+  if (s != DDA_OK) return s;
+  double kh[3] = {1, 0, 0};
+  cd ev[3] = {0.0, 1.0, 0.0};
+  if (t->method == DDA_POL_LDR) {
+    if (!khat || !e) return fail(DDA_ERR_INVALID_ARG, "LDR needs khat and e");
+    double kn = std::sqrt(khat[0] * khat[0] + khat[1] * khat[1] + khat[2] * khat[2]);
+    if (!(kn > 0)) return fail(DDA_ERR_INVALID_ARG, "khat is zero");
+    for (int c = 0; c < 3; ++c) { kh[c] = khat[c] / kn; ev[c] = cd(e[2 * c], e[2 * c + 1]); }
+  }
+  try {
+    CK(cudaSetDevice(t->device));
+    const int filtered = t->method == DDA_POL_FCD ? 1 : 0;
+    build_green(t, kd, filtered);
+    const bool f32 = precision != DDA_PREC_FP64;
+    ensure_workspace(t, 1, f32 ? DDA_PREC_FP32 : DDA_PREC_FP64, 0);
+    configure(t);
+    Workspace& w = t->ws;
+    std::vector<double2> ai(t->ncomp + 1, make_double2(0, 0));
+    std::vector<float2> ai32(t->ncomp + 1, make_float2(0, 0));
+    for (int c = 1; c <= t->ncomp; ++c) {
+      cd a = 1.0 / alpha_of(t->method, t->m[c - 1], kd, kh, ev);
+      ai[c] = make_double2(a.real(), a.imag());
+      ai32[c] = make_float2((float)a.real(), (float)a.imag());
+    }
+    cudaStream_t st = t->stream;
+    CK(cudaMemcpyAsync(w.ainv64.p, ai.data(), sizeof(double2) * ai.size(),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w.ainv32.p, ai32.data(), sizeof(float2) * ai32.size(),
+                       cudaMemcpyHostToDevice, st));
+    const int64_t N = t->N, nbox = t->nbox;
+    CK(cudaMemcpyAsync(w.sitebuf.p, x, sizeof(double2) * 3 * N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(w.x64.p, 0, sizeof(double2) * 3 * nbox, st));
+    CK(launch_sites_to_box(N, nbox, 1, t->site.as<int64_t>(), w.sitebuf.as<double2>(),
+                           w.x64.as<double2>(), st));
+    if (!f32) {
+      OpView<double> op = make_view<double>(t, t->g64.p, w.ainv64.p, t->tw64.p);
+      CK(launch_matvec<double>(op, t->L64, 1, w.x64.as<double2>(), w.r64.as<double2>(),
+                               w.scr64.as<double2>(), nullptr, st));
+    } else {
+      OpView<float> op = make_view<float>(t, t->g32.p, w.ainv32.p, t->tw32.p);
+      CK(launch_f64_to_f32(3 * nbox, w.x64.as<double2>(), w.x32.as<float2>(), st));
+      CK(launch_matvec<float>(op, t->L32, 1, w.x32.as<float2>(), w.r32.as<float2>(),
+                              w.scr32.as<float2>(), nullptr, st));
+      CK(launch_f32_to_f64(3 * nbox, w.r32.as<float2>(), w.r64.as<double2>(), st));
+    }
+    CK(launch_box_to_sites(N, nbox, 1, t->site.as<int64_t>(), w.r64.as<double2>(),
+                           w.sitebuf.as<double2>(), st));
+    CK(cudaMemcpyAsync(y, w.sitebuf.p, sizeof(double2) * 3 * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  } catch (const CudaFail& f) {
+    return from_cuda(f);
+  }
+  return DDA_OK;
+}
+
+dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result* res) {
+  g_last_error.clear();
+  if (!t || !p || !res) return fail(DDA_ERR_INVALID_ARG, "null argument");
+  dda_status s = check_kd(t, p->kd);
+  if (s != DDA_OK) return s;
+  if (p->n_inc < 1 || !p->khat || !p->e01) return fail(DDA_ERR_INVALID_ARG, "need n_inc >= 1, khat, e01");
+  if (p->npol != 1 && p->npol != 2) return fail(DDA_ERR_INVALID_ARG, "npol must be 1 or 2");
+  if (!(p->tol > 0.0) || p->max_iter < 1) return fail(DDA_ERR_INVALID_ARG, "tol > 0 and max_iter >= 1");
+  if (p->n_dirs < 0 || (p->n_dirs > 0 && !p->dirs)) return fail(DDA_ERR_INVALID_ARG, "bad dirs");
+  if (p->precision != DDA_PREC_FP64 && p->precision != DDA_PREC_FP32 &&
+      p->precision != DDA_PREC_FP32_REFINED)
+    return fail(DDA_ERR_INVALID_ARG, "unknown precision");
+  const int R = p->n_inc * p->npol;
+  if (R > 4096) return fail(DDA_ERR_INVALID_ARG, "at most 4096 right-hand sides");
+  std::vector<Incidence> incs(p->n_inc);
+  for (int i = 0; i < p->n_inc; ++i) {
+    s = make_incidence(p, i, incs[i]);
+    if (s != DDA_OK) return s;
+  }
+  const double kd = p->kd;
+  const int64_t N = t->N, nbox = t->nbox;
+  const int64_t n = 3 * nbox;
+  const int D = p->n_dirs + 1;
+  dda_status result_status = DDA_OK;
+  try {
+    CK(cudaSetDevice(t->device));
+    cudaStream_t st = t->stream;
+    const int filtered = t->method == DDA_POL_FCD ? 1 : 0;
+    CK(cudaEventRecord(t->ev0, st));
+    build_green(t, kd, filtered);
+    CK(cudaEventRecord(t->ev1, st));
+    CK(cudaEventSynchronize(t->ev1));
+    float setup_ms = 0.f;
+    CK(cudaEventElapsedTime(&setup_ms, t->ev0, t->ev1));
+    ensure_workspace(t, R, p->precision, p->n_dirs);
+    configure(t);
+    Workspace& w = t->ws;
+    const long long launches0 = launch_count();
+    t->prof.on = p->profile != 0;
+    if (t->prof.on) t->prof.create();
+    t->prof.reset();
+    CK(cudaEventRecord(t->ev0, st));
+    // ---- per-RHS tables ----
+    const int nc1 = t->ncomp + 1;
+    std::vector<double2> pol(3 * R), ph, ai(R * nc1), fph;
+    std::vector<float2> ai32(R * nc1);
+    std::vector<double> wabs(R * nc1, 0.0);
+    const double k3 = kd * kd * kd;
+    for (int i = 0; i < p->n_inc; ++i)
+      for (int l = 0; l < p->npol; ++l) {
+        const int r = i * p->npol + l;
+        for (int c = 0; c < 3; ++c)
+          pol[3 * r + c] = make_double2(incs[i].e[l][c].real(), incs[i].e[l][c].imag());
+        ai[r * nc1] = make_double2(0, 0);
+        ai32[r * nc1] = make_float2(0, 0);
+        for (int c = 1; c < nc1; ++c) {
+          const cd a = 1.0 / alpha_of(t->method, t->m[c - 1], kd, incs[i].khat, incs[i].e[l]);
+          ai[r * nc1 + c] = make_double2(a.real(), a.imag());
+          ai32[r * nc1 + c] = make_float2((float)a.real(), (float)a.imag());
+          wabs[r * nc1 + c] = -a.imag() - (2.0 / 3.0) * k3;
+        }
+      }
+    // phases: all x tables, then y, then z
+    for (int r = 0; r < R; ++r) axis_phase(t->nx, kd, incs[r / p->npol].khat[0], 1.0, ph);
+    for (int r = 0; r < R; ++r) axis_phase(t->ny, kd, incs[r / p->npol].khat[1], 1.0, ph);
+    for (int r = 0; r < R; ++r) axis_phase(t->nz, kd, incs[r / p->npol].khat[2], 1.0, ph);
+    CK(cudaMemcpyAsync(w.pol.p, pol.data(), sizeof(double2) * pol.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w.ph.p, ph.data(), sizeof(double2) * ph.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w.ainv64.p, ai.data(), sizeof(double2) * ai.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w.ainv32.p, ai32.data(), sizeof(float2) * ai32.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w.wabs.p, wabs.data(), sizeof(double) * wabs.size(), cudaMemcpyHostToDevice, st));
+    RhsTables tb;
+    tb.pol = w.pol.as<double2>();
+    tb.phx = w.ph.as<double2>();
+    tb.phy = tb.phx + (size_t)R * t->nx;
+    tb.phz = tb.phy + (size_t)R * t->ny;
+    // ---- b = E_inc, x = P0 or 0 ----
+    CK(launch_einc<double>(t->nx, t->ny, t->nz, t->comp.as<uint8_t>(), tb, R,
+                           w.b64.as<double2>(), st));
+    bool x_nonzero = false;
+    CK(cudaMemsetAsync(w.x64.p, 0, sizeof(double2) * n * R, st));
+    if (p->P0) {
+      CK(cudaMemcpyAsync(w.sitebuf.p, p->P0, sizeof(double2) * 3 * N * R, cudaMemcpyHostToDevice, st));
+      CK(launch_sites_to_box(N, nbox, R, t->site.as<int64_t>(), w.sitebuf.as<double2>(),
+                             w.x64.as<double2>(), st));
+      x_nonzero = true;
+    }
+    OpView<double> op64 = make_view<double>(t, t->g64.p, w.ainv64.p, t->tw64.p);
+    OpView<float> op32 = make_view<float>(t, t->g32.p, w.ainv32.p, t->tw32.p);
+    std::vector<int> its_total(R, 0), sweeps(R, 0), status(R, KS_RUN);
+    int64_t matvecs = 0, matvecs64 = 0;
+    const int nblk = reduce_blocks(n);
+    double* part = w.partials.as<double>();
+    std::vector<double> bn2(R), rn2(R);
+    // ||b||^2 per RHS
+    CK(launch_norm2(n, R, w.b64.as<double2>(), part, st));
+    CK(launch_finalize_sums(R, nblk, 1, part, w.sums.as<double>(), st));
+    CK(cudaMemcpyAsync(bn2.data(), w.sums.p, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+
+    if (p->precision == DDA_PREC_FP64) {
+      Vecs<double> V{w.b64.as<double2>(), w.x64.as<double2>(), w.r64.as<double2>(),
+                     w.rh64.as<double2>(), w.p64.as<double2>(), w.v64.as<double2>(),
+                     w.s64.as<double2>(), w.t64.as<double2>(), w.scr64.as<double2>()};
+      std::vector<int> its;
+      bicgstab<double>(t, op64, t->L64, R, V, x_nonzero, p->tol, p->max_iter, its, status,
+                       matvecs);
+      matvecs64 = matvecs;
+      for (int r = 0; r < R; ++r) { its_total[r] = its[r]; sweeps[r] = 1; }
+    } else if (p->precision == DDA_PREC_FP32) {
+      Vecs<float> V{w.b32.as<float2>(), w.x32.as<float2>(), w.r32.as<float2>(),
+                    w.rh32.as<float2>(), w.p32.as<float2>(), w.v32.as<float2>(),
+                    w.s32.as<float2>(), w.t32.as<float2>(), w.scr32.as<float2>()};
+      CK(launch_f64_to_f32(n * R, w.b64.as<double2>(), V.b, st));
+      CK(launch_f64_to_f32(n * R, w.x64.as<double2>(), V.x, st));
+      std::vector<int> its;
+      bicgstab<float>(t, op32, t->L32, R, V, x_nonzero, p->tol, p->max_iter, its, status,
+                      matvecs);
+      CK(launch_f32_to_f64(n * R, V.x, w.x64.as<double2>(), st));
+      for (int r = 0; r < R; ++r) { its_total[r] = its[r]; sweeps[r] = 1; }
+    } else {
+      // FP64 iterative refinement around FP32 BiCGSTAB
+      const double inner_tol = p->inner_tol > 0 ? p->inner_tol : 1e-4;
+      Vecs<float> V{w.b32.as<float2>(), w.x32.as<float2>(), w.r32.as<float2>(),
+                    w.rh32.as<float2>(), w.p32.as<float2>(), w.v32.as<float2>(),
+                    w.s32.as<float2>(), w.t32.as<float2>(), w.scr32.as<float2>()};
+      std::vector<int> outer_act(R, 1);
+      std::vector<double> prev(R, 0.0);
+      bool first = true;
+      for (int sweep = 0; sweep < 30; ++sweep) {
+        // r = b - A x (FP64); skipped when x = 0
+        if (first && !x_nonzero) {
+          CK(cudaMemcpyAsync(w.r64.p, w.b64.p, sizeof(double2) * n * R, cudaMemcpyDeviceToDevice, st));
+        } else {
+          CK(launch_matvec<double>(op64, t->L64, R, w.x64.as<double2>(), w.r64.as<double2>(),
+                                   w.scr64.as<double2>(), nullptr, st, t->prof.set(2)));
+          matvecs += R; matvecs64 += R;
+          CK(launch_residual(n, R, w.b64.as<double2>(), w.r64.as<double2>(),
+                             w.r64.as<double2>(), st));
+        }
+        first = false;
+        CK(launch_norm2(n, R, w.r64.as<double2>(), part, st));
+        CK(launch_finalize_sums(R, nblk, 1, part, w.norms.as<double>(), st));
+        CK(cudaMemcpyAsync(rn2.data(), w.norms.p, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (!(sweep == 0 && !x_nonzero)) t->prof.harvest(1, 2);
+        int nact = 0;
+        for (int r = 0; r < R; ++r) {
+          if (!outer_act[r]) continue;
+          if (rn2[r] <= p->tol * p->tol * bn2[r]) { outer_act[r] = 0; status[r] = KS_CONV; continue; }
+          if (!std::isfinite(rn2[r])) { outer_act[r] = 0; status[r] = KS_BREAKDOWN; continue; }
+          if (its_total[r] >= p->max_iter || (sweep > 0 && rn2[r] > 0.25 * prev[r])) {
+            // out of iterations, or the last sweep stagnated
+            outer_act[r] = 0;
+            status[r] = KS_NOCONV;
+            continue;
+          }
+          prev[r] = rn2[r];
+          ++nact;
+        }
+        if (nact == 0) break;
+        CK(cudaMemcpyAsync(w.active_outer.p, outer_act.data(), sizeof(int) * R,
+                           cudaMemcpyHostToDevice, st));
+        // inner: A d = r / ||r|| in FP32 (converged RHS get a zero right-hand side)
+        CK(launch_scale_to_f32(n, R, w.r64.as<double2>(), w.norms.as<double>(), V.b,
+                               w.active_outer.as<int>(), st));
+        CK(cudaMemsetAsync(V.x, 0, sizeof(float2) * n * R, st));
+        std::vector<int> its, st_in;
+        int cap = 0;
+        for (int r = 0; r < R; ++r)
+          if (outer_act[r]) cap = std::max(cap, p->max_iter - its_total[r]);
+        bicgstab<float>(t, op32, t->L32, R, V, false, inner_tol, std::max(1, cap), its, st_in,
+                        matvecs);
+        for (int r = 0; r < R; ++r) {
+          if (!outer_act[r]) continue;
+          its_total[r] += its[r];
+          sweeps[r] += 1;
+          status[r] = st_in[r] == KS_BREAKDOWN ? KS_BREAKDOWN : KS_RUN;
+          if (st_in[r] == KS_BREAKDOWN && its[r] == 0) outer_act[r] = 0;
+        }
+        CK(launch_accumulate(n, R, w.x64.as<double2>(), V.x, w.norms.as<double>(),
+                             w.active_outer.as<int>(), st));
+      }
+      for (int r = 0; r < R; ++r)
+        if (status[r] == KS_RUN) status[r] = KS_NOCONV;
+    }
+
+    // ---- true residual (FP64) of the result ----
+    CK(launch_matvec<double>(op64, t->L64, R, w.x64.as<double2>(), w.r64.as<double2>(),
+                             w.scr64.as<double2>(), nullptr, st, t->prof.set(2)));
+    matvecs += R; matvecs64 += R;
+    CK(launch_residual(n, R, w.b64.as<double2>(), w.r64.as<double2>(), w.r64.as<double2>(), st));
+    CK(launch_norm2(n, R, w.r64.as<double2>(), part, st));
+    CK(launch_finalize_sums(R, nblk, 1, part, w.norms.as<double>(), st));
+    CK(cudaMemcpyAsync(rn2.data(), w.norms.p, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+
+    // ---- observables ----
+    CK(launch_cross_sections(t->nx, t->ny, t->nz, t->comp.as<uint8_t>(), tb, R,
+                             w.x64.as<double2>(), w.wabs.as<double>(), nc1, part, nblk, st));
+    std::vector<double> qs(2 * R);
+    CK(launch_finalize_sums(R, nblk, 2, part, w.sums.as<double>(), st));
+    CK(cudaMemcpyAsync(qs.data(), w.sums.p, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    t->prof.harvest(1, 2);
+    std::vector<double> ff;
+    if (res->famp) {
+      ff.resize((size_t)p->n_inc * D * p->npol * 6);
+      const int fblk = std::min(reduce_blocks(nbox), 304);
+      for (int i = 0; i < p->n_inc; ++i) {
+        fph.clear();
+        std::vector<double2> fx, fy, fz;
+        const double* x = incs[i].khat;
+        const double* y = incs[i].yhat;
+        const double zz[3] = {x[1] * y[2] - x[2] * y[1], x[2] * y[0] - x[0] * y[2],
+                              x[0] * y[1] - x[1] * y[0]};
+        for (int d = 0; d < D; ++d) {
+          const double th = d == 0 ? 0.0 : p->dirs[2 * (d - 1)];
+          const double phi = d == 0 ? 0.0 : p->dirs[2 * (d - 1) + 1];
+          double nv[3];
+          for (int c = 0; c < 3; ++c)
+            nv[c] = x[c] * std::cos(th) + y[c] * std::sin(th) * std::cos(phi) +
+                    zz[c] * std::sin(th) * std::sin(phi);
+          axis_phase(t->nx, kd, nv[0], -1.0, fx);
+          axis_phase(t->ny, kd, nv[1], -1.0, fy);
+          axis_phase(t->nz, kd, nv[2], -1.0, fz);
+        }
+        fph.insert(fph.end(), fx.begin(), fx.end());
+        fph.insert(fph.end(), fy.begin(), fy.end());
+        fph.insert(fph.end(), fz.begin(), fz.end());
+        CK(cudaMemcpyAsync(w.fph.p, fph.data(), sizeof(double2) * fph.size(),
+                           cudaMemcpyHostToDevice, st));
+        const double2* dfx = w.fph.as<double2>();
+        const double2* dfy = dfx + (size_t)D * t->nx;
+        const double2* dfz = dfy + (size_t)D * t->ny;
+        const double2* Pi = w.x64.as<double2>() + (size_t)i * p->npol * n;
+        CK(launch_farfield(t->nx, t->ny, t->nz, t->comp.as<uint8_t>(), p->npol, D, Pi, dfx,
+                           dfy, dfz, part, fblk, st));
+        CK(launch_finalize_sums(p->npol * D, fblk, 6, part, w.sums.as<double>(), st));
+        CK(cudaMemcpyAsync(ff.data() + (size_t)i * D * p->npol * 6, w.sums.p,
+                           sizeof(double) * D * p->npol * 6, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+      }
+    }
+    if (res->P) {
+      CK(launch_box_to_sites(N, nbox, R, t->site.as<int64_t>(), w.x64.as<double2>(),
+                             w.sitebuf.as<double2>(), st));
+      CK(cudaMemcpyAsync(res->P, w.sitebuf.p, sizeof(double2) * 3 * N * R,
+                         cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaEventRecord(t->ev1, st));
+    CK(cudaEventSynchronize(t->ev1));
+    float solve_ms = 0.f;
+    CK(cudaEventElapsedTime(&solve_ms, t->ev0, t->ev1));
+
+    // ---- outputs ----
+    const double pi = 3.14159265358979323846;
+    const double aeff = std::cbrt(3.0 * (double)N / (4.0 * pi));
+    const double geo = pi * aeff * aeff;
+    for (int r = 0; r < R; ++r) {
+      const double qe = 4.0 * pi * kd * qs[2 * r] / geo;
+      const double qa = 4.0 * pi * kd * qs[2 * r + 1] / geo;
+      if (res->Qext) res->Qext[r] = qe;
+      if (res->Qabs) res->Qabs[r] = qa;
+      if (res->Qsca) res->Qsca[r] = qe - qa;
+      if (res->iters) res->iters[r] = its_total[r];
+      if (res->sweeps) res->sweeps[r] = sweeps[r];
+      if (res->resid) res->resid[r] = bn2[r] > 0 ? std::sqrt(rn2[r] / bn2[r]) : 0.0;
+    }
+    if (res->famp) {
+      // sums layout per incidence: [(d*npol + l)][6] -> famp[i][d][m][l][2]
+      for (int i = 0; i < p->n_inc; ++i) {
+        const double* x = incs[i].khat;
+        const double* y = incs[i].yhat;
+        const double zz[3] = {x[1] * y[2] - x[2] * y[1], x[2] * y[0] - x[0] * y[2],
+                              x[0] * y[1] - x[1] * y[0]};
+        for (int d = 0; d < D; ++d) {
+          const double th = d == 0 ? 0.0 : p->dirs[2 * (d - 1)];
+          const double phi = d == 0 ? 0.0 : p->dirs[2 * (d - 1) + 1];
+          double eth[3], eph[3];
+          for (int c = 0; c < 3; ++c) {
+            eth[c] = -x[c] * std::sin(th) + y[c] * std::cos(th) * std::cos(phi) +
+                     zz[c] * std::cos(th) * std::sin(phi);
+            eph[c] = -y[c] * std::sin(phi) + zz[c] * std::cos(phi);
+          }
+          for (int l = 0; l < p->npol; ++l) {
+            const double* F = ff.data() + ((size_t)i * D * p->npol + (size_t)d * p->npol + l) * 6;
+            for (int mm = 0; mm < 2; ++mm) {
+              const double* e = mm == 0 ? eth : eph;
+              double re = 0, im = 0;
+              for (int c = 0; c < 3; ++c) { re += e[c] * F[2 * c]; im += e[c] * F[2 * c + 1]; }
+              double* o = res->famp + ((((size_t)i * D + d) * 2 + mm) * p->npol + l) * 2;
+              o[0] = k3 * re;
+              o[1] = k3 * im;
+            }
+          }
+        }
+      }
+    }
+    res->t_setup_ms = setup_ms;
+    res->t_solve_ms = solve_ms;
+    for (int pp = 0; pp < 2; ++pp)
+      for (int i = 0; i < kMatvecPasses; ++i) {
+        res->kernel_ms[pp * kMatvecPasses + i] = t->prof.ms[pp][i];
+        res->kernel_calls[pp * kMatvecPasses + i] = t->prof.calls[pp][i];
+      }
+    res->launches = launch_count() - launches0;
+    t->prof.on = false;
+    res->matvecs = matvecs;
+    res->matvecs_fp64 = matvecs64;
+    for (int r = 0; r < R; ++r) {
+      if (status[r] == KS_BREAKDOWN) result_status = DDA_ERR_BREAKDOWN;
+      else if (status[r] != KS_CONV && result_status == DDA_OK) result_status = DDA_ERR_NOCONV;
+    }
+    if (result_status == DDA_ERR_BREAKDOWN) g_last_error = "BiCGSTAB breakdown on some RHS";
+    if (result_status == DDA_ERR_NOCONV) g_last_error = "some RHS did not reach tol";
+  } catch (const CudaFail& f) {
+    return from_cuda(f);
+  }
+  return result_status;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Host-side launchers of the device kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dda_common.cuh"
+
+namespace dda {
+
+// Count one kernel launch of this library (process-wide, for reporting).
+void note_launch();
+long long launch_count();
+
+struct MatvecLaunch {
+  int x_lines, x_threads; size_t x_smem;
+  int y_tile, y_threads; size_t y_smem;
+  int z_tile, z_threads; size_t z_smem;
+};
+
+template <typename T> MatvecLaunch plan_matvec(const OpView<T>& op);
+template <typename T> cudaError_t configure_matvec_kernels(const MatvecLaunch& L);
+// y = A x for R right-hand sides (box layout); scratch holds R*3*nz*Ly*Lx.
+// With ev (6 events), the five passes are bracketed by events for profiling.
+constexpr int kMatvecPasses = 5;
+template <typename T>
+cudaError_t launch_matvec(const OpView<T>& op, const MatvecLaunch& L, int R,
+                          const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch,
+                          const int* active, cudaStream_t st,
+                          const cudaEvent_t* ev = nullptr);
+
+// x pass forward only (box rows -> spectral rows), used by the setup transforms.
+template <typename T>
+cudaError_t launch_x_fwd(const OpView<T>& op, const MatvecLaunch& L, int R,
+                         const cplx_t<T>* x, cplx_t<T>* out, cudaStream_t st);
+
+// ---- Green tensor ----------------------------------------------------------
+// Fill the 6 components of G on the full FFT grid (FP64), parity-mirrored.
+cudaError_t launch_green_fill(int nx, int ny, int nz, int Lx, int Ly, int Lz, double kd,
+                              int filtered, double2* grid6, cudaStream_t st);
+// Forward 3-D FFT of `count` full grids in place (FP64, unpruned).
+cudaError_t launch_fft3d_full(const OpView<double>& op, const MatvecLaunch& L, int count,
+                              double2* grids, double2* tmp, cudaStream_t st);
+// Copy the octant of the transformed grids (frequency k of an axis sits at
+// position pos[k]), scaled by 1/(Lx Ly Lz), to FP64 and FP32.
+cudaError_t launch_green_octant(int Lx, int Ly, int Lz, const int* posx, const int* posy,
+                                const int* posz, const double2* grid6, double2* g64,
+                                float2* g32, cudaStream_t st);
+
+// ---- Krylov / vector kernels -----------------------------------------------
+struct KState {
+  double2 rho, rho_old, alpha, omega, beta;
+  double bnorm2, rnorm2, tol2;
+  int active_unused;
+  int iters, status, max_iter;
+};
+
+enum { KS_RUN = 0, KS_CONV = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3 };
+
+struct RhsTables {            // per-RHS incident-wave data (device)
+  const double2* pol;         // [R][3] polarization vector
+  const double2* phx;         // [R][nx] exp(i k khat_x x)
+  const double2* phy;         // [R][ny]
+  const double2* phz;         // [R][nz]
+};
+
+// b = E_inc on occupied sites (box layout), in precision T.
+template <typename T>
+cudaError_t launch_einc(int nx, int ny, int nz, const uint8_t* comp, RhsTables tb, int R,
+                        cplx_t<T>* b, cudaStream_t st);
+
+int reduce_blocks(int64_t n);
+
+// BiCGSTAB building blocks (all R RHS per launch; inactive RHS are skipped).
+template <typename T>
+cudaError_t launch_bicg_init(int64_t n, int R, const cplx_t<T>* b, const cplx_t<T>* ax,
+                             cplx_t<T>* r, cplx_t<T>* rhat, cplx_t<T>* p, cplx_t<T>* v,
+                             double* partials, cudaStream_t st);
+cudaError_t launch_state_init(int R, int nblk, const double* partials, KState* ks,
+                              int* active, double tol, int max_iter, cudaStream_t st);
+template <typename T>
+cudaError_t launch_update_p(int64_t n, int R, const cplx_t<T>* r, cplx_t<T>* p,
+                            const cplx_t<T>* v, const KState* ks, const int* active,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t launch_dot_rhat_v(int64_t n, int R, const cplx_t<T>* rhat, const cplx_t<T>* v,
+                              double* partials, const int* active, cudaStream_t st);
+cudaError_t launch_scalar_alpha(int R, int nblk, const double* partials, KState* ks,
+                                int* active, cudaStream_t st);
+template <typename T>
+cudaError_t launch_update_s(int64_t n, int R, const cplx_t<T>* r, const cplx_t<T>* v,
+                            cplx_t<T>* s, const KState* ks, const int* active,
+                            cudaStream_t st);
+template <typename T>
+cudaError_t launch_dot_ts(int64_t n, int R, const cplx_t<T>* t, const cplx_t<T>* s,
+                          double* partials, const int* active, cudaStream_t st);
+cudaError_t launch_scalar_omega(int R, int nblk, const double* partials, KState* ks,
+                                int* active, cudaStream_t st);
+template <typename T>
+cudaError_t launch_update_xr(int64_t n, int R, cplx_t<T>* x, cplx_t<T>* r,
+                             const cplx_t<T>* p, const cplx_t<T>* s, const cplx_t<T>* t,
+                             const cplx_t<T>* rhat, double* partials, const KState* ks,
+                             const int* active, cudaStream_t st);
+cudaError_t launch_scalar_rho(int R, int nblk, const double* partials, KState* ks,
+                              int* active, cudaStream_t st);
+
+// ---- refinement helpers -----------------------------------------------------
+// partials of ||v||^2 per RHS (FP64 vector)
+cudaError_t launch_norm2(int64_t n, int R, const double2* v, double* partials,
+                         cudaStream_t st);
+// out[r] = sum of partials (fixed order)
+cudaError_t launch_finalize_sums(int R, int nblk, int nval, const double* partials,
+                                 double* out, cudaStream_t st);
+// r = b - ax (FP64)
+cudaError_t launch_residual(int64_t n, int R, const double2* b, const double2* ax,
+                            double2* r, cudaStream_t st);
+// r32 = r64 * scale[r]  (scale = 1/||r|| per RHS)
+cudaError_t launch_scale_to_f32(int64_t n, int R, const double2* r64, const double* norms,
+                                float2* r32, const int* active, cudaStream_t st);
+// x64 += d32 * norm[r]
+cudaError_t launch_accumulate(int64_t n, int R, double2* x64, const float2* d32,
+                              const double* norms, const int* active, cudaStream_t st);
+// precision casts
+cudaError_t launch_f64_to_f32(int64_t n, const double2* a, float2* b, cudaStream_t st);
+cudaError_t launch_f32_to_f64(int64_t n, const float2* a, double2* b, cudaStream_t st);
+
+// ---- site gather / scatter (box layout <-> site list) ------------------------
+cudaError_t launch_sites_to_box(int64_t N, int64_t nbox, int R, const int64_t* site,
+                                const double2* v, double2* box, cudaStream_t st);
+cudaError_t launch_box_to_sites(int64_t N, int64_t nbox, int R, const int64_t* site,
+                                const double2* box, double2* v, cudaStream_t st);
+
+// ---- observables --------------------------------------------------------------
+// partial sums per RHS: [Im(E^*.P), |P|^2 * w(comp)] (w per RHS per comp),
+// written as [R][nblk][2]
+cudaError_t launch_cross_sections(int nx, int ny, int nz, const uint8_t* comp, RhsTables tb,
+                                  int R, const double2* P, const double* wabs, int ncomp1,
+                                  double* partials, int nblk, cudaStream_t st);
+// far-field sums F[d][r][3] = sum_j P_j exp(-i k n_d . r_j), partials per block
+cudaError_t launch_farfield(int nx, int ny, int nz, const uint8_t* comp, int R, int D,
+                            const double2* P, const double2* fphx, const double2* fphy,
+                            const double2* fphz, double* partials, int nblk,
+                            cudaStream_t st);
+
+}  // namespace dda

@@ -1,0 +1,534 @@
+// BiCGSTAB (van der Vorst 1992; the PIM method the guide's PBCGST option runs,
+// Sec. "Choice of Iterative Algorithm") for R right-hand sides at once, plus
+// the vector kernels of the FP64-refined FP32 solve.
+//
+// Every kernel covers all R right-hand sides (grid.y = rhs) and skips the ones
+// whose `active` flag is 0, so a converged RHS is frozen while the others go
+// on.  Inner products and norms are accumulated in FP64 whatever the vector
+// precision, with a deterministic two-stage reduction: each block writes one
+// partial per value, and a single block per RHS adds the partials in a fixed
+// tree order inside the scalar kernels, so repeated runs are bit-identical.
+#include "dda_ops.h"
+#include "reduce.cuh"
+
+namespace dda {
+
+int reduce_blocks(int64_t n) {
+  int64_t b = (n + 4 * kThreads - 1) / (4 * kThreads);
+  if (b > 1216) b = 1216;  // 8 per SM on 152 SMs
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+__device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+template <typename C> __device__ __forceinline__ C from_d2(double2 a) {
+  return mk<C>(a.x, a.y);
+}
+
+
+// ---- incident field ------------------------------------------------------------
+template <typename T>
+__global__ void k_einc(int nx, int ny, int nz, const uint8_t* __restrict__ comp,
+                       RhsTables tb, cplx_t<T>* __restrict__ b) {
+  using C = cplx_t<T>;
+  const int r = blockIdx.y;
+  const int64_t nbox = (int64_t)nx * ny * nz;
+  GRID_LOOP(i, nbox) {
+    const int ix = (int)(i % nx);
+    const int64_t q = i / nx;
+    const int iy = (int)(q % ny), iz = (int)(q / ny);
+    double2 ph = make_double2(0.0, 0.0);
+    if (comp[i]) ph = cmul(cmul(tb.phx[(int64_t)r * nx + ix], tb.phy[(int64_t)r * ny + iy]),
+                           tb.phz[(int64_t)r * nz + iz]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 e = tb.pol[r * 3 + c];
+      b[((int64_t)r * 3 + c) * nbox + i] = from_d2<C>(cmul(e, ph));
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_einc(int nx, int ny, int nz, const uint8_t* comp, RhsTables tb, int R,
+                        cplx_t<T>* b, cudaStream_t st) {
+  const int64_t nbox = (int64_t)nx * ny * nz;
+  dim3 g(reduce_blocks(nbox), R);
+  k_einc<T><<<g, kThreads, 0, st>>>(nx, ny, nz, comp, tb, b);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ---- BiCGSTAB -------------------------------------------------------------------
+template <typename T>
+__global__ void k_bicg_init(int64_t n, const cplx_t<T>* __restrict__ b,
+                            const cplx_t<T>* __restrict__ ax, cplx_t<T>* __restrict__ r,
+                            cplx_t<T>* __restrict__ rhat, cplx_t<T>* __restrict__ p,
+                            cplx_t<T>* __restrict__ v, double* partials) {
+  using C = cplx_t<T>;
+  const int64_t off = (int64_t)blockIdx.y * n;
+  double acc[2] = {0.0, 0.0};
+  GRID_LOOP(i, n) {
+    const C bi = b[off + i];
+    C ri = bi;
+    if (ax) ri = csub(bi, ax[off + i]);
+    r[off + i] = ri;
+    rhat[off + i] = ri;
+    p[off + i] = mk<C>(0, 0);
+    v[off + i] = mk<C>(0, 0);
+    acc[0] += (double)ri.x * ri.x + (double)ri.y * ri.y;
+    acc[1] += (double)bi.x * bi.x + (double)bi.y * bi.y;
+  }
+  write_partials<2>(acc, partials);
+}
+
+template <typename T>
+cudaError_t launch_bicg_init(int64_t n, int R, const cplx_t<T>* b, const cplx_t<T>* ax,
+                             cplx_t<T>* r, cplx_t<T>* rhat, cplx_t<T>* p, cplx_t<T>* v,
+                             double* partials, cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_bicg_init<T><<<g, kThreads, 0, st>>>(n, b, ax, r, rhat, p, v, partials);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_state_init(int nblk, const double* partials, KState* ks, int* active,
+                             double tol, int max_iter) {
+  const int r = blockIdx.x;
+  double tot[2];
+  sum_partials<2>(partials, nblk, r, tot);
+  if (threadIdx.x == 0) {
+    KState k;
+    k.rnorm2 = tot[0];
+    k.bnorm2 = tot[1];
+    k.rho = make_double2(tot[0], 0.0);
+    k.rho_old = make_double2(1.0, 0.0);
+    k.alpha = make_double2(1.0, 0.0);
+    k.omega = make_double2(1.0, 0.0);
+    k.beta = make_double2(0.0, 0.0);
+    k.tol2 = tol * tol;
+    k.iters = 0;
+    k.max_iter = max_iter;
+    k.active_unused = 0;
+    const bool done = !(k.rnorm2 > k.tol2 * k.bnorm2);
+    k.status = done ? KS_CONV : KS_RUN;
+    if (!isfinite(k.rnorm2)) k.status = KS_BREAKDOWN;
+    ks[r] = k;
+    active[r] = k.status == KS_RUN ? 1 : 0;
+  }
+}
+
+cudaError_t launch_state_init(int R, int nblk, const double* partials, KState* ks,
+                              int* active, double tol, int max_iter, cudaStream_t st) {
+  k_state_init<<<R, kThreads, 0, st>>>(nblk, partials, ks, active, tol, max_iter);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_update_p(int64_t n, const cplx_t<T>* __restrict__ r, cplx_t<T>* __restrict__ p,
+                           const cplx_t<T>* __restrict__ v, const KState* __restrict__ ks,
+                           const int* __restrict__ active) {
+  using C = cplx_t<T>;
+  const int rr = blockIdx.y;
+  if (!active[rr]) return;
+  const C beta = from_d2<C>(ks[rr].beta);
+  const C omega = from_d2<C>(ks[rr].omega);
+  const int64_t off = (int64_t)rr * n;
+  GRID_LOOP(i, n) {
+    const C pv = csub(p[off + i], cmul(omega, v[off + i]));
+    p[off + i] = cadd(r[off + i], cmul(beta, pv));
+  }
+}
+
+template <typename T>
+cudaError_t launch_update_p(int64_t n, int R, const cplx_t<T>* r, cplx_t<T>* p,
+                            const cplx_t<T>* v, const KState* ks, const int* active,
+                            cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_update_p<T><<<g, kThreads, 0, st>>>(n, r, p, v, ks, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_dot_rhat_v(int64_t n, const cplx_t<T>* __restrict__ rhat,
+                             const cplx_t<T>* __restrict__ v, double* partials,
+                             const int* __restrict__ active) {
+  using C = cplx_t<T>;
+  const int rr = blockIdx.y;
+  if (!active[rr]) return;
+  const int64_t off = (int64_t)rr * n;
+  double acc[2] = {0.0, 0.0};
+  GRID_LOOP(i, n) {
+    const C a = rhat[off + i], b = v[off + i];
+    acc[0] += (double)a.x * b.x + (double)a.y * b.y;
+    acc[1] += (double)a.x * b.y - (double)a.y * b.x;
+  }
+  write_partials<2>(acc, partials);
+}
+
+template <typename T>
+cudaError_t launch_dot_rhat_v(int64_t n, int R, const cplx_t<T>* rhat, const cplx_t<T>* v,
+                              double* partials, const int* active, cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_dot_rhat_v<T><<<g, kThreads, 0, st>>>(n, rhat, v, partials, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_scalar_alpha(int nblk, const double* partials, KState* ks, int* active) {
+  const int r = blockIdx.x;
+  if (!active[r]) return;
+  double tot[2];
+  sum_partials<2>(partials, nblk, r, tot);
+  if (threadIdx.x == 0) {
+    const double2 rv = make_double2(tot[0], tot[1]);
+    KState& k = ks[r];
+    if (!(rv.x != 0.0 || rv.y != 0.0) || !finite2(rv)) {
+      k.status = KS_BREAKDOWN;
+      active[r] = 0;
+      return;
+    }
+    k.alpha = cdiv(k.rho, rv);
+  }
+}
+
+cudaError_t launch_scalar_alpha(int R, int nblk, const double* partials, KState* ks,
+                                int* active, cudaStream_t st) {
+  k_scalar_alpha<<<R, kThreads, 0, st>>>(nblk, partials, ks, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_update_s(int64_t n, const cplx_t<T>* __restrict__ r,
+                           const cplx_t<T>* __restrict__ v, cplx_t<T>* __restrict__ s,
+                           const KState* __restrict__ ks, const int* __restrict__ active) {
+  using C = cplx_t<T>;
+  const int rr = blockIdx.y;
+  if (!active[rr]) return;
+  const C alpha = from_d2<C>(ks[rr].alpha);
+  const int64_t off = (int64_t)rr * n;
+  GRID_LOOP(i, n) s[off + i] = csub(r[off + i], cmul(alpha, v[off + i]));
+}
+
+template <typename T>
+cudaError_t launch_update_s(int64_t n, int R, const cplx_t<T>* r, const cplx_t<T>* v,
+                            cplx_t<T>* s, const KState* ks, const int* active,
+                            cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_update_s<T><<<g, kThreads, 0, st>>>(n, r, v, s, ks, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_dot_ts(int64_t n, const cplx_t<T>* __restrict__ t,
+                         const cplx_t<T>* __restrict__ s, double* partials,
+                         const int* __restrict__ active) {
+  using C = cplx_t<T>;
+  const int rr = blockIdx.y;
+  if (!active[rr]) return;
+  const int64_t off = (int64_t)rr * n;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  GRID_LOOP(i, n) {
+    const C a = t[off + i], b = s[off + i];
+    acc[0] += (double)a.x * b.x + (double)a.y * b.y;
+    acc[1] += (double)a.x * b.y - (double)a.y * b.x;
+    acc[2] += (double)a.x * a.x + (double)a.y * a.y;
+  }
+  write_partials<4>(acc, partials);
+}
+
+template <typename T>
+cudaError_t launch_dot_ts(int64_t n, int R, const cplx_t<T>* t, const cplx_t<T>* s,
+                          double* partials, const int* active, cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_dot_ts<T><<<g, kThreads, 0, st>>>(n, t, s, partials, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_scalar_omega(int nblk, const double* partials, KState* ks, int* active) {
+  const int r = blockIdx.x;
+  if (!active[r]) return;
+  double tot[4];
+  sum_partials<4>(partials, nblk, r, tot);
+  if (threadIdx.x == 0) {
+    KState& k = ks[r];
+    const double tt = tot[2];
+    if (tt > 0.0 && isfinite(tt)) k.omega = make_double2(tot[0] / tt, tot[1] / tt);
+    else k.omega = make_double2(0.0, 0.0);
+  }
+}
+
+cudaError_t launch_scalar_omega(int R, int nblk, const double* partials, KState* ks,
+                                int* active, cudaStream_t st) {
+  k_scalar_omega<<<R, kThreads, 0, st>>>(nblk, partials, ks, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_update_xr(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __restrict__ r,
+                            const cplx_t<T>* __restrict__ p, const cplx_t<T>* __restrict__ s,
+                            const cplx_t<T>* __restrict__ t, const cplx_t<T>* __restrict__ rhat,
+                            double* partials, const KState* __restrict__ ks,
+                            const int* __restrict__ active) {
+  using C = cplx_t<T>;
+  const int rr = blockIdx.y;
+  if (!active[rr]) return;
+  const C alpha = from_d2<C>(ks[rr].alpha);
+  const C omega = from_d2<C>(ks[rr].omega);
+  const int64_t off = (int64_t)rr * n;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  GRID_LOOP(i, n) {
+    const C si = s[off + i];
+    x[off + i] = cadd(x[off + i], cadd(cmul(alpha, p[off + i]), cmul(omega, si)));
+    const C ri = csub(si, cmul(omega, t[off + i]));
+    r[off + i] = ri;
+    const C h = rhat[off + i];
+    acc[0] += (double)h.x * ri.x + (double)h.y * ri.y;
+    acc[1] += (double)h.x * ri.y - (double)h.y * ri.x;
+    acc[2] += (double)ri.x * ri.x + (double)ri.y * ri.y;
+  }
+  write_partials<4>(acc, partials);
+}
+
+template <typename T>
+cudaError_t launch_update_xr(int64_t n, int R, cplx_t<T>* x, cplx_t<T>* r,
+                             const cplx_t<T>* p, const cplx_t<T>* s, const cplx_t<T>* t,
+                             const cplx_t<T>* rhat, double* partials, const KState* ks,
+                             const int* active, cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_update_xr<T><<<g, kThreads, 0, st>>>(n, x, r, p, s, t, rhat, partials, ks, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_scalar_rho(int nblk, const double* partials, KState* ks, int* active) {
+  const int r = blockIdx.x;
+  if (!active[r]) return;
+  double tot[4];
+  sum_partials<4>(partials, nblk, r, tot);
+  if (threadIdx.x == 0) {
+    KState& k = ks[r];
+    const double2 rho_new = make_double2(tot[0], tot[1]);
+    k.rnorm2 = tot[2];
+    k.iters += 1;
+    if (k.rnorm2 <= k.tol2 * k.bnorm2) {
+      k.status = KS_CONV; active[r] = 0; return;
+    }
+    if (!isfinite(k.rnorm2) || !finite2(rho_new) ||
+        (rho_new.x == 0.0 && rho_new.y == 0.0) ||
+        (k.omega.x == 0.0 && k.omega.y == 0.0)) {
+      k.status = KS_BREAKDOWN; active[r] = 0; return;
+    }
+    if (k.iters >= k.max_iter) {
+      k.status = KS_NOCONV; active[r] = 0; return;
+    }
+    k.beta = cmul(cdiv(rho_new, k.rho), cdiv(k.alpha, k.omega));
+    k.rho_old = k.rho;
+    k.rho = rho_new;
+  }
+}
+
+cudaError_t launch_scalar_rho(int R, int nblk, const double* partials, KState* ks,
+                              int* active, cudaStream_t st) {
+  k_scalar_rho<<<R, kThreads, 0, st>>>(nblk, partials, ks, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ---- refinement helpers -------------------------------------------------------------
+__global__ void k_norm2(int64_t n, const double2* __restrict__ v, double* partials) {
+  const int64_t off = (int64_t)blockIdx.y * n;
+  double acc[1] = {0.0};
+  GRID_LOOP(i, n) {
+    const double2 a = v[off + i];
+    acc[0] += a.x * a.x + a.y * a.y;
+  }
+  write_partials<1>(acc, partials);
+}
+
+cudaError_t launch_norm2(int64_t n, int R, const double2* v, double* partials,
+                         cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_norm2<<<g, kThreads, 0, st>>>(n, v, partials);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int NV>
+__global__ void k_finalize(int nblk, const double* partials, double* out) {
+  const int r = blockIdx.x;
+  double tot[NV];
+  sum_partials<NV>(partials, nblk, r, tot);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[r * NV + i] = tot[i];
+  }
+}
+
+cudaError_t launch_finalize_sums(int R, int nblk, int nval, const double* partials,
+                                 double* out, cudaStream_t st) {
+  switch (nval) {
+    case 1: k_finalize<1><<<R, kThreads, 0, st>>>(nblk, partials, out); break;
+    case 2: k_finalize<2><<<R, kThreads, 0, st>>>(nblk, partials, out); break;
+    case 4: k_finalize<4><<<R, kThreads, 0, st>>>(nblk, partials, out); break;
+    case 6: k_finalize<6><<<R, kThreads, 0, st>>>(nblk, partials, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+// r may alias ax (each element is read before it is written by the same thread)
+__global__ void k_residual(int64_t n, const double2* __restrict__ b, const double2* ax,
+                           double2* r) {
+  const int64_t off = (int64_t)blockIdx.y * n;
+  GRID_LOOP(i, n) r[off + i] = csub(b[off + i], ax[off + i]);
+}
+
+cudaError_t launch_residual(int64_t n, int R, const double2* b, const double2* ax,
+                            double2* r, cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_residual<<<g, kThreads, 0, st>>>(n, b, ax, r);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_scale_to_f32(int64_t n, const double2* __restrict__ r64,
+                               const double* __restrict__ norms, float2* __restrict__ r32,
+                               const int* __restrict__ active) {
+  const int rr = blockIdx.y;
+  const double nr = norms[rr];
+  // inactive RHS get a zero right-hand side, so the inner solve skips them
+  const double sc = (nr > 0.0 && (!active || active[rr])) ? 1.0 / sqrt(nr) : 0.0;
+  const int64_t off = (int64_t)rr * n;
+  GRID_LOOP(i, n) {
+    const double2 a = r64[off + i];
+    r32[off + i] = make_float2((float)(a.x * sc), (float)(a.y * sc));
+  }
+}
+
+cudaError_t launch_scale_to_f32(int64_t n, int R, const double2* r64, const double* norms,
+                                float2* r32, const int* active, cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_scale_to_f32<<<g, kThreads, 0, st>>>(n, r64, norms, r32, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_accumulate(int64_t n, double2* __restrict__ x64, const float2* __restrict__ d32,
+                             const double* __restrict__ norms, const int* __restrict__ active) {
+  const int rr = blockIdx.y;
+  if (active && !active[rr]) return;
+  const double sc = sqrt(norms[rr]);
+  const int64_t off = (int64_t)rr * n;
+  GRID_LOOP(i, n) {
+    const float2 d = d32[off + i];
+    double2 a = x64[off + i];
+    a.x += sc * (double)d.x;
+    a.y += sc * (double)d.y;
+    x64[off + i] = a;
+  }
+}
+
+cudaError_t launch_accumulate(int64_t n, int R, double2* x64, const float2* d32,
+                              const double* norms, const int* active, cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_accumulate<<<g, kThreads, 0, st>>>(n, x64, d32, norms, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double2* __restrict__ a, float2* __restrict__ b) {
+  GRID_LOOP(i, n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+__global__ void k_f32_to_f64(int64_t n, const float2* __restrict__ a, double2* __restrict__ b) {
+  GRID_LOOP(i, n) b[i] = make_double2((double)a[i].x, (double)a[i].y);
+}
+
+cudaError_t launch_f64_to_f32(int64_t n, const double2* a, float2* b, cudaStream_t st) {
+  k_f64_to_f32<<<reduce_blocks(n), kThreads, 0, st>>>(n, a, b);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_f32_to_f64(int64_t n, const float2* a, double2* b, cudaStream_t st) {
+  k_f32_to_f64<<<reduce_blocks(n), kThreads, 0, st>>>(n, a, b);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ---- gather / scatter between the site list and the box ------------------------------
+__global__ void k_sites_to_box(int64_t N, int64_t nbox, const int64_t* __restrict__ site,
+                               const double2* __restrict__ v, double2* __restrict__ box) {
+  const int r = blockIdx.y;
+  GRID_LOOP(j, N) {
+    const int64_t s = site[j];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      box[((int64_t)r * 3 + c) * nbox + s] = v[((int64_t)r * N + j) * 3 + c];
+  }
+}
+
+__global__ void k_box_to_sites(int64_t N, int64_t nbox, const int64_t* __restrict__ site,
+                               const double2* __restrict__ box, double2* __restrict__ v) {
+  const int r = blockIdx.y;
+  GRID_LOOP(j, N) {
+    const int64_t s = site[j];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      v[((int64_t)r * N + j) * 3 + c] = box[((int64_t)r * 3 + c) * nbox + s];
+  }
+}
+
+cudaError_t launch_sites_to_box(int64_t N, int64_t nbox, int R, const int64_t* site,
+                                const double2* v, double2* box, cudaStream_t st) {
+  dim3 g(reduce_blocks(N), R);
+  k_sites_to_box<<<g, kThreads, 0, st>>>(N, nbox, site, v, box);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_box_to_sites(int64_t N, int64_t nbox, int R, const int64_t* site,
+                                const double2* box, double2* v, cudaStream_t st) {
+  dim3 g(reduce_blocks(N), R);
+  k_box_to_sites<<<g, kThreads, 0, st>>>(N, nbox, site, box, v);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ---- explicit instantiations ---------------------------------------------------------
+#define INST(T)                                                                              \
+  template cudaError_t launch_einc<T>(int, int, int, const uint8_t*, RhsTables, int,         \
+                                      cplx_t<T>*, cudaStream_t);                             \
+  template cudaError_t launch_bicg_init<T>(int64_t, int, const cplx_t<T>*, const cplx_t<T>*, \
+                                           cplx_t<T>*, cplx_t<T>*, cplx_t<T>*, cplx_t<T>*,   \
+                                           double*, cudaStream_t);                           \
+  template cudaError_t launch_update_p<T>(int64_t, int, const cplx_t<T>*, cplx_t<T>*,        \
+                                          const cplx_t<T>*, const KState*, const int*,       \
+                                          cudaStream_t);                                     \
+  template cudaError_t launch_dot_rhat_v<T>(int64_t, int, const cplx_t<T>*,                  \
+                                            const cplx_t<T>*, double*, const int*,           \
+                                            cudaStream_t);                                   \
+  template cudaError_t launch_update_s<T>(int64_t, int, const cplx_t<T>*, const cplx_t<T>*,  \
+                                          cplx_t<T>*, const KState*, const int*,             \
+                                          cudaStream_t);                                     \
+  template cudaError_t launch_dot_ts<T>(int64_t, int, const cplx_t<T>*, const cplx_t<T>*,    \
+                                        double*, const int*, cudaStream_t);                  \
+  template cudaError_t launch_update_xr<T>(int64_t, int, cplx_t<T>*, cplx_t<T>*,             \
+                                           const cplx_t<T>*, const cplx_t<T>*,               \
+                                           const cplx_t<T>*, const cplx_t<T>*, double*,      \
+                                           const KState*, const int*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace dda

@@ -1,0 +1,157 @@
+"""GPU parity of the whole solve (BiCGSTAB, refinement, observables) against
+the CPU oracle.
+
+The oracle solves to a relative residual of 1e-12; the GPU to the tolerance
+given.  Q_ext and Q_abs must agree to 1e-6 relative (the method's FP64 bar),
+P to 1e-6 in norm, f_ml to 1e-6 relative to max |f|.  The GPU's reported
+residual is recomputed by the oracle from the returned P.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from dda_inputs import targets as tg
+from dda_inputs import workloads as W
+from oracle import dda as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1305_6497_gb300 import binding
+    return binding
+
+
+def _oracle(w, i=0, tol=1e-12):
+    return O.solve_target(w.occ, w.comp, w.m, w.kd, w.khat[i], w.yhat[i], w.e01[i],
+                          w.method, npol=w.npol, tol=tol, dirs=w.dirs)
+
+
+def _check(out, ref, r0=0, tolq=1e-6, tolp=1e-6):
+    for l in range(len(ref["Qext"])):
+        r = r0 + l
+        assert abs(out["Qext"][r] / ref["Qext"][l] - 1) < tolq, (r, out["Qext"][r], ref["Qext"][l])
+        assert abs(out["Qabs"][r] / ref["Qabs"][l] - 1) < tolq
+        assert abs(out["Qsca"][r] - (out["Qext"][r] - out["Qabs"][r])) < 1e-14
+        perr = np.linalg.norm(out["P"][r] - ref["P"][l]) / np.linalg.norm(ref["P"][l])
+        assert perr < tolp, (r, perr)
+
+
+@pytest.mark.parametrize("method", ["LDR", "CM", "FCD"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+def test_solve_small_ellipsoid(B, method, precision):
+    w = W.small_ellipsoid(6, 10, 12, m=1.5 + 0.1j, kd=0.4, method=method)
+    ref = _oracle(w)
+    t = B.Target(w.occ, w.comp, w.m, method=method)
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=2, tol=1e-10, precision=precision,
+                  dirs=w.dirs)
+    assert out["status"] == B.DDA_OK
+    _check(out, ref)
+    assert np.all(out["resid"] <= 1e-10 * 1.01)
+    fa, fr = out["famp"][0], ref["famp"]
+    assert np.abs(fa - fr).max() < 1e-6 * np.abs(fr).max()
+    t.close()
+
+
+def test_solve_two_materials_with_vacancies(B):
+    w = W.two_material_brick()
+    ref = _oracle(w)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-10, dirs=w.dirs)
+    _check(out, ref)
+    t.close()
+
+
+def test_solve_many_orientations_batched(B):
+    """Several incidences x 2 polarizations solved as one batch of RHS; each
+    one must equal the oracle's solve of that incidence alone."""
+    w = W.small_ellipsoid(8, 6, 7, m=1.7 + 0.1j, kd=0.5, method="FCD", n_orient=4, seed=9)
+    t = B.Target(w.occ, w.comp, w.m, method="FCD")
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-10, precision="fp32_refined",
+                  dirs=w.dirs)
+    for i in range(4):
+        ref = _oracle(w, i)
+        _check(out, ref, r0=2 * i)
+        assert np.abs(out["famp"][i] - ref["famp"]).max() < 1e-6 * np.abs(ref["famp"]).max()
+    t.close()
+
+
+def test_c1_sphere16_vs_oracle_and_mie(B):
+    """Sphere 16^3, m = 1.33+0.01i, x = 1, LDR, FP64, tol 1e-8."""
+    from oracle import mie
+    w = W.c1_sphere16()
+    ref = _oracle(w, tol=1e-12)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-8, precision="fp64", dirs=w.dirs)
+    assert out["status"] == B.DDA_OK
+    _check(out, ref, tolq=1e-6, tolp=1e-5)
+    qe_mie = mie.mie_q(w.m[0], w.x)[0]
+    assert abs(np.mean(out["Qext"]) / qe_mie - 1) < 0.02
+    t.close()
+
+
+def test_optical_theorem_on_gpu_outputs(B):
+    w = W.small_ellipsoid(9, 7, 5, m=1.4 + 0.05j, kd=0.6, method="LDR", n_orient=3, seed=2)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-9, dirs=w.dirs)
+    g = math.pi * O.effective_radius(w.n_dipoles) ** 2
+    for i in range(3):
+        for l in range(2):
+            cext = 4 * math.pi / w.kd ** 2 * out["famp"][i, 0, l, l].imag
+            assert abs(cext / g / out["Qext"][2 * i + l] - 1) < 1e-10
+    t.close()
+
+
+def test_reported_residual_matches_oracle_residual(B):
+    w = W.small_ellipsoid(7, 8, 9, m=1.6 + 0.2j, kd=0.45, method="LDR")
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-6, precision="fp32_refined")
+    flat, pos = O.site_positions(w.occ)
+    e1, e2 = O.polarization_pair(w.khat[0], w.e01[0])
+    for l, e in enumerate((e1, e2)):
+        ainv = O.site_alpha_inverse(w.comp.reshape(-1)[flat], w.m, "LDR", w.kd, w.khat[0], e)
+        E = O.incident_field(pos, w.kd, w.khat[0], e)
+        r = E - O.matvec_direct(out["P"][l], pos, ainv, w.kd, "LDR")
+        res = np.linalg.norm(r) / np.linalg.norm(E)
+        assert abs(res / out["resid"][l] - 1) < 1e-3
+        assert res <= 1e-6
+    t.close()
+
+
+def test_warm_start_from_solution_needs_no_iterations(B):
+    w = W.small_ellipsoid(6, 6, 6, m=1.5 + 0.1j, kd=0.4, method="CM")
+    t = B.Target(w.occ, w.comp, w.m, method="CM")
+    a = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-9)
+    b = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-8, P0=a["P"])
+    assert np.all(b["iters"] == 0)
+    assert np.allclose(a["Qext"], b["Qext"], rtol=1e-12)
+    t.close()
+
+
+def test_noconv_reports_last_iterate(B):
+    w = W.small_ellipsoid(8, 8, 8, m=1.5 + 0.1j, kd=0.4, method="LDR")
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    out = t.solve(w.kd, w.khat, w.e01, tol=1e-14, max_iter=2, precision="fp64")
+    assert out["status"] == B.DDA_ERR_NOCONV
+    assert np.all(out["iters"] == 2)
+    assert np.all(np.isfinite(out["Qext"]))
+    t.close()
+
+
+def test_invalid_arguments_are_rejected(B):
+    occ, comp = tg.sphere(4)
+    with pytest.raises(B.DDAError):
+        B.Target(np.zeros((3, 3, 3), np.uint8), None, [1.5])
+    with pytest.raises(B.DDAError):
+        B.Target(occ, comp * 3, [1.5])
+    t = B.Target(occ, comp, [1.5 + 0.1j])
+    with pytest.raises(B.DDAError):
+        t.solve(-1.0, [1, 0, 0], [0, 1, 0])
+    with pytest.raises(B.DDAError):
+        t.solve(0.3, [1, 0, 0], [1, 0, 0])   # e01 not transverse
+    t.set_polarizability("FCD")
+    with pytest.raises(B.DDAError):
+        t.solve(3.5, [1, 0, 0], [0, 1, 0])   # FCD needs kd < pi
+    t.close()
