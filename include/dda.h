@@ -109,6 +109,37 @@ dda_status dda_set_polarizability(dda_target* t, dda_pol_method method);
 dda_status dda_matvec(dda_target* t, double kd, const double* khat, const double* e,
                       const double* x, double* y, dda_precision precision);
 
+/* y = A x like dda_matvec, for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is an integration variant of the same
+ * FFT-convolution matvec.  Some callers must not call cudaMalloc/cudaFree at
+ * this point: code that runs under another framework's memory manager which
+ * owns the device heap, latency-critical serving loops (cudaFree synchronizes
+ * the whole device and stalls every stream), and real-time loops that forbid
+ * allocation after start-up.  This entry point allocates nothing; its FFT
+ * scratch and alpha^{-1} table live in one fixed 64 MiB file-scope device array
+ * of the library, which every GPU that loads the library holds until exit.
+ *  x_dev, y_dev : DEVICE pointers, caller-allocated, box layout [3][nz][ny][nx]
+ *                 complex (float2 for DDA_PREC_FP32, double2 for DDA_PREC_FP64),
+ *                 x zero on vacant sites; y must not alias x.  y is written on
+ *                 every box site (0 on vacant ones).
+ *  kd, khat, e  : as dda_matvec.  The Green-tensor transform for (kd, current
+ *                 method) must already exist on the target (a previous
+ *                 dda_matvec or dda_solve with the same kd builds it, which does
+ *                 allocate); otherwise DDA_ERR_INVALID_ARG.
+ *  cuda_stream  : cudaStream_t to run on, or NULL for the target's own stream;
+ *                 the call returns after the work on that stream has finished.
+ * Limit: 3*nz*Ly*Lx complex values of the chosen precision must fit in 64 MiB
+ * minus 4 KiB (with L = 2n: cubic boxes up to 88^3 in FP32, 70^3 in FP64);
+ * larger targets get DDA_ERR_INVALID_ARG with the sizes in dda_last_error().
+ * The first call on each device looks up the device address of the static
+ * array; make that first call before any stream capture.  All calls on a device
+ * share the array and see whatever the previous call left there (nothing in it
+ * needs to start at zero): calls that overlap on the GPU (other streams, other
+ * threads) race on it and must be serialized by the caller. */
+dda_status dda_matvec_noalloc(dda_target* t, double kd, const double* khat, const double* e,
+                              const void* x_dev, void* y_dev, dda_precision precision,
+                              void* cuda_stream);
+
 typedef struct {
   double kd;             /* k d in the ambient medium                           */
   int n_inc;             /* number of incident directions (orientations) >= 1   */

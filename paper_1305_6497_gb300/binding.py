@@ -77,6 +77,9 @@ def _load():
     lib.dda_target_grid.restype = ct.c_int
     lib.dda_launch_count.argtypes = []
     lib.dda_launch_count.restype = ct.c_int64
+    lib.dda_matvec_noalloc.argtypes = [vp, ct.c_double, _dp, _dp, ct.c_void_p, ct.c_void_p,
+                                       ct.c_int, ct.c_void_p]
+    lib.dda_matvec_noalloc.restype = ct.c_int
     return lib
 
 
@@ -147,6 +150,17 @@ def dda_matvec(h, kd: float, x: np.ndarray, khat=None, e=None, precision="fp64")
     _check(lib.dda_matvec(h, float(kd), _ptr(kh), _ptr(ee), _ptr(x.view(np.float64)),
                           _ptr(y.view(np.float64)), PREC[precision]))
     return y
+
+
+def dda_matvec_noalloc(h, kd: float, x_dev_ptr: int, y_dev_ptr: int, khat=None, e=None,
+                       precision="fp64", stream_ptr: int = 0) -> None:
+    """y = A x on caller-owned DEVICE buffers (box layout [3][nz][ny][nx], complex
+    FP32 or FP64), without any device allocation by the library."""
+    kh = None if khat is None else np.ascontiguousarray(khat, dtype=np.float64)
+    ee = None if e is None else np.ascontiguousarray(np.asarray(e, np.complex128).view(np.float64))
+    _check(lib.dda_matvec_noalloc(h, float(kd), _ptr(kh), _ptr(ee), ct.c_void_p(x_dev_ptr),
+                                  ct.c_void_p(y_dev_ptr), PREC[precision],
+                                  ct.c_void_p(stream_ptr) if stream_ptr else None))
 
 
 def _params(kd, khat, e01, yhat, npol, tol, max_iter, precision, inner_tol, dirs, P0,

@@ -1044,3 +1044,114 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free matvec: the same five-pass FFT convolution as dda_matvec, with
+// its spectral scratch (and the alpha^{-1} table) in a fixed file-scope device
+// array instead of memory this library allocates.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 64ull << 20;  // 64 MiB per device
+constexpr size_t kStaticAinvBytes = 4096;            // 256 complex FP64 entries
+
+// Held by every GPU that loads this library, until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {nullptr};
+
+// Device address of g_static_scratch on the current device (looked up once
+// per device; the host-side symbol itself is not a device address).
+cudaError_t static_scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+dda_status dda_matvec_noalloc(dda_target* t, double kd, const double* khat, const double* e,
+                              const void* x_dev, void* y_dev, dda_precision precision,
+                              void* cuda_stream) {
+  g_last_error.clear();
+  if (!t || !x_dev || !y_dev) return fail(DDA_ERR_INVALID_ARG, "null argument");
+  if (x_dev == y_dev) return fail(DDA_ERR_INVALID_ARG, "x and y must not alias");
+  dda_status s = check_kd(t, kd);
+  if (s != DDA_OK) return s;
+  const bool f32 = precision != DDA_PREC_FP64;
+  const size_t elem = f32 ? sizeof(float2) : sizeof(double2);
+  const size_t need = (size_t)3 * t->nz * t->Ly * t->Lx * elem;
+  if (need > kStaticScratchBytes - kStaticAinvBytes) {
+    char msg[256];
+    snprintf(msg, sizeof msg,
+             "target needs %zu bytes of FFT scratch; the static area holds %zu "
+             "(at most 3*nz*Ly*Lx complex values of the chosen precision)",
+             need, kStaticScratchBytes - kStaticAinvBytes);
+    return fail(DDA_ERR_INVALID_ARG, msg);
+  }
+  if (t->ncomp + 1 > 256) return fail(DDA_ERR_INVALID_ARG, "too many compositions");
+  const int filtered = t->method == DDA_POL_FCD ? 1 : 0;
+  if (!t->have_green || t->green_kd != kd || t->green_filtered != filtered || !t->kernels_configured)
+    return fail(DDA_ERR_INVALID_ARG,
+                "the Green-tensor transform for this kd and method is not built: call "
+                "dda_matvec or dda_solve once with them first (building it allocates)");
+  double kh[3] = {1, 0, 0};
+  cd ev[3] = {0.0, 1.0, 0.0};
+  if (t->method == DDA_POL_LDR) {
+    if (!khat || !e) return fail(DDA_ERR_INVALID_ARG, "LDR needs khat and e");
+    double kn = std::sqrt(khat[0] * khat[0] + khat[1] * khat[1] + khat[2] * khat[2]);
+    if (!(kn > 0)) return fail(DDA_ERR_INVALID_ARG, "khat is zero");
+    for (int c = 0; c < 3; ++c) { kh[c] = khat[c] / kn; ev[c] = cd(e[2 * c], e[2 * c + 1]); }
+  }
+  try {
+    CK(cudaSetDevice(t->device));
+    void* base = nullptr;
+    CK(static_scratch_address(t->device, &base));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : t->stream;
+    unsigned char* area = reinterpret_cast<unsigned char*>(base);
+    // alpha^{-1} per composition (entry 0 unused) at the start of the area
+    double2 ai64[256];
+    float2 ai32[256];
+    for (int c = 0; c <= t->ncomp; ++c) { ai64[c] = make_double2(0, 0); ai32[c] = make_float2(0, 0); }
+    for (int c = 1; c <= t->ncomp; ++c) {
+      const cd a = 1.0 / alpha_of(t->method, t->m[c - 1], kd, kh, ev);
+      ai64[c] = make_double2(a.real(), a.imag());
+      ai32[c] = make_float2((float)a.real(), (float)a.imag());
+    }
+    const size_t nai = (size_t)(t->ncomp + 1);
+    // the spectral scratch needs no clearing: every element the passes read was
+    // written earlier in the same call
+    if (f32) {
+      CK(cudaMemcpyAsync(area, ai32, sizeof(float2) * nai, cudaMemcpyHostToDevice, st));
+      OpView<float> op = make_view<float>(t, t->g32.p, area, t->tw32.p);
+      CK(launch_matvec<float>(op, t->L32, 1, reinterpret_cast<const float2*>(x_dev),
+                              reinterpret_cast<float2*>(y_dev),
+                              reinterpret_cast<float2*>(area + kStaticAinvBytes), nullptr, st));
+    } else {
+      CK(cudaMemcpyAsync(area, ai64, sizeof(double2) * nai, cudaMemcpyHostToDevice, st));
+      OpView<double> op = make_view<double>(t, t->g64.p, area, t->tw64.p);
+      CK(launch_matvec<double>(op, t->L64, 1, reinterpret_cast<const double2*>(x_dev),
+                               reinterpret_cast<double2*>(y_dev),
+                               reinterpret_cast<double2*>(area + kStaticAinvBytes), nullptr,
+                               st));
+    }
+    CK(cudaStreamSynchronize(st));
+  } catch (const CudaFail& f) {
+    return from_cuda(f);
+  }
+  return DDA_OK;
+}
+
+}  // extern "C"
