@@ -87,18 +87,27 @@ static int smooth_at_least(int m) {
   return n;
 }
 
+// Radices of L, largest first: 16s, then one 8/4/2 for the rest of the powers
+// of two, then 3s and 5s; a trailing 16 is split into 4 x 4 so that the last
+// stage (which the z pass runs forward, multiplies and runs back in registers
+// for three components at once) has radix <= 8.
 static std::vector<int> factor_radices(int L) {
   int a = 0, n = L;
   while (n % 2 == 0) { n /= 2; ++a; }
   std::vector<int> r;
-  // powers of two: radix 8 as long as no single 2 is left over
-  int e8 = a / 3, rem = a % 3;
-  if (rem == 1 && e8 >= 1) { e8 -= 1; r.push_back(4); r.push_back(4); }
-  else if (rem == 1) r.push_back(2);
-  else if (rem == 2) r.push_back(4);
-  for (int i = 0; i < e8; ++i) r.insert(r.begin(), 8);
+  int q = a / 4, rem = a % 4;
+  for (int i = 0; i < q; ++i) r.push_back(16);
+  if (rem == 1) {
+    if (q >= 1) { r.back() = 8; r.push_back(4); }   // 16*2 -> 8*4
+    else r.push_back(2);
+  } else if (rem == 2) {
+    r.push_back(4);
+  } else if (rem == 3) {
+    r.push_back(8);
+  }
   while (n % 3 == 0) { n /= 3; r.push_back(3); }
   while (n % 5 == 0) { n /= 5; r.push_back(5); }
+  if (!r.empty() && r.back() == 16) { r.back() = 4; r.push_back(4); }
   return r;
 }
 
@@ -171,11 +180,16 @@ struct Workspace {
   }
 };
 
-// Per-pass CUDA-event timing of the matvec kernels (enabled per solve).
+// Per-pass CUDA-event timing of the matvec kernels (enabled per solve).  Event
+// sets: [slot][matvec 0/1] for the iterations between two convergence checks,
+// plus one set for the FP64 residual matvecs.
+constexpr int kCheckEvery = 4;  // BiCGSTAB iterations between host convergence checks
+
 struct Profiler {
   bool on = false;
   bool created = false;
-  cudaEvent_t ev[3][kMatvecPasses + 1];
+  cudaEvent_t ev[kCheckEvery][2][kMatvecPasses + 1];
+  cudaEvent_t evr[kMatvecPasses + 1];
   double ms[2][kMatvecPasses];
   long long calls[2][kMatvecPasses];
   void reset() {
@@ -184,26 +198,38 @@ struct Profiler {
   }
   void create() {
     if (created) return;
-    for (auto& set : ev)
-      for (auto& e : set) CK(cudaEventCreate(&e));
+    for (auto& slot : ev)
+      for (auto& set : slot)
+        for (auto& e : set) CK(cudaEventCreate(&e));
+    for (auto& e : evr) CK(cudaEventCreate(&e));
     created = true;
   }
   void destroy() {
     if (!created) return;
-    for (auto& set : ev)
-      for (auto& e : set) cudaEventDestroy(e);
+    for (auto& slot : ev)
+      for (auto& set : slot)
+        for (auto& e : set) cudaEventDestroy(e);
+    for (auto& e : evr) cudaEventDestroy(e);
     created = false;
   }
-  const cudaEvent_t* set(int k) const { return on ? ev[k] : nullptr; }
-  // after a synchronize: add the pass times of event set k to precision slot p
-  void harvest(int p, int k) {
-    if (!on) return;
+  const cudaEvent_t* iter_set(int slot, int k) const { return on ? ev[slot][k] : nullptr; }
+  const cudaEvent_t* resid_set() const { return on ? evr : nullptr; }
+  void add(int p, const cudaEvent_t* e) {
     for (int i = 0; i < kMatvecPasses; ++i) {
       float t = 0.f;
-      CK(cudaEventElapsedTime(&t, ev[k][i], ev[k][i + 1]));
+      CK(cudaEventElapsedTime(&t, e[i], e[i + 1]));
       ms[p][i] += t;
       calls[p][i] += 1;
     }
+  }
+  // after a synchronize: add the times of the first `nslots` iteration slots
+  void harvest_iters(int p, int nslots) {
+    if (!on) return;
+    for (int sl = 0; sl < nslots; ++sl)
+      for (int k = 0; k < 2; ++k) add(p, ev[sl][k]);
+  }
+  void harvest_resid() {
+    if (on) add(1, evr);
   }
 };
 
@@ -409,25 +435,30 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
   int nact = 0;
   for (int a : hact) nact += a;
   int iter = 0;
+  const int nblk_mv = matvec_partial_blocks<T>(op, L);
   while (nact > 0 && iter < max_iter) {
-    CK(launch_update_p<T>(n, R, V.r, V.p, V.v, ks, act, st));
-    CK(launch_matvec<T>(op, L, R, V.p, V.v, V.scr, act, st, t->prof.set(0)));
-    CK(launch_dot_rhat_v<T>(n, R, V.rh, V.v, part, act, st));
-    CK(launch_scalar_alpha(R, nblk, part, ks, act, st));
-    CK(launch_update_s<T>(n, R, V.r, V.v, V.s, ks, act, st));
-    CK(launch_matvec<T>(op, L, R, V.s, V.t, V.scr, act, st, t->prof.set(1)));
-    CK(launch_dot_ts<T>(n, R, V.t, V.s, part, act, st));
-    CK(launch_scalar_omega(R, nblk, part, ks, act, st));
-    CK(launch_update_xr<T>(n, R, V.x, V.r, V.p, V.s, V.t, V.rh, part, ks, act, st));
-    CK(launch_scalar_rho(R, nblk, part, ks, act, st));
-    matvecs += 2 * (int64_t)nact;
+    // kCheckEvery iterations are queued back to back; a converged RHS is frozen
+    // on the device by its active flag, so the extra iterations cost nothing
+    const int nq = std::min(kCheckEvery, max_iter - iter);
+    for (int q = 0; q < nq; ++q) {
+      // p <- r + beta (p - omega v); v = A p; <rhat, v>
+      CK(launch_matvec_p<T>(op, L, R, V.r, V.p, V.v, V.rh, V.scr, ks, part, act, st,
+                            t->prof.iter_set(q, 0)));
+      CK(launch_scalar_alpha(R, nblk_mv, part, ks, act, st));
+      // s <- r - alpha v; t = A s; <t, s>, <t, t>
+      CK(launch_matvec_s<T>(op, L, R, V.r, V.v, V.s, V.t, V.scr, ks, part, act, st,
+                            t->prof.iter_set(q, 1)));
+      CK(launch_scalar_omega(R, nblk_mv, part, ks, act, st));
+      // x += alpha p + omega s; r = s - omega t; <rhat, r>, <r, r>
+      CK(launch_update_xr<T>(n, R, V.x, V.r, V.p, V.s, V.t, V.rh, part, ks, act, st));
+      CK(launch_scalar_rho(R, nblk, part, ks, act, st));
+    }
     CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    t->prof.harvest(sizeof(T) == 4 ? 0 : 1, 0);
-    t->prof.harvest(sizeof(T) == 4 ? 0 : 1, 1);
+    t->prof.harvest_iters(sizeof(T) == 4 ? 0 : 1, nq);
     nact = 0;
     for (int a : hact) nact += a;
-    ++iter;
+    iter += nq;
   }
   std::vector<KState> hks(R);
   CK(cudaMemcpyAsync(hks.data(), ks, sizeof(KState) * R, cudaMemcpyDeviceToHost, st));
@@ -435,6 +466,7 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
   its.resize(R);
   status.resize(R);
   for (int r = 0; r < R; ++r) {
+    matvecs += 2 * (int64_t)hks[r].iters;  // frozen RHS do no work
     its[r] = hks[r].iters;
     status[r] = hks[r].status == KS_RUN ? KS_NOCONV : hks[r].status;
   }
@@ -453,14 +485,17 @@ static int64_t workspace_bytes(const dda_target* t, int R, dda_precision prec, i
   if (!f32) b += 5 * nv * 16;
   b += ns * 16;  // FP64 scratch (final/true residual matvec)
   if (f32) b += 8 * nv * 8 + ns * 8;
-  const int nblk = reduce_blocks(3 * t->nbox);
+  const int nblk = std::max(reduce_blocks(3 * t->nbox), 3 * t->nz * t->ny);
   b += (int64_t)std::max(4 * R, 6 * R * (ndir + 1)) * nblk * 8;
   b += (int64_t)R * (sizeof(KState) + 64) + (int64_t)R * (t->nx + t->ny + t->nz + 8) * 16;
   b += (int64_t)(ndir + 1) * (t->nx + t->ny + t->nz) * 16 + t->N * (int64_t)R * 48;
   return b;
 }
 
+static void configure(dda_target* t);
+
 static void ensure_workspace(dda_target* t, int R, dda_precision prec, int ndir) {
+  configure(t);
   Workspace& w = t->ws;
   const int64_t nv = 3 * t->nbox * (int64_t)R;
   const int64_t ns = 3 * (int64_t)t->nz * t->Ly * t->Lx * R;
@@ -475,7 +510,9 @@ static void ensure_workspace(dda_target* t, int R, dda_precision prec, int ndir)
     w.v32.ensure(nv * 8); w.s32.ensure(nv * 8); w.t32.ensure(nv * 8); w.b32.ensure(nv * 8);
     w.scr32.ensure(ns * 8);
   }
-  const int nblk = reduce_blocks(3 * t->nbox);
+  const int rows = 3 * t->nz * t->ny;
+  const int nblk = std::max({reduce_blocks(3 * t->nbox), (rows + t->L32.x_lines - 1) / t->L32.x_lines,
+                             (rows + t->L64.x_lines - 1) / t->L64.x_lines});
   w.partials.ensure((size_t)std::max(4 * R, 6 * R * (ndir + 1)) * nblk * 8);
   w.ks.ensure(sizeof(KState) * R);
   w.active.ensure(sizeof(int) * R);
@@ -816,6 +853,7 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
     const int nblk = reduce_blocks(n);
     double* part = w.partials.as<double>();
     std::vector<double> bn2(R), rn2(R);
+    bool resid_fresh = false;  // rn2 already holds ||b - A x||^2 of the final x (FP64)
     // ||b||^2 per RHS
     CK(launch_norm2(n, R, w.b64.as<double2>(), part, st));
     CK(launch_finalize_sums(R, nblk, 1, part, w.sums.as<double>(), st));
@@ -857,7 +895,7 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
           CK(cudaMemcpyAsync(w.r64.p, w.b64.p, sizeof(double2) * n * R, cudaMemcpyDeviceToDevice, st));
         } else {
           CK(launch_matvec<double>(op64, t->L64, R, w.x64.as<double2>(), w.r64.as<double2>(),
-                                   w.scr64.as<double2>(), nullptr, st, t->prof.set(2)));
+                                   w.scr64.as<double2>(), nullptr, st, t->prof.resid_set()));
           matvecs += R; matvecs64 += R;
           CK(launch_residual(n, R, w.b64.as<double2>(), w.r64.as<double2>(),
                              w.r64.as<double2>(), st));
@@ -867,7 +905,8 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
         CK(launch_finalize_sums(R, nblk, 1, part, w.norms.as<double>(), st));
         CK(cudaMemcpyAsync(rn2.data(), w.norms.p, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (!(sweep == 0 && !x_nonzero)) t->prof.harvest(1, 2);
+        if (!(sweep == 0 && !x_nonzero)) t->prof.harvest_resid();
+        resid_fresh = true;
         int nact = 0;
         for (int r = 0; r < R; ++r) {
           if (!outer_act[r]) continue;
@@ -904,19 +943,26 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
         }
         CK(launch_accumulate(n, R, w.x64.as<double2>(), V.x, w.norms.as<double>(),
                              w.active_outer.as<int>(), st));
+        resid_fresh = false;
       }
       for (int r = 0; r < R; ++r)
         if (status[r] == KS_RUN) status[r] = KS_NOCONV;
     }
 
-    // ---- true residual (FP64) of the result ----
-    CK(launch_matvec<double>(op64, t->L64, R, w.x64.as<double2>(), w.r64.as<double2>(),
-                             w.scr64.as<double2>(), nullptr, st, t->prof.set(2)));
-    matvecs += R; matvecs64 += R;
-    CK(launch_residual(n, R, w.b64.as<double2>(), w.r64.as<double2>(), w.r64.as<double2>(), st));
-    CK(launch_norm2(n, R, w.r64.as<double2>(), part, st));
-    CK(launch_finalize_sums(R, nblk, 1, part, w.norms.as<double>(), st));
-    CK(cudaMemcpyAsync(rn2.data(), w.norms.p, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    // ---- true residual (FP64) of the result, unless the refinement loop's last
+    //      residual already belongs to the final iterate ----
+    const bool final_matvec = !resid_fresh;
+    if (final_matvec) {
+      CK(launch_matvec<double>(op64, t->L64, R, w.x64.as<double2>(), w.r64.as<double2>(),
+                               w.scr64.as<double2>(), nullptr, st, t->prof.resid_set()));
+      matvecs += R; matvecs64 += R;
+      CK(launch_residual(n, R, w.b64.as<double2>(), w.r64.as<double2>(), w.r64.as<double2>(),
+                         st));
+      CK(launch_norm2(n, R, w.r64.as<double2>(), part, st));
+      CK(launch_finalize_sums(R, nblk, 1, part, w.norms.as<double>(), st));
+      CK(cudaMemcpyAsync(rn2.data(), w.norms.p, sizeof(double) * R, cudaMemcpyDeviceToHost,
+                         st));
+    }
 
     // ---- observables ----
     CK(launch_cross_sections(t->nx, t->ny, t->nz, t->comp.as<uint8_t>(), tb, R,
@@ -925,7 +971,7 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
     CK(launch_finalize_sums(R, nblk, 2, part, w.sums.as<double>(), st));
     CK(cudaMemcpyAsync(qs.data(), w.sums.p, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    t->prof.harvest(1, 2);
+    if (final_matvec) t->prof.harvest_resid();
     std::vector<double> ff;
     if (res->famp) {
       ff.resize((size_t)p->n_inc * D * p->npol * 6);

@@ -15,7 +15,7 @@ long long launch_count();
 struct MatvecLaunch {
   int x_lines, x_threads; size_t x_smem;
   int y_tile, y_threads; size_t y_smem;
-  int z_tile, z_threads; size_t z_smem;
+  int z_tile, z_ps, z_threads; size_t z_smem;
 };
 
 template <typename T> MatvecLaunch plan_matvec(const OpView<T>& op);
@@ -56,6 +56,26 @@ struct KState {
 };
 
 enum { KS_RUN = 0, KS_CONV = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3 };
+
+// Matvecs fused with BiCGSTAB steps (same five passes as launch_matvec):
+//  launch_matvec_p: p <- r + beta (p - omega v); v = A p; partials of <rhat, v>
+//                   ([R][nblk][2])
+//  launch_matvec_s: s <- r - alpha v; t = A s; partials of <t, s>, <t, t>
+//                   ([R][nblk][4])
+// nblk = matvec_partial_blocks(op, L).
+template <typename T> int matvec_partial_blocks(const OpView<T>& op, const MatvecLaunch& L);
+template <typename T>
+cudaError_t launch_matvec_p(const OpView<T>& op, const MatvecLaunch& L, int R,
+                            const cplx_t<T>* r, cplx_t<T>* p, cplx_t<T>* v,
+                            const cplx_t<T>* rhat, cplx_t<T>* scratch, const KState* ks,
+                            double* partials, const int* active, cudaStream_t st,
+                            const cudaEvent_t* ev = nullptr);
+template <typename T>
+cudaError_t launch_matvec_s(const OpView<T>& op, const MatvecLaunch& L, int R,
+                            const cplx_t<T>* r, const cplx_t<T>* v, cplx_t<T>* s_vec,
+                            cplx_t<T>* t_vec, cplx_t<T>* scratch, const KState* ks,
+                            double* partials, const int* active, cudaStream_t st,
+                            const cudaEvent_t* ev = nullptr);
 
 struct RhsTables {            // per-RHS incident-wave data (device)
   const double2* pol;         // [R][3] polarization vector

@@ -99,12 +99,54 @@ template <bool INV, typename C> __device__ __forceinline__ void dft5(C (&a)[5]) 
   }
 }
 
+// w * a with w = c - i s (forward) or c + i s (inverse)
+template <bool INV, typename C, typename T>
+__device__ __forceinline__ C rot(C a, T c, T s) {
+  C r;
+  if (INV) { r.x = c * a.x - s * a.y; r.y = c * a.y + s * a.x; }
+  else     { r.x = c * a.x + s * a.y; r.y = c * a.y - s * a.x; }
+  return r;
+}
+
+// 16 = 4 x 4: DFT4 over n1 for each n2, twiddle w16^(n2 k1), DFT4 over n2;
+// X[k1 + 4 k2] ends in a[k1 + 4 k2].
+template <bool INV, typename C> __device__ __forceinline__ void dft16(C (&a)[16]) {
+  using T = decltype(a[0].x);
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;  // pi/8
+  const T h = (T)0.70710678118654752440;
+  C y[4][4];  // y[n2][k1]
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C b0 = a[n2], b1 = a[4 + n2], b2 = a[8 + n2], b3 = a[12 + n2];
+    dft4<INV>(b0, b1, b2, b3);
+    y[n2][0] = b0; y[n2][1] = b1; y[n2][2] = b2; y[n2][3] = b3;
+  }
+  // twiddles w16^(n2 k1): (1,1)=1, (1,2)=2, (1,3)=3, (2,1)=2, (2,2)=4, (2,3)=6,
+  // (3,1)=3, (3,2)=6, (3,3)=9 in units of pi/8
+  y[1][1] = rot<INV>(y[1][1], c1, s1);
+  y[1][2] = rot<INV>(y[1][2], h, h);
+  y[1][3] = rot<INV>(y[1][3], s1, c1);
+  y[2][1] = rot<INV>(y[2][1], h, h);
+  y[2][2] = cmul_i<INV>(y[2][2]);
+  y[2][3] = rot<INV>(y[2][3], -h, h);
+  y[3][1] = rot<INV>(y[3][1], s1, c1);
+  y[3][2] = rot<INV>(y[3][2], -h, h);
+  y[3][3] = rot<INV>(y[3][3], -c1, -s1);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C b0 = y[0][k1], b1 = y[1][k1], b2 = y[2][k1], b3 = y[3][k1];
+    dft4<INV>(b0, b1, b2, b3);
+    a[k1] = b0; a[k1 + 4] = b1; a[k1 + 8] = b2; a[k1 + 12] = b3;
+  }
+}
+
 template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C (&v)[R]) {
   if constexpr (R == 2) dft2<INV>(v[0], v[1]);
   else if constexpr (R == 3) dft3<INV>(v[0], v[1], v[2]);
   else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
   else if constexpr (R == 5) dft5<INV>(v);
-  else dft8<INV>(v);
+  else if constexpr (R == 8) dft8<INV>(v);
+  else dft16<INV>(v);
 }
 
 // ---- one in-place stage ------------------------------------------------------
@@ -139,6 +181,26 @@ __device__ __forceinline__ void fft_stage(C* s, int nlines, int pstride, int L, 
   __syncthreads();
 }
 
+#define DDA_RADIX_DISPATCH(radix, BODY)                 \
+  switch (radix) {                                      \
+    case 16: { constexpr int RR = 16; BODY; } break;    \
+    case 8: { constexpr int RR = 8; BODY; } break;      \
+    case 4: { constexpr int RR = 4; BODY; } break;      \
+    case 2: { constexpr int RR = 2; BODY; } break;      \
+    case 3: { constexpr int RR = 3; BODY; } break;      \
+    default: { constexpr int RR = 5; BODY; } break;     \
+  }
+
+// the same without radix 16 (stages the plan never gives radix 16)
+#define DDA_RADIX_DISPATCH_SMALL(radix, BODY)           \
+  switch (radix) {                                      \
+    case 8: { constexpr int RR = 8; BODY; } break;      \
+    case 4: { constexpr int RR = 4; BODY; } break;      \
+    case 2: { constexpr int RR = 2; BODY; } break;      \
+    case 3: { constexpr int RR = 3; BODY; } break;      \
+    default: { constexpr int RR = 5; BODY; } break;     \
+  }
+
 template <typename C, bool INV, int R>
 __device__ __forceinline__ void run_stage(C* s, int nlines, int pstride, const AxisPlan& P,
                                           int st, const C* __restrict__ tw) {
@@ -152,14 +214,118 @@ __device__ void fft_smem(C* s, int nlines, int pstride, const AxisPlan& P,
                          const C* __restrict__ tw) {
   for (int k = 0; k < P.nstage; ++k) {
     const int st = INV ? P.nstage - 1 - k : k;
-    switch (P.radix[st]) {
-      case 8: run_stage<C, INV, 8>(s, nlines, pstride, P, st, tw); break;
-      case 4: run_stage<C, INV, 4>(s, nlines, pstride, P, st, tw); break;
-      case 2: run_stage<C, INV, 2>(s, nlines, pstride, P, st, tw); break;
-      case 3: run_stage<C, INV, 3>(s, nlines, pstride, P, st, tw); break;
-      default: run_stage<C, INV, 5>(s, nlines, pstride, P, st, tw); break;
-    }
+    DDA_RADIX_DISPATCH(P.radix[st], (run_stage<C, INV, RR>(s, nlines, pstride, P, st, tw)));
   }
+}
+
+// ---- stages fused with global memory ---------------------------------------------
+// The first forward stage (block = L) reads its R inputs straight from global
+// memory through ld(line, p) (which returns 0 for positions beyond the input);
+// the last inverse stage (its adjoint) writes straight to global memory through
+// st(line, p, v) (which drops positions beyond the output).  The last forward
+// stage (block = R, span 1) and its adjoint read/write R consecutive positions.
+// Consecutive threads take consecutive lines, so with lines = consecutive
+// columns of a row-major plane every global access is coalesced.
+
+template <typename C, int R, class LD>
+__device__ __forceinline__ void stage_first_fwd(C* s, int nlines, int ps, int L,
+                                                const C* __restrict__ tw, const LD& ld) {
+  const int S = L / R;
+  const int nb = nlines * S;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int line = b % nlines, j = b / nlines;
+    C v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = ld(line, j + i * S);
+    dft<R, false>(v);
+    if (j > 0) {
+#pragma unroll
+      for (int m = 1; m < R; ++m) v[m] = cmul(v[m], __ldg(&tw[j * (R - 1) + (m - 1)]));
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) s[(j + m * S) * ps + line] = v[m];
+  }
+  __syncthreads();
+}
+
+template <typename C, int R, class ST>
+__device__ __forceinline__ void stage_last_inv(const C* s, int nlines, int ps, int L,
+                                               const C* __restrict__ tw, const ST& st) {
+  const int S = L / R;
+  const int nb = nlines * S;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int line = b % nlines, j = b / nlines;
+    C v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = s[(j + m * S) * ps + line];
+    if (j > 0) {
+#pragma unroll
+      for (int m = 1; m < R; ++m) v[m] = cmulc(__ldg(&tw[j * (R - 1) + (m - 1)]), v[m]);
+    }
+    dft<R, true>(v);
+#pragma unroll
+    for (int i = 0; i < R; ++i) st(line, j + i * S, v[i]);
+  }
+}
+
+template <typename C, int R, class ST>
+__device__ __forceinline__ void stage_last_fwd(const C* s, int nlines, int ps, int L,
+                                               const ST& st) {
+  const int nb = nlines * (L / R);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int line = b % nlines, blk = b / nlines;
+    C v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = s[(blk * R + i) * ps + line];
+    dft<R, false>(v);
+#pragma unroll
+    for (int m = 0; m < R; ++m) st(line, blk * R + m, v[m]);
+  }
+}
+
+template <typename C, int R, class LD>
+__device__ __forceinline__ void stage_first_inv(C* s, int nlines, int ps, int L, const LD& ld) {
+  const int nb = nlines * (L / R);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int line = b % nlines, blk = b / nlines;
+    C v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = ld(line, blk * R + m);
+    dft<R, true>(v);
+#pragma unroll
+    for (int i = 0; i < R; ++i) s[(blk * R + i) * ps + line] = v[i];
+  }
+  __syncthreads();
+}
+
+// Middle forward stages 1 .. nstage-2, or inverse stages nstage-2 .. 1.
+template <typename C, bool INV>
+__device__ __forceinline__ void fft_inner_stages(C* s, int nlines, int ps, const AxisPlan& P,
+                                                 const C* __restrict__ tw) {
+  for (int k = 1; k + 1 < P.nstage; ++k) {
+    const int st = INV ? P.nstage - 1 - k : k;
+    DDA_RADIX_DISPATCH(P.radix[st], (run_stage<C, INV, RR>(s, nlines, ps, P, st, tw)));
+  }
+}
+
+// Forward transform of lines read from global memory, results written to
+// global memory (needs nstage >= 2).
+template <typename C, class LD, class ST>
+__device__ void fft_global_fwd(C* s, int nlines, int ps, const AxisPlan& P,
+                               const C* __restrict__ tw, const LD& ld, const ST& st) {
+  DDA_RADIX_DISPATCH(P.radix[0], (stage_first_fwd<C, RR>(s, nlines, ps, P.L, tw, ld)));
+  fft_inner_stages<C, false>(s, nlines, ps, P, tw);
+  DDA_RADIX_DISPATCH(P.radix[P.nstage - 1], (stage_last_fwd<C, RR>(s, nlines, ps, P.L, st)));
+}
+
+// Inverse transform of lines read from global memory (digit-reversed), natural
+// order results written to global memory (needs nstage >= 2).
+template <typename C, class LD, class ST>
+__device__ void fft_global_inv(C* s, int nlines, int ps, const AxisPlan& P,
+                               const C* __restrict__ tw, const LD& ld, const ST& st) {
+  DDA_RADIX_DISPATCH(P.radix[P.nstage - 1], (stage_first_inv<C, RR>(s, nlines, ps, P.L, ld)));
+  fft_inner_stages<C, true>(s, nlines, ps, P, tw);
+  DDA_RADIX_DISPATCH(P.radix[0], (stage_last_inv<C, RR>(s, nlines, ps, P.L, tw, st)));
 }
 
 }  // namespace dda

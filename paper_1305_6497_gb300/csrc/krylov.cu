@@ -71,7 +71,7 @@ __global__ void k_bicg_init(int64_t n, const cplx_t<T>* __restrict__ b,
                             cplx_t<T>* __restrict__ v, double* partials) {
   using C = cplx_t<T>;
   const int64_t off = (int64_t)blockIdx.y * n;
-  double acc[2] = {0.0, 0.0};
+  ChunkAcc<T, 2> acc;
   GRID_LOOP(i, n) {
     const C bi = b[off + i];
     C ri = bi;
@@ -80,10 +80,12 @@ __global__ void k_bicg_init(int64_t n, const cplx_t<T>* __restrict__ b,
     rhat[off + i] = ri;
     p[off + i] = mk<C>(0, 0);
     v[off + i] = mk<C>(0, 0);
-    acc[0] += (double)ri.x * ri.x + (double)ri.y * ri.y;
-    acc[1] += (double)bi.x * bi.x + (double)bi.y * bi.y;
+    acc.add(0, ri.x * ri.x + ri.y * ri.y);
+    acc.add(1, bi.x * bi.x + bi.y * bi.y);
+    acc.step();
   }
-  write_partials<2>(acc, partials);
+  acc.flush();
+  write_partials<2>(acc.tot, partials);
 }
 
 template <typename T>
@@ -163,13 +165,15 @@ __global__ void k_dot_rhat_v(int64_t n, const cplx_t<T>* __restrict__ rhat,
   const int rr = blockIdx.y;
   if (!active[rr]) return;
   const int64_t off = (int64_t)rr * n;
-  double acc[2] = {0.0, 0.0};
+  ChunkAcc<T, 2> acc;
   GRID_LOOP(i, n) {
     const C a = rhat[off + i], b = v[off + i];
-    acc[0] += (double)a.x * b.x + (double)a.y * b.y;
-    acc[1] += (double)a.x * b.y - (double)a.y * b.x;
+    acc.add(0, a.x * b.x + a.y * b.y);
+    acc.add(1, a.x * b.y - a.y * b.x);
+    acc.step();
   }
-  write_partials<2>(acc, partials);
+  acc.flush();
+  write_partials<2>(acc.tot, partials);
 }
 
 template <typename T>
@@ -235,14 +239,16 @@ __global__ void k_dot_ts(int64_t n, const cplx_t<T>* __restrict__ t,
   const int rr = blockIdx.y;
   if (!active[rr]) return;
   const int64_t off = (int64_t)rr * n;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  ChunkAcc<T, 4> acc;
   GRID_LOOP(i, n) {
     const C a = t[off + i], b = s[off + i];
-    acc[0] += (double)a.x * b.x + (double)a.y * b.y;
-    acc[1] += (double)a.x * b.y - (double)a.y * b.x;
-    acc[2] += (double)a.x * a.x + (double)a.y * a.y;
+    acc.add(0, a.x * b.x + a.y * b.y);
+    acc.add(1, a.x * b.y - a.y * b.x);
+    acc.add(2, a.x * a.x + a.y * a.y);
+    acc.step();
   }
-  write_partials<4>(acc, partials);
+  acc.flush();
+  write_partials<4>(acc.tot, partials);
 }
 
 template <typename T>
@@ -286,18 +292,20 @@ __global__ void k_update_xr(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __r
   const C alpha = from_d2<C>(ks[rr].alpha);
   const C omega = from_d2<C>(ks[rr].omega);
   const int64_t off = (int64_t)rr * n;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  ChunkAcc<T, 4> acc;
   GRID_LOOP(i, n) {
     const C si = s[off + i];
     x[off + i] = cadd(x[off + i], cadd(cmul(alpha, p[off + i]), cmul(omega, si)));
     const C ri = csub(si, cmul(omega, t[off + i]));
     r[off + i] = ri;
     const C h = rhat[off + i];
-    acc[0] += (double)h.x * ri.x + (double)h.y * ri.y;
-    acc[1] += (double)h.x * ri.y - (double)h.y * ri.x;
-    acc[2] += (double)ri.x * ri.x + (double)ri.y * ri.y;
+    acc.add(0, h.x * ri.x + h.y * ri.y);
+    acc.add(1, h.x * ri.y - h.y * ri.x);
+    acc.add(2, ri.x * ri.x + ri.y * ri.y);
+    acc.step();
   }
-  write_partials<4>(acc, partials);
+  acc.flush();
+  write_partials<4>(acc.tot, partials);
 }
 
 template <typename T>
