@@ -252,6 +252,7 @@ def run_gpu(args, rank, world, local_rank):
         iters.append(int(np.sum(out["iters"])))
         fp32_rhs_mv += out["matvecs"] - out["matvecs_fp64"]
         fp64_rhs_mv += out["matvecs_fp64"]
+        sweeps = out["sweeps"]
         for k, v in out["kernel_ms"].items():
             kern_ms[k] = kern_ms.get(k, 0.0) + v
             kern_calls[k] = kern_calls.get(k, 0) + out["kernel_calls"][k]
@@ -342,6 +343,9 @@ def run_gpu(args, rank, world, local_rank):
                        "p99": sorted(step_ms)[min(len(step_ms) - 1,
                                                    int(math.ceil(0.99 * len(step_ms))) - 1)]},
         "iters_per_rhs": sum(iters) / (R * args.steps),
+        "refinement": {"sweeps_per_rhs": [int(x) for x in sweeps],
+                       "fp64_rhs_matvecs_per_step": fp64_rhs_mv / args.steps,
+                       "fp32_rhs_matvecs_per_step": fp32_rhs_mv / args.steps},
         "fp64_vs_refined": {
             "fp64_ms_per_solve_batch": statistics.mean(ms64),
             "fp64_dipole_iters_per_s": N * sum(it64) / (sum(ms64) / 1e3),

@@ -227,20 +227,29 @@ def green(kind: str):
 # The matrix A of eq. (AP=E):  (A P)_j = alpha_j^{-1} P_j - sum_{l != j} G(r_j - r_l) P_l
 # --------------------------------------------------------------------------
 def matvec_direct(P: np.ndarray, pos: np.ndarray, ainv: np.ndarray, kd: float,
-                  method: str = "LDR", rows=None, block: int = 256) -> np.ndarray:
-    """A.P by direct O(N^2) summation.  P [N, 3] complex; returns [len(rows), 3]."""
+                  method: str = "LDR", rows=None, block: int = 256,
+                  col_block: int | None = None) -> np.ndarray:
+    """A.P by direct O(N^2) summation.  P [N, 3] complex; returns [len(rows), 3].
+
+    The interaction sum over l runs over all sites at once, or in chunks of
+    `col_block` sites (for very large N; only the grouping of the sum changes).
+    """
     G = green(method)
     N = pos.shape[0]
     rows = np.arange(N) if rows is None else np.asarray(rows)
+    cb = N if col_block is None else int(col_block)
     out = np.empty((len(rows), 3), dtype=np.complex128)
     for s in range(0, len(rows), block):
         rb = rows[s:s + block]
-        dr = pos[rb, None, :] - pos[None, :, :]            # [b, N, 3]
-        self_mask = (rb[:, None] == np.arange(N)[None, :])
-        dr[self_mask] = 1.0                                 # placeholder, zeroed below
-        T = G(dr, kd)                                       # [b, N, 3, 3]
-        T[self_mask] = 0.0
-        field = np.einsum("bnij,nj->bi", T, P)
+        field = np.zeros((len(rb), 3), dtype=np.complex128)
+        for c0 in range(0, N, cb):
+            cols = np.arange(c0, min(N, c0 + cb))
+            dr = pos[rb, None, :] - pos[None, cols, :]          # [b, n, 3]
+            self_mask = (rb[:, None] == cols[None, :])
+            dr[self_mask] = 1.0                                 # placeholder, zeroed below
+            T = G(dr, kd)                                       # [b, n, 3, 3]
+            T[self_mask] = 0.0
+            field += np.einsum("bnij,nj->bi", T, P[cols])
         out[s:s + block] = ainv[rb, None] * P[rb] - field
     return out
 

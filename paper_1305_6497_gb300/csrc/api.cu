@@ -20,6 +20,7 @@ using cd = std::complex<double>;
 #include <atomic>
 static std::atomic<long long> g_launches{0};
 void dda::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long dda::launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
@@ -133,6 +134,7 @@ static AxisPlan make_plan(int L, std::vector<long double>& twr, std::vector<long
     P.radix[t] = R;
     P.blk[t] = B;
     P.tw_off[t] = off;
+    P.sdiv[t] = ((1ull << 36) + (unsigned long long)Sp - 1) / (unsigned long long)Sp;
     for (int j = 0; j < Sp; ++j)
       for (int m = 1; m < R; ++m) {
         const long long num = ((long long)j * m) % (long long)B;
@@ -233,6 +235,18 @@ struct Profiler {
   }
 };
 
+// An instantiated CUDA graph of one block of BiCGSTAB iterations.
+struct IterGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uintptr_t> sig;
+  long long kernels = 0;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    sig.clear();
+  }
+};
+
 struct dda_target {
   int nx = 0, ny = 0, nz = 0;
   int64_t nbox = 0, N = 0;
@@ -255,6 +269,7 @@ struct dda_target {
   bool kernels_configured = false;
   Workspace ws;
   Profiler prof;
+  IterGraph graphs[2];  // FP32, FP64
 };
 
 static int64_t octant_size(const dda_target* t) {
@@ -282,6 +297,8 @@ static OpView<T> make_view(const dda_target* t, const void* ghat, const void* ai
   v.ky_at = pm + t->Lx;
   v.kz_at = pm + t->Lx + t->Ly;
   v.px = t->px; v.py = t->py; v.pz = t->pz;
+  auto magic = [](int d) { return ((1ull << 36) + (unsigned long long)d - 1) / (unsigned long long)d; };
+  v.div_nx = magic(v.nx); v.div_ny = magic(v.ny); v.div_nz = magic(v.nz); v.div_Lx = magic(v.Lx);
   return v;
 }
 
@@ -303,6 +320,8 @@ static void build_green(dda_target* t, double kd, int filtered) {
     op.nx = t->Lx; op.ny = t->Ly; op.nz = t->Lz;
     op.nbox = M;
     op.comp = nullptr;
+    auto magic = [](int d) { return ((1ull << 36) + (unsigned long long)d - 1) / (unsigned long long)d; };
+    op.div_nx = magic(op.nx); op.div_ny = magic(op.ny); op.div_nz = magic(op.nz);
     MatvecLaunch L = plan_matvec<double>(op);
     CK(configure_matvec_kernels<double>(L));
     CK(launch_fft3d_full(op, L, 6, full.as<double2>(), tmp.as<double2>(), t->stream));
@@ -436,10 +455,9 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
   for (int a : hact) nact += a;
   int iter = 0;
   const int nblk_mv = matvec_partial_blocks<T>(op, L);
-  while (nact > 0 && iter < max_iter) {
-    // kCheckEvery iterations are queued back to back; a converged RHS is frozen
-    // on the device by its active flag, so the extra iterations cost nothing
-    const int nq = std::min(kCheckEvery, max_iter - iter);
+  // one block of nq iterations: every pointer and scalar lives in device memory,
+  // so the same launch sequence is valid for every block of the solve
+  auto enqueue_block = [&](int nq) {
     for (int q = 0; q < nq; ++q) {
       // p <- r + beta (p - omega v); v = A p; <rhat, v>
       CK(launch_matvec_p<T>(op, L, R, V.r, V.p, V.v, V.rh, V.scr, ks, part, act, st,
@@ -452,6 +470,47 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
       // x += alpha p + omega s; r = s - omega t; <rhat, r>, <r, r>
       CK(launch_update_xr<T>(n, R, V.x, V.r, V.p, V.s, V.t, V.rh, part, ks, act, st));
       CK(launch_scalar_rho(R, nblk, part, ks, act, st));
+    }
+  };
+  // A full block is captured once into a CUDA graph and replayed; the graph is
+  // rebuilt only when a pointer, the batch size or the profiling mode changes.
+  std::vector<uintptr_t> sig = {(uintptr_t)sizeof(T), (uintptr_t)R, (uintptr_t)t->prof.on,
+                                (uintptr_t)V.r, (uintptr_t)V.p, (uintptr_t)V.v,
+                                (uintptr_t)V.rh, (uintptr_t)V.s, (uintptr_t)V.t,
+                                (uintptr_t)V.x, (uintptr_t)V.scr, (uintptr_t)ks,
+                                (uintptr_t)part, (uintptr_t)act, (uintptr_t)op.ghat,
+                                (uintptr_t)op.ainv, (uintptr_t)nblk_mv, (uintptr_t)nblk};
+  IterGraph& g = t->graphs[sizeof(T) == 4 ? 0 : 1];
+  if (g.exec && g.sig != sig) g.reset();
+  if (!g.exec) {
+    const long long before = launch_count();
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue_block(kCheckEvery);
+    } catch (...) {
+      cudaGraph_t broken = nullptr;
+      cudaStreamEndCapture(st, &broken);  // leave capture mode before reporting
+      if (broken) cudaGraphDestroy(broken);
+      throw;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamEndCapture(st, &graph));
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie);
+    g.kernels = launch_count() - before;
+    note_launches(-g.kernels);  // captured, not run
+    g.sig = sig;
+  }
+  while (nact > 0 && iter < max_iter) {
+    // kCheckEvery iterations are queued back to back; a converged RHS is frozen
+    // on the device by its active flag, so the extra iterations cost nothing
+    const int nq = std::min(kCheckEvery, max_iter - iter);
+    if (nq == kCheckEvery) {
+      CK(cudaGraphLaunch(g.exec, st));
+      note_launches(g.kernels);
+    } else {
+      enqueue_block(nq);
     }
     CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -579,6 +638,8 @@ void dda_target_destroy(dda_target* t) {
   t->perm.release();
   t->g64.release(); t->g32.release();
   t->prof.destroy();
+  t->graphs[0].reset();
+  t->graphs[1].reset();
   if (t->ev0) cudaEventDestroy(t->ev0);
   if (t->ev1) cudaEventDestroy(t->ev1);
   if (t->stream) cudaStreamDestroy(t->stream);
@@ -882,7 +943,10 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
       for (int r = 0; r < R; ++r) { its_total[r] = its[r]; sweeps[r] = 1; }
     } else {
       // FP64 iterative refinement around FP32 BiCGSTAB
-      const double inner_tol = p->inner_tol > 0 ? p->inner_tol : 1e-4;
+      // inner tolerance: the caller's, or adaptive -- reduce the residual only as far
+      // as the outer target needs (half of tol / current relative residual), but no
+      // further than FP32 arithmetic can carry the inner solve (1e-5)
+      const double kInnerFloor = 1e-5;
       Vecs<float> V{w.b32.as<float2>(), w.x32.as<float2>(), w.r32.as<float2>(),
                     w.rh32.as<float2>(), w.p32.as<float2>(), w.v32.as<float2>(),
                     w.s32.as<float2>(), w.t32.as<float2>(), w.scr32.as<float2>()};
@@ -932,6 +996,14 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
         int cap = 0;
         for (int r = 0; r < R; ++r)
           if (outer_act[r]) cap = std::max(cap, p->max_iter - its_total[r]);
+        double inner_tol = p->inner_tol;
+        if (!(inner_tol > 0)) {
+          inner_tol = 1.0;
+          for (int r = 0; r < R; ++r)
+            if (outer_act[r] && rn2[r] > 0)
+              inner_tol = std::min(inner_tol, 0.5 * p->tol * std::sqrt(bn2[r] / rn2[r]));
+          inner_tol = std::max(inner_tol, kInnerFloor);
+        }
         bicgstab<float>(t, op32, t->L32, R, V, false, inner_tol, std::max(1, cap), its, st_in,
                         matvecs);
         for (int r = 0; r < R; ++r) {

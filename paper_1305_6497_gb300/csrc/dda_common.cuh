@@ -7,9 +7,9 @@
 //    y < ny, the y pass expands each (z, column) to Ly rows in place, the fused
 //    z pass transforms along z, multiplies by the Green tensor transform and
 //    transforms back in place, and the inverse y and x passes shrink back;
-//  - Green tensor transform: one octant [6][Lz/2+1][Ly/2+1][Lx/2+1] complex
-//    (components xx, xy, xz, yy, yz, zz), the rest follows from the parity of
-//    each component in each axis.
+//  - Green tensor transform: one octant [Lz/2+1][Ly/2+1][Lx/2+1][6] complex
+//    (components xx, xy, xz, yy, yz, zz side by side), the rest follows from
+//    the parity of each component in each axis.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -66,8 +66,15 @@ struct AxisPlan {
   int radix[kMaxStages];
   int blk[kMaxStages];
   int tw_off[kMaxStages];
+  unsigned long long sdiv[kMaxStages];  // ceil(2^36 / span): q / span = (q * sdiv) >> 36
   int tw_len;
 };
+
+// q / d with m = ceil(2^36 / d): exact whenever q d <= 2^36, since m d - 2^36
+// is below d.
+__host__ __device__ __forceinline__ int fast_div(int q, unsigned long long m) {
+  return (int)(((unsigned long long)q * m) >> 36);
+}
 
 // Everything a matvec kernel needs about one target's operator.
 template <typename T> struct OpView {
@@ -77,13 +84,35 @@ template <typename T> struct OpView {
   int Hx, Hy, Hz;                 // octant sizes L/2 + 1
   int64_t nbox;                   // nx*ny*nz
   const uint8_t* comp;            // [nbox] 0 = vacant, else composition 1..ncomp
-  const C* ghat;                  // [6][Hz][Hy][Hx], already divided by Lx*Ly*Lz
+  const C* ghat;                  // [Hz][Hy][Hx][6], already divided by Lx*Ly*Lz
   const C* ainv;                  // [R][ncomp+1] alpha^{-1} per RHS, entry 0 unused
   int ncomp1;                     // ncomp + 1
   const C* twx; const C* twy; const C* twz;
   const int* kx_at; const int* ky_at; const int* kz_at;  // frequency held at each
                                                           // digit-reversed position
+  unsigned long long div_nx, div_ny, div_nz, div_Lx;     // fast_div magics
   AxisPlan px, py, pz;
 };
+
+// ---- asynchronous global -> shared copies (cp.async) ------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+// BYTES = 4, 8 or 16; both addresses aligned to BYTES
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst_smem, const void* src_gmem) {
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst_smem)),
+                 "l"(src_gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst_smem)),
+                 "l"(src_gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 
 }  // namespace dda

@@ -13,7 +13,7 @@ void note_launch();
 long long launch_count();
 
 struct MatvecLaunch {
-  int x_lines, x_threads; size_t x_smem;
+  int x_lines, x_threads; size_t x_smem, xinv_smem;
   int y_tile, y_threads; size_t y_smem;
   int z_tile, z_ps, z_threads; size_t z_smem;
 };
@@ -21,7 +21,8 @@ struct MatvecLaunch {
 template <typename T> MatvecLaunch plan_matvec(const OpView<T>& op);
 template <typename T> cudaError_t configure_matvec_kernels(const MatvecLaunch& L);
 // y = A x for R right-hand sides (box layout); scratch holds R*3*nz*Ly*Lx.
-// With ev (6 events), the five passes are bracketed by events for profiling.
+// With ev (6 events), the five passes are bracketed by events for profiling
+// (recorded as external events, so they also time passes inside CUDA graphs).
 constexpr int kMatvecPasses = 5;
 template <typename T>
 cudaError_t launch_matvec(const OpView<T>& op, const MatvecLaunch& L, int R,

@@ -152,12 +152,12 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C (&v
 // ---- one in-place stage ------------------------------------------------------
 template <typename C, int R, bool INV>
 __device__ __forceinline__ void fft_stage(C* s, int nlines, int pstride, int L, int B,
-                                          const C* __restrict__ tw) {
+                                          unsigned long long sdiv, const C* __restrict__ tw) {
   const int S = B / R;
   const int nb = nlines * (L / R);
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     const int line = b % nlines, q = b / nlines;
-    const int blk = q / S, j = q - blk * S;
+    const int blk = fast_div(q, sdiv), j = q - blk * S;
     C* base = s + (blk * B + j) * pstride + line;
     C v[R];
 #pragma unroll
@@ -204,7 +204,7 @@ __device__ __forceinline__ void fft_stage(C* s, int nlines, int pstride, int L, 
 template <typename C, bool INV, int R>
 __device__ __forceinline__ void run_stage(C* s, int nlines, int pstride, const AxisPlan& P,
                                           int st, const C* __restrict__ tw) {
-  fft_stage<C, R, INV>(s, nlines, pstride, P.L, P.blk[st], tw + P.tw_off[st]);
+  fft_stage<C, R, INV>(s, nlines, pstride, P.L, P.blk[st], P.sdiv[st], tw + P.tw_off[st]);
 }
 
 // Full transform of `nlines` lines in shared memory, in place.  Forward: natural

@@ -253,8 +253,8 @@ __global__ void k_green_octant(int Lx, int Ly, int Lz, const int* __restrict__ p
     const int hy = (int)(q % Hy), hz = (int)(q / Hy);
     const double2 v = full[c * M + ((int64_t)posz[hz] * Ly + posy[hy]) * Lx + posx[hx]];
     const double2 w = make_double2(v.x * inv, v.y * inv);
-    g64[i] = w;
-    g32[i] = make_float2((float)w.x, (float)w.y);
+    g64[6 * o + c] = w;  // the six components of a point side by side
+    g32[6 * o + c] = make_float2((float)w.x, (float)w.y);
   }
 }
 

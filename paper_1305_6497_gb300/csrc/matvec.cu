@@ -37,7 +37,7 @@ template <typename T> struct XinArgs {
 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpView<T> op, const cplx_t<T>* __restrict__ in,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_fwd(OpView<T> op, const cplx_t<T>* __restrict__ in,
                             cplx_t<T>* __restrict__ buf, int nlines,
                             const int* __restrict__ active, XinArgs<T> xa) {
   using C = cplx_t<T>;
@@ -57,12 +57,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpVie
   } else if (MODE == XIN_S) {
     c1 = mk<C>(xa.ks[r].alpha.x, xa.ks[r].alpha.y);
   }
+  // the CTA's rows are one contiguous chunk of the box vector
+  const int nin = min(nlines, rows - row0) * nx;
+  const int64_t g0 = off + (int64_t)row0 * nx;
+#pragma unroll 4
   for (int e = threadIdx.x; e < nlines * nx; e += blockDim.x) {
-    const int line = e / nx, p = e - line * nx;
-    const int row = row0 + line;
+    const int line = fast_div(e, op.div_nx), p = e - line * nx;
     C val = mk<C>(0, 0);
-    if (row < rows) {
-      const int64_t g = off + (int64_t)row * nx + p;
+    if (e < nin) {
+      const int64_t g = g0 + e;
       if (MODE == XIN_PLAIN) {
         val = in[g];
       } else if (MODE == XIN_P) {
@@ -83,11 +86,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpVie
   fft_smem<C, false>(s, nlines, ps, op.px, op.twx);
   const int64_t plane_sz = (int64_t)op.Ly * Lx;
   C* dst = buf + (int64_t)r * 3 * op.nz * plane_sz;
+#pragma unroll 4
   for (int e = threadIdx.x; e < nlines * Lx; e += blockDim.x) {
-    const int line = e / Lx, p = e - line * Lx;
+    const int line = fast_div(e, op.div_Lx), p = e - line * Lx;
     const int row = row0 + line;
     if (row < rows) {
-      const int plane = row / op.ny, y = row - plane * op.ny;
+      const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
       dst[plane * plane_sz + (int64_t)y * Lx + p] = s[p * ps + line];
     }
   }
@@ -151,40 +155,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_y(OpView<T>
 // The last forward stage, the multiply and the first inverse stage run in
 // registers for all three components of one butterfly.
 // --------------------------------------------------------------------------
-// Octant index of frequency (kx, ky, kz) and the reflections applied per axis.
-template <typename T>
-__device__ __forceinline__ void ghat_index(const OpView<T>& op, int kx, int ky, int kz,
-                                           int64_t& idx, bool& fx, bool& fy, bool& fz) {
-  fx = kx > (op.Lx >> 1); fy = ky > (op.Ly >> 1); fz = kz > (op.Lz >> 1);
-  const int hx = fx ? op.Lx - kx : kx;
-  const int hy = fy ? op.Ly - ky : ky;
-  const int hz = fz ? op.Lz - kz : kz;
-  idx = ((int64_t)hz * op.Hy + hy) * op.Hx + hx;
-}
-
-template <typename T>
-__device__ __forceinline__ void ghat_apply(const OpView<T>& op, int kx, int ky, int kz,
-                                           cplx_t<T>& x0, cplx_t<T>& x1, cplx_t<T>& x2) {
-  using C = cplx_t<T>;
-  int64_t gi; bool fx, fy, fz;
-  ghat_index(op, kx, ky, kz, gi, fx, fy, fz);
-  const int64_t gs = (int64_t)op.Hz * op.Hy * op.Hx;
-  const C gxx = __ldg(&op.ghat[gi]);
-  C gxy = __ldg(&op.ghat[gi + gs]);
-  C gxz = __ldg(&op.ghat[gi + 2 * gs]);
-  const C gyy = __ldg(&op.ghat[gi + 3 * gs]);
-  C gyz = __ldg(&op.ghat[gi + 4 * gs]);
-  const C gzz = __ldg(&op.ghat[gi + 5 * gs]);
-  // odd components change sign under the reflection of an odd axis
-  if (fx != fy) { gxy.x = -gxy.x; gxy.y = -gxy.y; }
-  if (fx != fz) { gxz.x = -gxz.x; gxz.y = -gxz.y; }
-  if (fy != fz) { gyz.x = -gyz.x; gyz.y = -gyz.y; }
-  const C a = x0, b = x1, c = x2;
-  x0 = cadd(cadd(cmul(gxx, a), cmul(gxy, b)), cmul(gxz, c));
-  x1 = cadd(cadd(cmul(gxy, a), cmul(gyy, b)), cmul(gyz, c));
-  x2 = cadd(cadd(cmul(gxz, a), cmul(gyz, b)), cmul(gzz, c));
-}
-
 template <typename C> struct ZIO {
   C* base;          // component 0, row 0, first column of the tile
   int64_t comp_sz;  // elements between components
@@ -200,55 +170,122 @@ template <typename C> struct ZIO {
   }
 };
 
+// The six components of Ghat at octant point o are stored together,
+// ghat[6 o .. 6 o + 5] = xx, xy, xz, yy, yz, zz (48 B in FP32, 96 B in FP64).
+template <typename T> struct G6;
+template <> struct G6<float> {
+  static __device__ __forceinline__ void load_smem(const float2* g, float2 (&v)[6]) {
+    const float4* q = reinterpret_cast<const float4*>(g);
+    const float4 a = q[0], b = q[1], c = q[2];
+    v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+    v[4] = make_float2(c.x, c.y); v[5] = make_float2(c.z, c.w);
+  }
+  static __device__ __forceinline__ void load(const float2* g, float2 (&v)[6]) {
+    const float4* q = reinterpret_cast<const float4*>(g);
+    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+    v[4] = make_float2(c.x, c.y); v[5] = make_float2(c.z, c.w);
+  }
+};
+template <> struct G6<double> {
+  static __device__ __forceinline__ void load_smem(const double2* g, double2 (&v)[6]) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = g[i];
+  }
+  static __device__ __forceinline__ void load(const double2* g, double2 (&v)[6]) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = __ldg(g + i);
+  }
+};
+
 // last forward stage + multiply + first inverse stage (block = R, span 1).  A
 // thread owns R consecutive positions of one column for all three components;
 // it transforms each component in registers and leaves it in place, multiplies
 // position by position, and transforms back -- no barrier is needed between
 // these steps because no other thread touches those positions.
-template <typename T, int R>
-__device__ __forceinline__ void z_mid(cplx_t<T>* s, int tile, int ps, int ncol, int col0,
-                                      int ky, const OpView<T>& op) {
+template <typename T, int R, int TILE>
+__device__ __forceinline__ void z_mid(cplx_t<T>* s, int ps, int ncol, int col0, bool fy,
+                                      const cplx_t<T>* gs, const OpView<T>& op) {
   using C = cplx_t<T>;
-  const int nb = tile * (op.Lz / R);
+  const int nb = TILE * (op.Lz / R);
+  const int hz_half = op.Lz >> 1;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    const int t = b % tile, blk = b / tile;
+    const int t = b % TILE, blk = b / TILE;
     C* q = s + (blk * R) * ps + t;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       C v[R];
 #pragma unroll
-      for (int i = 0; i < R; ++i) v[i] = q[i * ps + c * tile];
+      for (int i = 0; i < R; ++i) v[i] = q[i * ps + c * TILE];
       dft<R, false>(v);
 #pragma unroll
-      for (int i = 0; i < R; ++i) q[i * ps + c * tile] = v[i];
+      for (int i = 0; i < R; ++i) q[i * ps + c * TILE] = v[i];
     }
     if (t < ncol) {
       const int kx = op.kx_at[col0 + t];
-#pragma unroll 1
+      const bool fx = kx > (op.Lx >> 1);
+#pragma unroll
       for (int i = 0; i < R; ++i) {
+        const int kz = op.kz_at[blk * R + i];
+        const bool fz = kz > hz_half;
+        const int hz = fz ? op.Lz - kz : kz;
+        C g[6];
+        G6<T>::load_smem(gs + 6 * (hz * TILE + t), g);
+        // odd components change sign under the reflection of an odd axis
+        if (fx != fy) { g[1].x = -g[1].x; g[1].y = -g[1].y; }
+        if (fx != fz) { g[2].x = -g[2].x; g[2].y = -g[2].y; }
+        if (fy != fz) { g[4].x = -g[4].x; g[4].y = -g[4].y; }
         C* w = q + i * ps;
-        C a = w[0], bb = w[tile], c = w[2 * tile];
-        ghat_apply<T>(op, kx, ky, op.kz_at[blk * R + i], a, bb, c);
-        w[0] = a; w[tile] = bb; w[2 * tile] = c;
+        const C a = w[0], bb = w[TILE], c = w[2 * TILE];
+        w[0] = cadd(cadd(cmul(g[0], a), cmul(g[1], bb)), cmul(g[2], c));
+        w[TILE] = cadd(cadd(cmul(g[1], a), cmul(g[3], bb)), cmul(g[4], c));
+        w[2 * TILE] = cadd(cadd(cmul(g[2], a), cmul(g[4], bb)), cmul(g[5], c));
       }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       C v[R];
 #pragma unroll
-      for (int i = 0; i < R; ++i) v[i] = q[i * ps + c * tile];
+      for (int i = 0; i < R; ++i) v[i] = q[i * ps + c * TILE];
       dft<R, true>(v);
 #pragma unroll
-      for (int i = 0; i < R; ++i) q[i * ps + c * tile] = v[i];
+      for (int i = 0; i < R; ++i) q[i * ps + c * TILE] = v[i];
     }
   }
   __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf,
-                                                   int tile, int ps,
-                                                   const int* __restrict__ active) {
+// Start copying the CTA's Ghat tile -- rows hz = 0..Lz/2 of the octant for its
+// fixed ky and its TILE columns, gs[6 (hz TILE + t) + c] -- into shared memory
+// with cp.async; it lands while the forward z transform runs.
+template <typename T, int TILE>
+__device__ __forceinline__ void ghat_tile_async(const OpView<T>& op, cplx_t<T>* gs, int col0,
+                                                int ncol, int hy) {
+  constexpr int CH = 6 * (int)sizeof(cplx_t<T>) / 16;  // 16-byte chunks per point
+  const int n = op.Hz * TILE * CH;
+  const int64_t plane = (int64_t)op.Hy * op.Hx;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int ch = e % CH, pt = e / CH;
+    const int t = pt % TILE, hz = pt / TILE;
+    if (t < ncol) {
+      const int kx = op.kx_at[col0 + t];
+      const int hx = kx > (op.Lx >> 1) ? op.Lx - kx : kx;
+      const char* src = reinterpret_cast<const char*>(
+          op.ghat + 6 * (hz * plane + (int64_t)hy * op.Hx + hx)) + 16 * ch;
+      char* dst = reinterpret_cast<char*>(gs + 6 * (hz * TILE + t)) + 16 * ch;
+      cp_async<16>(dst, src);
+    }
+  }
+  cp_async_commit();
+}
+
+// grid: (column tiles, Ly, R).  Shared memory: Lz x ps, lines c * TILE + t,
+// then the Ghat tile (16-byte aligned).
+template <typename T, int TILE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __restrict__ active) {
   using C = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
@@ -257,43 +294,56 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_z_mul(OpVie
   const int Lx = op.Lx, Ly = op.Ly, Lz = op.Lz, nz = op.nz;
   const int pyy = blockIdx.y;
   const int ky = op.ky_at[pyy];
-  const int col0 = blockIdx.x * tile;
-  const int ncol = min(tile, Lx - col0);
-  const int nl = 3 * tile;
+  const bool fy = ky > (Ly >> 1);
+  const int hy = fy ? Ly - ky : ky;
+  const int col0 = blockIdx.x * TILE;
+  const int ncol = min(TILE, Lx - col0);
+  constexpr int NL = 3 * TILE;
   const int64_t plane_sz = (int64_t)Ly * Lx;
   const int64_t comp_sz = (int64_t)nz * plane_sz;
   C* base = buf + (int64_t)r * 3 * comp_sz + (int64_t)pyy * Lx + col0;
-  ZIO<C> io{base, comp_sz, plane_sz, tile, ncol, nz};
+  ZIO<C> io{base, comp_sz, plane_sz, TILE, ncol, nz};
+  C* gs = reinterpret_cast<C*>(smem_raw + (((size_t)Lz * ps * sizeof(C) + 15) & ~(size_t)15));
+  ghat_tile_async<T, TILE>(op, gs, col0, ncol, hy);
   const AxisPlan& P = op.pz;
   const int last = P.nstage - 1;
   if (P.nstage >= 2) {
-    DDA_RADIX_DISPATCH(P.radix[0], (stage_first_fwd<C, RR>(s, nl, ps, Lz, op.twz, io)));
-    fft_inner_stages<C, false>(s, nl, ps, P, op.twz);
+    DDA_RADIX_DISPATCH(P.radix[0], (stage_first_fwd<C, RR>(s, NL, ps, Lz, op.twz, io)));
+    fft_inner_stages<C, false>(s, NL, ps, P, op.twz);
   } else {
-    for (int e = threadIdx.x; e < Lz * nl; e += blockDim.x) {
-      const int p = e / nl, l = e - p * nl;
+    for (int e = threadIdx.x; e < Lz * NL; e += blockDim.x) {
+      const int p = e / NL, l = e - p * NL;
       s[p * ps + l] = io(l, p);
     }
-    __syncthreads();
   }
+  cp_async_wait_all();
+  __syncthreads();
   if (P.nstage >= 1) {
     // the plan puts a radix <= 8 last
-    DDA_RADIX_DISPATCH_SMALL(P.radix[last], (z_mid<T, RR>(s, tile, ps, ncol, col0, ky, op)));
-  } else {  // Lz = 1
+    DDA_RADIX_DISPATCH_SMALL(P.radix[last], (z_mid<T, RR, TILE>(s, ps, ncol, col0, fy, gs, op)));
+  } else {  // Lz = 1: multiply only
     for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
-      C* q = s + t;
-      C a = q[0], b = q[tile], c = q[2 * tile];
-      ghat_apply<T>(op, op.kx_at[col0 + t], ky, 0, a, b, c);
-      q[0] = a; q[tile] = b; q[2 * tile] = c;
+      const int kx = op.kx_at[col0 + t];
+      const bool fx = kx > (Lx >> 1);
+      C g[6];
+      G6<T>::load_smem(gs + 6 * t, g);
+      if (fx != fy) { g[1].x = -g[1].x; g[1].y = -g[1].y; }
+      if (fx) { g[2].x = -g[2].x; g[2].y = -g[2].y; }
+      if (fy) { g[4].x = -g[4].x; g[4].y = -g[4].y; }
+      C* w = s + t;
+      const C a = w[0], bb = w[TILE], c = w[2 * TILE];
+      w[0] = cadd(cadd(cmul(g[0], a), cmul(g[1], bb)), cmul(g[2], c));
+      w[TILE] = cadd(cadd(cmul(g[1], a), cmul(g[3], bb)), cmul(g[4], c));
+      w[2 * TILE] = cadd(cadd(cmul(g[2], a), cmul(g[4], bb)), cmul(g[5], c));
     }
     __syncthreads();
   }
   if (P.nstage >= 2) {
-    fft_inner_stages<C, true>(s, nl, ps, P, op.twz);
-    DDA_RADIX_DISPATCH(P.radix[0], (stage_last_inv<C, RR>(s, nl, ps, Lz, op.twz, io)));
+    fft_inner_stages<C, true>(s, NL, ps, P, op.twz);
+    DDA_RADIX_DISPATCH(P.radix[0], (stage_last_inv<C, RR>(s, NL, ps, Lz, op.twz, io)));
   } else {
-    for (int e = threadIdx.x; e < Lz * nl; e += blockDim.x) {
-      const int p = e / nl, l = e - p * nl;
+    for (int e = threadIdx.x; e < Lz * NL; e += blockDim.x) {
+      const int p = e / NL, l = e - p * NL;
       io(l, p, s[p * ps + l]);
     }
   }
@@ -311,7 +361,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_z_mul(OpVie
 enum { XOUT_PLAIN = 0, XOUT_RV = 1, XOUT_TS = 2 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpView<T> op, const cplx_t<T>* __restrict__ buf,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_inv(OpView<T> op, const cplx_t<T>* __restrict__ buf,
                             const cplx_t<T>* __restrict__ xin, cplx_t<T>* __restrict__ yout,
                             int nlines, const int* __restrict__ active,
                             const cplx_t<T>* __restrict__ rhat, double* __restrict__ partials) {
@@ -326,36 +376,50 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   const int ps = nlines + 1;
   const int64_t plane_sz = (int64_t)op.Ly * Lx;
   const C* src = buf + (int64_t)r * 3 * op.nz * plane_sz;
-  for (int e = threadIdx.x; e < nlines * Lx; e += blockDim.x) {
-    const int line = e / Lx, p = e - line * Lx;
-    const int row = row0 + line;
-    C v = mk<C>(0, 0);
-    if (row < rows) {
-      const int plane = row / op.ny, y = row - plane * op.ny;
-      v = src[plane * plane_sz + (int64_t)y * Lx + p];
-    }
-    s[p * ps + line] = v;
+  // the epilogue's inputs (x, and rhat for XOUT_RV) are contiguous chunks of the
+  // box vectors: start copying them now, behind the spectral rows
+  C* sx = s + (size_t)Lx * ps;
+  C* sh = sx + (size_t)nlines * nx;
+  const int nin = min(nlines, rows - row0) * nx;
+  const int64_t g0 = ((int64_t)r * rows + row0) * nx;
+  for (int e = threadIdx.x; e < nin; e += blockDim.x) {
+    cp_async<(int)sizeof(C)>(&sx[e], &xin[g0 + e]);
+    if (MODE == XOUT_RV) cp_async<(int)sizeof(C)>(&sh[e], &rhat[g0 + e]);
   }
+  // all of the tile's loads in flight at once (asynchronous copies)
+  for (int e = threadIdx.x; e < nlines * Lx; e += blockDim.x) {
+    const int line = fast_div(e, op.div_Lx), p = e - line * Lx;
+    const int row = row0 + line;
+    if (row < rows) {
+      const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
+      cp_async<(int)sizeof(C)>(&s[p * ps + line], &src[plane * plane_sz + (int64_t)y * Lx + p]);
+    } else {
+      s[p * ps + line] = mk<C>(0, 0);
+    }
+  }
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   fft_smem<C, true>(s, nlines, ps, op.px, op.twx);
   const C* ai = op.ainv + (int64_t)r * op.ncomp1;
-  const C* xr = xin + (int64_t)r * rows * nx;
-  C* yr = yout + (int64_t)r * rows * nx;
-  const int nyz = op.ny * op.nz;
+  C* yr = yout + g0;
   ChunkAcc<T, 4> acc;
-  for (int e = threadIdx.x; e < nlines * nx; e += blockDim.x) {
-    const int line = e / nx, p = e - line * nx;
+#pragma unroll 2
+  for (int e = threadIdx.x; e < nin; e += blockDim.x) {
+    const int line = fast_div(e, op.div_nx), p = e - line * nx;
     const int row = row0 + line;
-    if (row < rows) {
-      const int64_t site = (int64_t)(row % nyz) * nx + p;
-      const int cm = op.comp[site];
-      const int64_t g = (int64_t)row * nx + p;
-      C out = mk<C>(0, 0);
-      const C xv = xr[g];
-      if (cm) out = csub(cmul(ai[cm], xv), s[p * ps + line]);
-      yr[g] = out;
+    // row = (c nz + z) ny + y  ->  site (z ny + y) nx + p
+    const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
+    const int z = plane - fast_div(plane, op.div_nz) * op.nz;
+    const int64_t site = ((int64_t)z * op.ny + y) * nx + p;
+    const int cm = op.comp[site];
+    C out = mk<C>(0, 0);
+    const C xv = sx[e];
+    if (cm) out = csub(cmul(ai[cm], xv), s[p * ps + line]);
+    yr[e] = out;
+    {
       if (MODE == XOUT_RV) {
-        const C h = rhat[(int64_t)r * rows * nx + g];
+        const C h = sh[e];
         acc.add(0, h.x * out.x + h.y * out.y);
         acc.add(1, h.x * out.y - h.y * out.x);
         acc.step();
@@ -387,26 +451,34 @@ MatvecLaunch plan_matvec(const OpView<T>& op) {
   MatvecLaunch L{};
   // x passes: 256 threads, lines of Lx points, <= 32 KB of shared memory per CTA
   int nl = 16;
-  while (nl > 1 && (size_t)nl * (op.Lx + 1) * sizeof(C) > 32 * 1024) nl >>= 1;
-  while (nl < 64 && (size_t)(2 * nl) * (op.Lx + 1) * sizeof(C) <= 16 * 1024) nl <<= 1;
+  while (nl > 1 && (size_t)nl * (op.Lx + 1) * sizeof(C) > 36 * 1024) nl >>= 1;
+  while (nl < 64 && (size_t)(2 * nl) * (op.Lx + 1) * sizeof(C) <= 36 * 1024) nl <<= 1;
   L.x_lines = nl;
   L.x_threads = 256;
   L.x_smem = (size_t)op.Lx * (nl + 1) * sizeof(C);
+  L.xinv_smem = L.x_smem + (size_t)2 * nl * op.nx * sizeof(C);  // + x and rhat chunks
   // y pass: a tile of 128 B of columns (16 FP32 / 8 FP64 complex), 256 threads
   int ty = 128 / (int)sizeof(C);
   while (ty > 2 && (size_t)ty * op.Ly * sizeof(C) > 64 * 1024) ty >>= 1;
   L.y_tile = ty;
   L.y_threads = 256;
   L.y_smem = (size_t)op.Ly * ty * sizeof(C);
-  // z pass: three components of a tile of columns; the row pitch is made odd
-  // when the tile is narrower than a half-warp's 128 B so that the butterflies
-  // of neighbouring blocks fall on different banks
-  int tz = 128 / (int)sizeof(C);
-  while (tz > 2 && (size_t)3 * tz * op.Lz * sizeof(C) > 64 * 1024) tz >>= 1;
+  // z pass: three components of a tile of 64 B of columns plus the tile's Ghat
+  // rows (octant, 6 components), halved while the CTA would need more than
+  // 64 KB; the row pitch is made odd when the tile is narrower than a
+  // half-warp's 128 B so that the butterflies of neighbouring blocks fall on
+  // different banks
+  int tz = 64 / (int)sizeof(C);
+  auto zbytes = [&](int tt) {
+    const int pps = 3 * tt + (tt * (int)sizeof(C) < 128 ? 1 : 0);
+    return (((size_t)op.Lz * pps * sizeof(C) + 15) & ~(size_t)15) +
+           (size_t)6 * op.Hz * tt * sizeof(C);
+  };
+  while (tz > 2 && zbytes(tz) > 64 * 1024) tz >>= 1;
   L.z_tile = tz;
   L.z_ps = 3 * tz + (tz * (int)sizeof(C) < 128 ? 1 : 0);
   L.z_threads = 256;
-  L.z_smem = (size_t)op.Lz * L.z_ps * sizeof(C);
+  L.z_smem = zbytes(tz);
   return L;
 }
 
@@ -427,8 +499,12 @@ cudaError_t configure_matvec_kernels(const MatvecLaunch& L) {
   e = cudaFuncSetAttribute(k_fft_y<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            200 * 1024);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fft_z_mul<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           200 * 1024);
+  const void* zk[] = {(const void*)k_fft_z_mul<T, 16>, (const void*)k_fft_z_mul<T, 8>,
+                      (const void*)k_fft_z_mul<T, 4>, (const void*)k_fft_z_mul<T, 2>};
+  for (const void* k : zk) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+  }
   return e;
 }
 
@@ -438,26 +514,40 @@ static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int
                                  const int* active, cudaStream_t st, const cudaEvent_t* ev,
                                  XinArgs<T> xa, const cplx_t<T>* rhat, double* partials) {
   const int rows = 3 * op.nz * op.ny;
-  if (ev) cudaEventRecord(ev[0], st);
+  // inside a stream capture the events must be external nodes to be recorded
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (ev) cudaStreamIsCapturing(st, &cap);
+  auto record = [&](cudaEvent_t e) {
+    if (cap == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+  };
+  if (ev) record(ev[0]);
   dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
   k_fft_x_fwd<T, XIN><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines, active, xa);
   note_launch();
-  if (ev) cudaEventRecord(ev[1], st);
+  if (ev) record(ev[1]);
   dim3 gy((op.Lx + L.y_tile - 1) / L.y_tile, 3 * op.nz, R);
   k_fft_y<T, false><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, active);
   note_launch();
-  if (ev) cudaEventRecord(ev[2], st);
-  dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
-  k_fft_z_mul<T><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_tile, L.z_ps, active);
-  note_launch();
-  if (ev) cudaEventRecord(ev[3], st);
+  if (ev) record(ev[2]);
+  {
+    dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
+    switch (L.z_tile) {
+      case 16: k_fft_z_mul<T, 16><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active); break;
+      case 8: k_fft_z_mul<T, 8><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active); break;
+      case 4: k_fft_z_mul<T, 4><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active); break;
+      default: k_fft_z_mul<T, 2><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active); break;
+    }
+    note_launch();
+  }
+  if (ev) record(ev[3]);
   k_fft_y<T, true><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, active);
   note_launch();
-  if (ev) cudaEventRecord(ev[4], st);
-  k_fft_x_inv<T, XOUT><<<gx, L.x_threads, L.x_smem, st>>>(op, scratch, x, y, L.x_lines, active,
-                                                          rhat, partials);
+  if (ev) record(ev[4]);
+  k_fft_x_inv<T, XOUT><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y, L.x_lines,
+                                                             active, rhat, partials);
   note_launch();
-  if (ev) cudaEventRecord(ev[5], st);
+  if (ev) record(ev[5]);
   return cudaGetLastError();
 }
 
