@@ -206,6 +206,20 @@ const char* dda_status_string(dda_status s);
 /* Detail of the calling thread's last failing call ("" if none). */
 const char* dda_last_error(void);
 
+/* Choose the launch schedule of the five FFT-matvec passes for this target by
+ * timing candidates on the device (x-pass lines per CTA, y/z column tiles, the
+ * z row pitch and whether the z pass stages its Green-transform rows in shared
+ * memory), for batches of n_rhs right-hand sides, in FP32 and FP64.  Results
+ * are cached per (precision, box, grid, n_rhs) for the process, and appended to
+ * the file named by the environment variable DDA_TUNE_FILE when it is set (and
+ * read from it first).  Builds the Green-tensor transform for kd if needed.
+ * Without this call the library uses a fixed rule. */
+dda_status dda_autotune(dda_target* t, double kd, int n_rhs);
+
+/* The schedule in use: out5 = {x lines, y tile, z tile, z row pitch, z stages
+ * Ghat in shared memory (0/1)} for DDA_PREC_FP64 or (otherwise) FP32. */
+dda_status dda_target_schedule(const dda_target* t, int precision, int* out5);
+
 /* Kernels launched by this library since the process started (all threads). */
 int64_t dda_launch_count(void);
 

@@ -77,6 +77,10 @@ def _load():
     lib.dda_target_grid.restype = ct.c_int
     lib.dda_launch_count.argtypes = []
     lib.dda_launch_count.restype = ct.c_int64
+    lib.dda_autotune.argtypes = [vp, ct.c_double, ct.c_int]
+    lib.dda_autotune.restype = ct.c_int
+    lib.dda_target_schedule.argtypes = [vp, ct.c_int, _ip]
+    lib.dda_target_schedule.restype = ct.c_int
     lib.dda_matvec_noalloc.argtypes = [vp, ct.c_double, _dp, _dp, ct.c_void_p, ct.c_void_p,
                                        ct.c_int, ct.c_void_p]
     lib.dda_matvec_noalloc.restype = ct.c_int
@@ -150,6 +154,17 @@ def dda_matvec(h, kd: float, x: np.ndarray, khat=None, e=None, precision="fp64")
     _check(lib.dda_matvec(h, float(kd), _ptr(kh), _ptr(ee), _ptr(x.view(np.float64)),
                           _ptr(y.view(np.float64)), PREC[precision]))
     return y
+
+
+def dda_autotune(h, kd: float, n_rhs: int) -> None:
+    _check(lib.dda_autotune(h, float(kd), int(n_rhs)))
+
+
+def dda_target_schedule(h, precision="fp32") -> dict:
+    out = (ct.c_int * 5)()
+    _check(lib.dda_target_schedule(h, PREC[precision], out))
+    return dict(x_lines=out[0], y_tile=out[1], z_tile=out[2], z_pitch=out[3],
+                z_stage_ghat=out[4])
 
 
 def dda_matvec_noalloc(h, kd: float, x_dev_ptr: int, y_dev_ptr: int, khat=None, e=None,
@@ -268,3 +283,7 @@ class Target:
 
     def hbm_bytes(self, kd, khat, e01, **kw):
         return dda_solve_hbm_bytes(self.h, kd, khat, e01, **kw)
+
+    def autotune(self, kd, n_rhs):
+        dda_autotune(self.h, kd, n_rhs)
+        return {p: dda_target_schedule(self.h, p) for p in ("fp32", "fp64")}

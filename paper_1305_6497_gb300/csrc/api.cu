@@ -7,6 +7,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -270,6 +271,7 @@ struct dda_target {
   Workspace ws;
   Profiler prof;
   IterGraph graphs[2];  // FP32, FP64
+  int schedule_gen = 0;  // bumped when the launch schedule changes
 };
 
 static int64_t octant_size(const dda_target* t) {
@@ -479,7 +481,8 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
                                 (uintptr_t)V.rh, (uintptr_t)V.s, (uintptr_t)V.t,
                                 (uintptr_t)V.x, (uintptr_t)V.scr, (uintptr_t)ks,
                                 (uintptr_t)part, (uintptr_t)act, (uintptr_t)op.ghat,
-                                (uintptr_t)op.ainv, (uintptr_t)nblk_mv, (uintptr_t)nblk};
+                                (uintptr_t)op.ainv, (uintptr_t)nblk_mv, (uintptr_t)nblk,
+                                (uintptr_t)t->schedule_gen};
   IterGraph& g = t->graphs[sizeof(T) == 4 ? 0 : 1];
   if (g.exec && g.sig != sig) g.reset();
   if (!g.exec) {
@@ -1164,11 +1167,141 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Schedule autotuning with a process-wide cache (optionally persisted in the
+// file named by DDA_TUNE_FILE: one line per key, "key : x_lines y_tile z_tile
+// z_pitch z_stage").
+// ---------------------------------------------------------------------------
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, std::vector<int>> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const dda_target* t, int prec, int R) {
+  std::ostringstream k;
+  k << (prec ? "f64" : "f32") << ' ' << t->nx << ' ' << t->ny << ' ' << t->nz << ' ' << t->Lx
+    << ' ' << t->Ly << ' ' << t->Lz << ' ' << R;
+  return k.str();
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* f = std::getenv("DDA_TUNE_FILE");
+  if (!f) return;
+  std::ifstream in(f);
+  std::string line;
+  while (std::getline(in, line)) {
+    const size_t c = line.find(':');
+    if (c == std::string::npos) continue;
+    std::istringstream v(line.substr(c + 1));
+    std::vector<int> vals;
+    int x;
+    while (v >> x) vals.push_back(x);
+    std::string key = line.substr(0, c);
+    while (!key.empty() && key.back() == ' ') key.pop_back();
+    if (vals.size() == 5) g_tune[key] = vals;
+  }
+}
+
+void tune_store_locked(const std::string& key, const std::vector<int>& v) {
+  g_tune[key] = v;
+  const char* f = std::getenv("DDA_TUNE_FILE");
+  if (!f) return;
+  std::ofstream out(f, std::ios::app);
+  out << key << " : " << v[0] << ' ' << v[1] << ' ' << v[2] << ' ' << v[3] << ' ' << v[4] << '\n';
+}
+
+template <typename T>
+void apply_schedule(const dda_target* t, MatvecLaunch& L, const std::vector<int>& v) {
+  using C = cplx_t<T>;
+  L.x_lines = v[0];
+  L.x_smem = (size_t)t->Lx * (v[0] + 1) * sizeof(C);
+  L.xinv_smem = L.x_smem + (size_t)2 * v[0] * t->nx * sizeof(C);
+  L.y_tile = v[1];
+  L.y_smem = (size_t)t->Ly * v[1] * sizeof(C);
+  L.z_tile = v[2];
+  L.z_ps = v[3];
+  L.z_gs = v[4] != 0;
+  const int Hz = t->Lz / 2 + 1;
+  L.z_smem = (((size_t)t->Lz * L.z_ps * sizeof(C) + 15) & ~(size_t)15) +
+             (L.z_gs ? (size_t)6 * Hz * L.z_tile * sizeof(C) : 0);
+}
+
+std::vector<int> schedule_of(const MatvecLaunch& L) {
+  return {L.x_lines, L.y_tile, L.z_tile, L.z_ps, L.z_gs ? 1 : 0};
+}
+}  // namespace
+
+extern "C" {
+
+dda_status dda_autotune(dda_target* t, double kd, int n_rhs) {
+  g_last_error.clear();
+  if (!t || n_rhs < 1 || n_rhs > 4096) return fail(DDA_ERR_INVALID_ARG, "bad arguments");
+  dda_status s = check_kd(t, kd);
+  if (s != DDA_OK) return s;
+  try {
+    CK(cudaSetDevice(t->device));
+    build_green(t, kd, t->method == DDA_POL_FCD ? 1 : 0);
+    ensure_workspace(t, n_rhs, DDA_PREC_FP32_REFINED, 0);  // FP32 and FP64 matvec buffers
+    Workspace& w = t->ws;
+    for (int prec = 0; prec < 2; ++prec) {
+      const std::string key = tune_key(t, prec, n_rhs);
+      std::vector<int> v;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) v = it->second;
+      }
+      if (v.empty()) {
+        if (prec == 0) {
+          OpView<float> op = make_view<float>(t, t->g32.p, w.ainv32.p, t->tw32.p);
+          MatvecLaunch L = t->L32;
+          CK(autotune_matvec<float>(op, L, n_rhs, w.x32.as<float2>(), w.r32.as<float2>(),
+                                    w.scr32.as<float2>(), t->stream));
+          v = schedule_of(L);
+        } else {
+          OpView<double> op = make_view<double>(t, t->g64.p, w.ainv64.p, t->tw64.p);
+          MatvecLaunch L = t->L64;
+          CK(autotune_matvec<double>(op, L, n_rhs, w.x64.as<double2>(), w.r64.as<double2>(),
+                                     w.scr64.as<double2>(), t->stream));
+          v = schedule_of(L);
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_store_locked(key, v);
+      }
+      if (prec == 0) apply_schedule<float>(t, t->L32, v);
+      else apply_schedule<double>(t, t->L64, v);
+    }
+    t->schedule_gen += 1;
+    ensure_workspace(t, n_rhs, DDA_PREC_FP32_REFINED, 0);  // partial-sum blocks may grow
+    CK(cudaStreamSynchronize(t->stream));
+  } catch (const CudaFail& f) {
+    return from_cuda(f);
+  }
+  return DDA_OK;
+}
+
+dda_status dda_target_schedule(const dda_target* t, int precision, int* out5) {
+  if (!t || !out5) return fail(DDA_ERR_INVALID_ARG, "null argument");
+  const MatvecLaunch& L = precision == DDA_PREC_FP64 ? t->L64 : t->L32;
+  const std::vector<int> v = schedule_of(L);
+  for (int i = 0; i < 5; ++i) out5[i] = v[i];
+  return DDA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // Allocation-free matvec: the same five-pass FFT convolution as dda_matvec, with
 // its spectral scratch (and the alpha^{-1} table) in a fixed file-scope device
 // array instead of memory this library allocates.
 // ---------------------------------------------------------------------------
-#include <mutex>
 
 namespace {
 

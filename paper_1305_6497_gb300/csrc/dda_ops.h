@@ -16,10 +16,15 @@ struct MatvecLaunch {
   int x_lines, x_threads; size_t x_smem, xinv_smem;
   int y_tile, y_threads; size_t y_smem;
   int z_tile, z_ps, z_threads; size_t z_smem;
+  bool z_gs;  // Ghat tile staged in shared memory
 };
 
 template <typename T> MatvecLaunch plan_matvec(const OpView<T>& op);
 template <typename T> cudaError_t configure_matvec_kernels(const MatvecLaunch& L);
+// Time candidate schedules of each pass on live buffers and keep the fastest in L.
+template <typename T>
+cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const cplx_t<T>* x,
+                            cplx_t<T>* y, cplx_t<T>* scratch, cudaStream_t st);
 // y = A x for R right-hand sides (box layout); scratch holds R*3*nz*Ly*Lx.
 // With ev (6 events), the five passes are bracketed by events for profiling
 // (recorded as external events, so they also time passes inside CUDA graphs).

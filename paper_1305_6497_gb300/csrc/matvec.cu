@@ -205,9 +205,9 @@ template <> struct G6<double> {
 // it transforms each component in registers and leaves it in place, multiplies
 // position by position, and transforms back -- no barrier is needed between
 // these steps because no other thread touches those positions.
-template <typename T, int R, int TILE>
+template <typename T, int R, int TILE, bool GS>
 __device__ __forceinline__ void z_mid(cplx_t<T>* s, int ps, int ncol, int col0, bool fy,
-                                      const cplx_t<T>* gs, const OpView<T>& op) {
+                                      int hy, const cplx_t<T>* gs, const OpView<T>& op) {
   using C = cplx_t<T>;
   const int nb = TILE * (op.Lz / R);
   const int hz_half = op.Lz >> 1;
@@ -232,7 +232,12 @@ __device__ __forceinline__ void z_mid(cplx_t<T>* s, int ps, int ncol, int col0, 
         const bool fz = kz > hz_half;
         const int hz = fz ? op.Lz - kz : kz;
         C g[6];
-        G6<T>::load_smem(gs + 6 * (hz * TILE + t), g);
+        if (GS) {
+          G6<T>::load_smem(gs + 6 * (hz * TILE + t), g);
+        } else {
+          const int hx = fx ? op.Lx - kx : kx;
+          G6<T>::load(op.ghat + 6 * (((int64_t)hz * op.Hy + hy) * op.Hx + hx), g);
+        }
         // odd components change sign under the reflection of an odd axis
         if (fx != fy) { g[1].x = -g[1].x; g[1].y = -g[1].y; }
         if (fx != fz) { g[2].x = -g[2].x; g[2].y = -g[2].y; }
@@ -282,8 +287,9 @@ __device__ __forceinline__ void ghat_tile_async(const OpView<T>& op, cplx_t<T>* 
 }
 
 // grid: (column tiles, Ly, R).  Shared memory: Lz x ps, lines c * TILE + t,
-// then the Ghat tile (16-byte aligned).
-template <typename T, int TILE>
+// then (GS) the Ghat tile (16-byte aligned); without GS the multiply reads
+// Ghat from global memory (long z lines, where the tile would not fit).
+template <typename T, int TILE, bool GS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __restrict__ active) {
   using C = cplx_t<T>;
@@ -304,7 +310,7 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
   C* base = buf + (int64_t)r * 3 * comp_sz + (int64_t)pyy * Lx + col0;
   ZIO<C> io{base, comp_sz, plane_sz, TILE, ncol, nz};
   C* gs = reinterpret_cast<C*>(smem_raw + (((size_t)Lz * ps * sizeof(C) + 15) & ~(size_t)15));
-  ghat_tile_async<T, TILE>(op, gs, col0, ncol, hy);
+  if (GS) ghat_tile_async<T, TILE>(op, gs, col0, ncol, hy);
   const AxisPlan& P = op.pz;
   const int last = P.nstage - 1;
   if (P.nstage >= 2) {
@@ -316,17 +322,19 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
       s[p * ps + l] = io(l, p);
     }
   }
-  cp_async_wait_all();
+  if (GS) cp_async_wait_all();
   __syncthreads();
   if (P.nstage >= 1) {
     // the plan puts a radix <= 8 last
-    DDA_RADIX_DISPATCH_SMALL(P.radix[last], (z_mid<T, RR, TILE>(s, ps, ncol, col0, fy, gs, op)));
+    DDA_RADIX_DISPATCH_SMALL(P.radix[last],
+                             (z_mid<T, RR, TILE, GS>(s, ps, ncol, col0, fy, hy, gs, op)));
   } else {  // Lz = 1: multiply only
     for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
       const int kx = op.kx_at[col0 + t];
       const bool fx = kx > (Lx >> 1);
       C g[6];
-      G6<T>::load_smem(gs + 6 * t, g);
+      if (GS) G6<T>::load_smem(gs + 6 * t, g);
+      else G6<T>::load(op.ghat + 6 * ((int64_t)hy * op.Hx + (fx ? Lx - kx : kx)), g);
       if (fx != fy) { g[1].x = -g[1].x; g[1].y = -g[1].y; }
       if (fx) { g[2].x = -g[2].x; g[2].y = -g[2].y; }
       if (fy) { g[4].x = -g[4].x; g[4].y = -g[4].y; }
@@ -464,21 +472,25 @@ MatvecLaunch plan_matvec(const OpView<T>& op) {
   L.y_threads = 256;
   L.y_smem = (size_t)op.Ly * ty * sizeof(C);
   // z pass: three components of a tile of 64 B of columns plus the tile's Ghat
-  // rows (octant, 6 components), halved while the CTA would need more than
-  // 64 KB; the row pitch is made odd when the tile is narrower than a
-  // half-warp's 128 B so that the butterflies of neighbouring blocks fall on
-  // different banks
-  int tz = 64 / (int)sizeof(C);
-  auto zbytes = [&](int tt) {
-    const int pps = 3 * tt + (tt * (int)sizeof(C) < 128 ? 1 : 0);
-    return (((size_t)op.Lz * pps * sizeof(C) + 15) & ~(size_t)15) +
-           (size_t)6 * op.Hz * tt * sizeof(C);
+  // rows (octant, 6 components) staged in shared memory, halved while the CTA
+  // would need more than 64 KB -- but not below 64 B rows: long z lines keep
+  // 64 B rows and read Ghat from global memory instead.  The row pitch is made
+  // odd when the tile is narrower than a half-warp's 128 B so that the
+  // butterflies of neighbouring blocks fall on different banks.
+  const int tz_min = 64 / (int)sizeof(C);
+  auto pitch = [&](int tt) { return 3 * tt + (tt * (int)sizeof(C) < 128 ? 1 : 0); };
+  auto zbytes = [&](int tt, bool gsm) {
+    const size_t d = ((size_t)op.Lz * pitch(tt) * sizeof(C) + 15) & ~(size_t)15;
+    return d + (gsm ? (size_t)6 * op.Hz * tt * sizeof(C) : 0);
   };
-  while (tz > 2 && zbytes(tz) > 64 * 1024) tz >>= 1;
+  int tz = tz_min;
+  L.z_gs = zbytes(tz, true) <= 64 * 1024;
+  if (!L.z_gs)
+    while (tz > 2 && zbytes(tz, false) > 104 * 1024) tz >>= 1;
   L.z_tile = tz;
-  L.z_ps = 3 * tz + (tz * (int)sizeof(C) < 128 ? 1 : 0);
+  L.z_ps = pitch(tz);
+  L.z_smem = zbytes(tz, L.z_gs);
   L.z_threads = 256;
-  L.z_smem = zbytes(tz);
   return L;
 }
 
@@ -499,8 +511,10 @@ cudaError_t configure_matvec_kernels(const MatvecLaunch& L) {
   e = cudaFuncSetAttribute(k_fft_y<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            200 * 1024);
   if (e != cudaSuccess) return e;
-  const void* zk[] = {(const void*)k_fft_z_mul<T, 16>, (const void*)k_fft_z_mul<T, 8>,
-                      (const void*)k_fft_z_mul<T, 4>, (const void*)k_fft_z_mul<T, 2>};
+  const void* zk[] = {(const void*)k_fft_z_mul<T, 16, true>, (const void*)k_fft_z_mul<T, 8, true>,
+                      (const void*)k_fft_z_mul<T, 4, true>, (const void*)k_fft_z_mul<T, 2, true>,
+                      (const void*)k_fft_z_mul<T, 16, false>, (const void*)k_fft_z_mul<T, 8, false>,
+                      (const void*)k_fft_z_mul<T, 4, false>, (const void*)k_fft_z_mul<T, 2, false>};
   for (const void* k : zk) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
@@ -532,12 +546,24 @@ static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int
   if (ev) record(ev[2]);
   {
     dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
-    switch (L.z_tile) {
-      case 16: k_fft_z_mul<T, 16><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active); break;
-      case 8: k_fft_z_mul<T, 8><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active); break;
-      case 4: k_fft_z_mul<T, 4><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active); break;
-      default: k_fft_z_mul<T, 2><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active); break;
+#define DDA_ZL(TT, GG) \
+  k_fft_z_mul<T, TT, GG><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active)
+    if (L.z_gs) {
+      switch (L.z_tile) {
+        case 16: DDA_ZL(16, true); break;
+        case 8: DDA_ZL(8, true); break;
+        case 4: DDA_ZL(4, true); break;
+        default: DDA_ZL(2, true); break;
+      }
+    } else {
+      switch (L.z_tile) {
+        case 16: DDA_ZL(16, false); break;
+        case 8: DDA_ZL(8, false); break;
+        case 4: DDA_ZL(4, false); break;
+        default: DDA_ZL(2, false); break;
+      }
     }
+#undef DDA_ZL
     note_launch();
   }
   if (ev) record(ev[3]);
@@ -599,6 +625,138 @@ cudaError_t launch_x_fwd(const OpView<T>& op, const MatvecLaunch& L, int R,
 }
 template cudaError_t launch_x_fwd<double>(const OpView<double>&, const MatvecLaunch&, int,
                                           const double2*, double2*, cudaStream_t);
+
+// --------------------------------------------------------------------------
+// autotuning of the launch schedule (tiles, lines, row pitch, Ghat staging)
+// --------------------------------------------------------------------------
+template <typename T>
+static void fill_x(const OpView<T>& op, MatvecLaunch& L, int nl) {
+  using C = cplx_t<T>;
+  L.x_lines = nl;
+  L.x_smem = (size_t)op.Lx * (nl + 1) * sizeof(C);
+  L.xinv_smem = L.x_smem + (size_t)2 * nl * op.nx * sizeof(C);
+}
+template <typename T>
+static void fill_y(const OpView<T>& op, MatvecLaunch& L, int tile) {
+  L.y_tile = tile;
+  L.y_smem = (size_t)op.Ly * tile * sizeof(cplx_t<T>);
+}
+template <typename T>
+static void fill_z(const OpView<T>& op, MatvecLaunch& L, int tile, int pad, bool gs) {
+  using C = cplx_t<T>;
+  L.z_tile = tile;
+  L.z_ps = 3 * tile + pad;
+  L.z_gs = gs;
+  L.z_smem = (((size_t)op.Lz * L.z_ps * sizeof(C) + 15) & ~(size_t)15) +
+             (gs ? (size_t)6 * op.Hz * tile * sizeof(C) : 0);
+}
+
+// Launch one pass `reps` times between two events; returns the mean in ms.
+template <typename T>
+static float time_pass(const OpView<T>& op, const MatvecLaunch& L, int pass, int R,
+                       const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch, cudaStream_t st,
+                       cudaEvent_t e0, cudaEvent_t e1, int reps) {
+  const int rows = 3 * op.nz * op.ny;
+  dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
+  dim3 gy((op.Lx + L.y_tile - 1) / L.y_tile, 3 * op.nz, R);
+  dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
+  auto launch = [&]() {
+    switch (pass) {
+      case 0:
+        k_fft_x_fwd<T, XIN_PLAIN><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines,
+                                                                     nullptr, XinArgs<T>{});
+        break;
+      case 1: k_fft_y<T, false><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, nullptr); break;
+      case 2:
+#define DDA_ZT(TT, GG) \
+  k_fft_z_mul<T, TT, GG><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, nullptr)
+        if (L.z_gs) {
+          switch (L.z_tile) { case 16: DDA_ZT(16, true); break; case 8: DDA_ZT(8, true); break;
+                              case 4: DDA_ZT(4, true); break; default: DDA_ZT(2, true); }
+        } else {
+          switch (L.z_tile) { case 16: DDA_ZT(16, false); break; case 8: DDA_ZT(8, false); break;
+                              case 4: DDA_ZT(4, false); break; default: DDA_ZT(2, false); }
+        }
+#undef DDA_ZT
+        break;
+      case 3: k_fft_y<T, true><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, nullptr); break;
+      default:
+        k_fft_x_inv<T, XOUT_PLAIN><<<gx, L.x_threads, L.xinv_smem, st>>>(
+            op, scratch, x, y, L.x_lines, nullptr, nullptr, nullptr);
+    }
+  };
+  launch();  // warm-up
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < reps; ++i) launch();
+  cudaEventRecord(e1, st);
+  if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) return 1e30f;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms / reps;
+}
+
+template <typename T>
+cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const cplx_t<T>* x,
+                            cplx_t<T>* y, cplx_t<T>* scratch, cudaStream_t st) {
+  using C = cplx_t<T>;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  const int reps = 3;
+  const size_t kMax = 200 * 1024;
+  MatvecLaunch best = L;
+  // x passes (forward and inverse together)
+  {
+    float bt = time_pass<T>(op, best, 0, R, x, y, scratch, st, e0, e1, reps) +
+               time_pass<T>(op, best, 4, R, x, y, scratch, st, e0, e1, reps);
+    for (int nl : {2, 4, 8, 16, 32, 64}) {
+      MatvecLaunch c = best;
+      fill_x<T>(op, c, nl);
+      if (c.xinv_smem > kMax || nl > 3 * op.nz * op.ny) continue;
+      const float tt = time_pass<T>(op, c, 0, R, x, y, scratch, st, e0, e1, reps) +
+                       time_pass<T>(op, c, 4, R, x, y, scratch, st, e0, e1, reps);
+      if (tt < bt) { bt = tt; best = c; }
+    }
+  }
+  // y passes
+  {
+    float bt = time_pass<T>(op, best, 1, R, x, y, scratch, st, e0, e1, reps) +
+               time_pass<T>(op, best, 3, R, x, y, scratch, st, e0, e1, reps);
+    for (int tile : {2, 4, 8, 16, 32}) {
+      MatvecLaunch c = best;
+      fill_y<T>(op, c, tile);
+      if (c.y_smem > kMax) continue;
+      const float tt = time_pass<T>(op, c, 1, R, x, y, scratch, st, e0, e1, reps) +
+                       time_pass<T>(op, c, 3, R, x, y, scratch, st, e0, e1, reps);
+      if (tt < bt) { bt = tt; best = c; }
+    }
+  }
+  // z pass
+  {
+    float bt = time_pass<T>(op, best, 2, R, x, y, scratch, st, e0, e1, reps);
+    for (int tile : {2, 4, 8, 16})
+      for (int gs = 0; gs < 2; ++gs)
+        for (int pad = 0; pad < 4; ++pad) {
+          MatvecLaunch c = best;
+          fill_z<T>(op, c, tile, pad, gs != 0);
+          if (c.z_smem > kMax) continue;
+          const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps);
+          if (tt < bt) { bt = tt; best = c; }
+        }
+  }
+  (void)sizeof(C);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L = best;
+  return cudaGetLastError();
+}
+
+template cudaError_t autotune_matvec<float>(const OpView<float>&, MatvecLaunch&, int,
+                                            const float2*, float2*, float2*, cudaStream_t);
+template cudaError_t autotune_matvec<double>(const OpView<double>&, MatvecLaunch&, int,
+                                             const double2*, double2*, double2*, cudaStream_t);
 
 template MatvecLaunch plan_matvec<float>(const OpView<float>&);
 template MatvecLaunch plan_matvec<double>(const OpView<double>&);

@@ -160,7 +160,6 @@ class Server:
         self.peak_in_use = 0
         self.peak_slots = 0
         self.queue_depth_max = 0
-        self.waiting = 0
         self.work = queue.Queue()
         self.results = []
         self.errors = []
@@ -175,11 +174,8 @@ class Server:
         if nbytes > self.budget:
             return False
         with self.cv:
-            self.waiting += 1
-            self.queue_depth_max = max(self.queue_depth_max, self.waiting)
             while self.slots >= self.max_slots or self.in_use + nbytes > self.budget:
                 self.cv.wait()
-            self.waiting -= 1
             self.slots += 1
             self.in_use += nbytes
             self.peak_in_use = max(self.peak_in_use, self.in_use)
@@ -229,7 +225,9 @@ class Server:
     def _admit_loop(self, requests, t0, realtime):
         # admission runs in arrival order; a request that does not fit waits
         # while later ones wait behind it (no reordering, no starvation)
-        for req in requests:
+        import bisect
+        arrivals = [r.t_arrival for r in requests]
+        for i, req in enumerate(requests):
             if realtime:
                 dt = req.t_arrival - (time.perf_counter() - t0)
                 if dt > 0:
@@ -243,7 +241,11 @@ class Server:
                 self.errors.append((req.id, f"rejected: needs {nbytes} B of a "
                                             f"{self.budget} B budget"))
                 continue
-            self.work.put((req, t0, nbytes, time.perf_counter() - t0))
+            now = time.perf_counter() - t0
+            self.work.put((req, t0, nbytes, now))
+            # requests that have arrived and still wait for admission
+            waiting = bisect.bisect_right(arrivals, now) - (i + 1) if realtime else 0
+            self.queue_depth_max = max(self.queue_depth_max, waiting)
 
     def stats(self):
         lat = sorted(r.latency for r in self.results)
@@ -291,7 +293,7 @@ def main():
     rate = args.rate
     if rate <= 0:
         # single-stream capacity on a small calibration sample of the stream
-        cal = requests_from_stream(W.serving_stream(n_requests=8, seed=7, n_max=args.n_max))
+        cal = requests_from_stream(W.serving_stream(n_requests=24, seed=7, n_max=args.n_max))
         t0 = time.perf_counter()
         for r in cal:
             solver.solve(r)
