@@ -275,6 +275,8 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     clocks.start()
     l0 = B.dda_launch_count()
+    # NVTX range: lets a profiler restrict its launch list to the timed steps
+    torch.cuda.nvtx.range_push("timed")
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1.0)                       # evict L2 between steps
@@ -293,6 +295,7 @@ def run_gpu(args, rank, world, local_rank):
         resid = out["resid"]
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
+    torch.cuda.nvtx.range_pop()
     launches = B.dda_launch_count() - l0
     clk = clocks.stop()
     barrier()
