@@ -255,7 +255,8 @@ def run_gpu(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    kw = dict(yhat=w.yhat, npol=2, tol=w.tol, max_iter=5000, dirs=None, want_famp=True)
+    kw = dict(yhat=w.yhat, npol=2, tol=w.tol, max_iter=5000, dirs=None, want_famp=True,
+              solver=args.solver)
     t = B.Target(w.occ, w.comp, w.m, method=w.method)
     grid = t.grid
     # schedule autotuning for this target and batch (setup, not timed)
@@ -315,6 +316,27 @@ def run_gpu(args, rank, world, local_rank):
         it64.append(int(np.sum(o64["iters"])))
     q64 = o64["Qext"]
     qerr = float(np.max(np.abs(qext / q64 - 1)))
+
+    # ---- the other Krylov method on the same refined FP32 solve ----
+    other = "qmr" if args.solver == "bicgstab" else "bicgstab"
+    kwo = dict(kw, solver=other)
+    t.solve(w.kd, w.khat, w.e01, precision="fp32_refined", want_P=False, **kwo)
+    ms_o, it_o, mv_o = [], [], []
+    for _ in range(k64):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        oo = t.solve(w.kd, w.khat, w.e01, precision="fp32_refined", want_P=False, **kwo)
+        ms_o.append(oo["t_solve_ms"])
+        it_o.append(int(np.sum(oo["iters"])))
+        mv_o.append(oo["matvecs"])
+    solver_cmp = {
+        "solver": other, "ms_per_solve_batch": statistics.mean(ms_o),
+        "iters_per_rhs": sum(it_o) / (R * k64),
+        "rhs_matvecs_per_solve_batch": sum(mv_o) / k64,
+        "headline_rhs_matvecs_per_solve_batch": (fp32_rhs_mv + fp64_rhs_mv) / args.steps,
+        "speedup_vs_headline": statistics.mean(step_ms) / statistics.mean(ms_o),
+        "qext_rel_diff_vs_fp64": float(np.max(np.abs(oo["Qext"] / q64 - 1))),
+        "resid": [float(r) for r in oo["resid"]]}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e_ms = []
@@ -388,6 +410,8 @@ def run_gpu(args, rank, world, local_rank):
             "refined_speedup": statistics.mean(ms64) / statistics.mean(step_ms),
             "qext_rel_diff": qerr, "qext": [float(q) for q in qext],
             "resid_refined": [float(r) for r in resid]},
+        "solver": args.solver,
+        "other_solver": solver_cmp,
         "setup_ms": setup["t_setup_ms"],
         "roofline": {"bound": "hbm", "kernel": f"k_fft_{dom} (fp32)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -415,6 +439,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sphere64", choices=sorted(WORKLOADS))
+    ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "qmr"],
+                    help="Krylov method of the timed solves (the other one is timed beside)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -44,7 +44,7 @@ typedef enum {
   DDA_ERR_OOM = 2,         /* device allocation failed (nothing is leaked)     */
   DDA_ERR_CUDA = 3,        /* CUDA error, or no device                         */
   DDA_ERR_NOCONV = 4,      /* max_iter reached; outputs hold the last iterate  */
-  DDA_ERR_BREAKDOWN = 5,   /* BiCGSTAB breakdown (rho or omega ~ 0, or NaN)     */
+  DDA_ERR_BREAKDOWN = 5,   /* Krylov breakdown (rho, omega or sigma = 0, NaN)  */
   DDA_ERR_TIMEOUT = 6      /* a bounded device wait ran out                    */
 } dda_status;
 
@@ -78,6 +78,17 @@ typedef enum {
   DDA_PREC_FP32 = 1,
   DDA_PREC_FP32_REFINED = 2
 } dda_precision;
+
+/* Krylov method of the solve (the guide's CMETHD choice, Sec. "Choice of
+ * Iterative Algorithm").
+ *  BICGSTAB : BiCGSTAB (van der Vorst 1992), the guide's PBCGST: two matvecs
+ *             per iteration; stops on the recursive residual.
+ *  QMR      : quasi-minimal residual for complex-symmetric A (Freund 1992),
+ *             the guide's QMRCCG: one matvec per iteration on the bilinear
+ *             form x^T y (A = A^T for the DDA matrix); stops when the bound
+ *             tau_k sqrt(k+1) >= ||E - A P_k|| reaches tol ||E||.
+ * Either way the reported residual is the FP64 true residual of the result. */
+typedef enum { DDA_SOLVER_BICGSTAB = 0, DDA_SOLVER_QMR = 1 } dda_solver;
 
 typedef struct dda_target dda_target; /* opaque, library-owned */
 
@@ -150,7 +161,7 @@ typedef struct {
                             library); e02 = khat x conj(e01)                    */
   int npol;              /* 1 or 2 polarizations per direction                  */
   double tol;            /* stop when ||E - A P|| / ||E|| <= tol (FP64)          */
-  int max_iter;          /* cap on BiCGSTAB iterations per RHS (all sweeps)     */
+  int max_iter;          /* cap on Krylov iterations per RHS (all sweeps)       */
   dda_precision precision;
   double inner_tol;      /* FP32_REFINED inner tolerance; <= 0: adaptive, each
                             sweep reduces the residual by what the target still
@@ -161,6 +172,8 @@ typedef struct {
                             y sin(theta) cos(phi) + z sin(theta) sin(phi)       */
   const double* P0;      /* optional warm start [n_inc*npol][N][3][2] or NULL   */
   int profile;           /* nonzero: time each FFT-matvec pass with CUDA events   */
+  int solver;            /* dda_solver: DDA_SOLVER_BICGSTAB (0, default) or
+                            DDA_SOLVER_QMR; unknown values: DDA_ERR_INVALID_ARG */
 } dda_solve_params;
 
 /* Results.  Every array is caller-allocated HOST memory; a NULL pointer means

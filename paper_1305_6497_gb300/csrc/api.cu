@@ -226,10 +226,11 @@ struct Profiler {
     }
   }
   // after a synchronize: add the times of the first `nslots` iteration slots
-  void harvest_iters(int p, int nslots) {
+  // (`nmv` matvecs per iteration)
+  void harvest_iters(int p, int nslots, int nmv = 2) {
     if (!on) return;
     for (int sl = 0; sl < nslots; ++sl)
-      for (int k = 0; k < 2; ++k) add(p, ev[sl][k]);
+      for (int k = 0; k < nmv; ++k) add(p, ev[sl][k]);
   }
   void harvest_resid() {
     if (on) add(1, evr);
@@ -270,7 +271,7 @@ struct dda_target {
   bool kernels_configured = false;
   Workspace ws;
   Profiler prof;
-  IterGraph graphs[2];  // FP32, FP64
+  IterGraph graphs[2];  // FP32, FP64 (for the solver that ran last)
   int schedule_gen = 0;  // bumped when the launch schedule changes
 };
 
@@ -532,6 +533,117 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
     its[r] = hks[r].iters;
     status[r] = hks[r].status == KS_RUN ? KS_NOCONV : hks[r].status;
   }
+}
+
+// ---------------------------------------------------------------------------
+// QMR driver for complex-symmetric A (one matvec per iteration), R RHS in
+// lockstep like bicgstab(): q lives in V.p, d in V.s, t in V.t.
+// ---------------------------------------------------------------------------
+template <typename T>
+static void qmr(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R,
+                const Vecs<T>& V, bool x_nonzero, double tol, int max_iter,
+                std::vector<int>& its, std::vector<int>& status, int64_t& matvecs) {
+  Workspace& w = t->ws;
+  const int64_t n = 3 * t->nbox;
+  const int nblk = reduce_blocks(n);
+  double* part = w.partials.as<double>();
+  KState* ks = w.ks.as<KState>();
+  int* act = w.active.as<int>();
+  cudaStream_t st = t->stream;
+  cplx_t<T>* q = V.p;
+  cplx_t<T>* d = V.s;
+  if (x_nonzero) {
+    CK(launch_matvec<T>(op, L, R, V.x, V.t, V.scr, nullptr, st));
+    matvecs += R;
+    CK(launch_qmr_init<T>(n, R, V.b, V.t, V.r, q, d, part, st));
+  } else {
+    CK(launch_qmr_init<T>(n, R, V.b, nullptr, V.r, q, d, part, st));
+  }
+  CK(launch_qmr_state(R, nblk, part, ks, act, tol, max_iter, st));
+  std::vector<int> hact(R);
+  CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int nact = 0;
+  for (int a : hact) nact += a;
+  int iter = 0;
+  const int nblk_mv = matvec_partial_blocks<T>(op, L);
+  auto enqueue_block = [&](int nq) {
+    for (int k = 0; k < nq; ++k) {
+      // pending d/x update, q <- r + beta q; t = A q; q^T t
+      CK(launch_matvec_q<T>(op, L, R, V.r, q, d, V.x, V.t, V.scr, ks, part, act, st,
+                            t->prof.iter_set(k, 0)));
+      CK(launch_qmr_sigma(R, nblk_mv, part, ks, act, st));
+      // r -= alpha t; ||r||^2, r^T r; rotation and the next pending update
+      CK(launch_qmr_update_r<T>(n, R, V.r, V.t, part, ks, act, st));
+      CK(launch_qmr_scalar(R, nblk, part, ks, act, st));
+    }
+  };
+  std::vector<uintptr_t> sig = {(uintptr_t)1000 + sizeof(T), (uintptr_t)R, (uintptr_t)t->prof.on,
+                                (uintptr_t)V.r, (uintptr_t)q, (uintptr_t)d, (uintptr_t)V.t,
+                                (uintptr_t)V.x, (uintptr_t)V.scr, (uintptr_t)ks,
+                                (uintptr_t)part, (uintptr_t)act, (uintptr_t)op.ghat,
+                                (uintptr_t)op.ainv, (uintptr_t)nblk_mv, (uintptr_t)nblk,
+                                (uintptr_t)t->schedule_gen};
+  IterGraph& g = t->graphs[sizeof(T) == 4 ? 0 : 1];
+  if (g.exec && g.sig != sig) g.reset();
+  if (!g.exec) {
+    const long long before = launch_count();
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue_block(kCheckEvery);
+    } catch (...) {
+      cudaGraph_t broken = nullptr;
+      cudaStreamEndCapture(st, &broken);
+      if (broken) cudaGraphDestroy(broken);
+      throw;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamEndCapture(st, &graph));
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie);
+    g.kernels = launch_count() - before;
+    note_launches(-g.kernels);
+    g.sig = sig;
+  }
+  while (nact > 0 && iter < max_iter) {
+    const int nq = std::min(kCheckEvery, max_iter - iter);
+    if (nq == kCheckEvery) {
+      CK(cudaGraphLaunch(g.exec, st));
+      note_launches(g.kernels);
+    } else {
+      enqueue_block(nq);
+    }
+    CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    t->prof.harvest_iters(sizeof(T) == 4 ? 0 : 1, nq, 1);
+    nact = 0;
+    for (int a : hact) nact += a;
+    iter += nq;
+  }
+  // the last iteration's d/x update
+  CK(launch_qmr_flush<T>(n, R, V.x, d, q, ks, st));
+  std::vector<KState> hks(R);
+  CK(cudaMemcpyAsync(hks.data(), ks, sizeof(KState) * R, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  its.resize(R);
+  status.resize(R);
+  for (int r = 0; r < R; ++r) {
+    matvecs += (int64_t)hks[r].iters;
+    its[r] = hks[r].iters;
+    status[r] = hks[r].status == KS_RUN ? KS_NOCONV : hks[r].status;
+  }
+}
+
+// Krylov solve with the requested method.
+template <typename T>
+static void krylov(int solver, dda_target* t, const OpView<T>& op, const MatvecLaunch& L,
+                   int R, const Vecs<T>& V, bool x_nonzero, double tol, int max_iter,
+                   std::vector<int>& its, std::vector<int>& status, int64_t& matvecs) {
+  if (solver == DDA_SOLVER_QMR)
+    qmr<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
+  else
+    bicgstab<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
 }
 
 // ---------------------------------------------------------------------------
@@ -835,6 +947,8 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
   if (p->precision != DDA_PREC_FP64 && p->precision != DDA_PREC_FP32 &&
       p->precision != DDA_PREC_FP32_REFINED)
     return fail(DDA_ERR_INVALID_ARG, "unknown precision");
+  if (p->solver != DDA_SOLVER_BICGSTAB && p->solver != DDA_SOLVER_QMR)
+    return fail(DDA_ERR_INVALID_ARG, "unknown solver");
   const int R = p->n_inc * p->npol;
   if (R > 4096) return fail(DDA_ERR_INVALID_ARG, "at most 4096 right-hand sides");
   std::vector<Incidence> incs(p->n_inc);
@@ -929,8 +1043,8 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
                      w.rh64.as<double2>(), w.p64.as<double2>(), w.v64.as<double2>(),
                      w.s64.as<double2>(), w.t64.as<double2>(), w.scr64.as<double2>()};
       std::vector<int> its;
-      bicgstab<double>(t, op64, t->L64, R, V, x_nonzero, p->tol, p->max_iter, its, status,
-                       matvecs);
+      krylov<double>(p->solver, t, op64, t->L64, R, V, x_nonzero, p->tol, p->max_iter, its,
+                     status, matvecs);
       matvecs64 = matvecs;
       for (int r = 0; r < R; ++r) { its_total[r] = its[r]; sweeps[r] = 1; }
     } else if (p->precision == DDA_PREC_FP32) {
@@ -940,8 +1054,8 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
       CK(launch_f64_to_f32(n * R, w.b64.as<double2>(), V.b, st));
       CK(launch_f64_to_f32(n * R, w.x64.as<double2>(), V.x, st));
       std::vector<int> its;
-      bicgstab<float>(t, op32, t->L32, R, V, x_nonzero, p->tol, p->max_iter, its, status,
-                      matvecs);
+      krylov<float>(p->solver, t, op32, t->L32, R, V, x_nonzero, p->tol, p->max_iter, its,
+                    status, matvecs);
       CK(launch_f32_to_f64(n * R, V.x, w.x64.as<double2>(), st));
       for (int r = 0; r < R; ++r) { its_total[r] = its[r]; sweeps[r] = 1; }
     } else {
@@ -1007,8 +1121,8 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
               inner_tol = std::min(inner_tol, 0.5 * p->tol * std::sqrt(bn2[r] / rn2[r]));
           inner_tol = std::max(inner_tol, kInnerFloor);
         }
-        bicgstab<float>(t, op32, t->L32, R, V, false, inner_tol, std::max(1, cap), its, st_in,
-                        matvecs);
+        krylov<float>(p->solver, t, op32, t->L32, R, V, false, inner_tol, std::max(1, cap),
+                      its, st_in, matvecs);
         for (int r = 0; r < R; ++r) {
           if (!outer_act[r]) continue;
           its_total[r] += its[r];

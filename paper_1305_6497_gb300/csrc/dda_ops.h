@@ -59,6 +59,11 @@ struct KState {
   double bnorm2, rnorm2, tol2;
   int active_unused;
   int iters, status, max_iter;
+  // QMR (complex symmetric): quasi-residual norm tau, rotation parameter
+  // theta, and the coefficients of the update d <- qa1 d + qa2 q, x <- x + d
+  // that each iteration leaves for the next one's first pass
+  double tau, theta;
+  double2 qa1, qa2;
 };
 
 enum { KS_RUN = 0, KS_CONV = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3 };
@@ -79,6 +84,16 @@ cudaError_t launch_matvec_p(const OpView<T>& op, const MatvecLaunch& L, int R,
 template <typename T>
 cudaError_t launch_matvec_s(const OpView<T>& op, const MatvecLaunch& L, int R,
                             const cplx_t<T>* r, const cplx_t<T>* v, cplx_t<T>* s_vec,
+                            cplx_t<T>* t_vec, cplx_t<T>* scratch, const KState* ks,
+                            double* partials, const int* active, cudaStream_t st,
+                            const cudaEvent_t* ev = nullptr);
+
+// QMR for complex-symmetric A (one matvec per iteration):
+//  launch_matvec_q: the pending d/x update, q <- r + beta q; t = A q; partials
+//                   of q^T t ([R][nblk][2])
+template <typename T>
+cudaError_t launch_matvec_q(const OpView<T>& op, const MatvecLaunch& L, int R,
+                            const cplx_t<T>* r, cplx_t<T>* q, cplx_t<T>* d, cplx_t<T>* x,
                             cplx_t<T>* t_vec, cplx_t<T>* scratch, const KState* ks,
                             double* partials, const int* active, cudaStream_t st,
                             const cudaEvent_t* ev = nullptr);
@@ -129,6 +144,33 @@ cudaError_t launch_update_xr(int64_t n, int R, cplx_t<T>* x, cplx_t<T>* r,
                              const int* active, cudaStream_t st);
 cudaError_t launch_scalar_rho(int R, int nblk, const double* partials, KState* ks,
                               int* active, cudaStream_t st);
+
+// QMR building blocks.
+//  qmr_init:    r = b - ax (ax may be null), q = d = 0; partials of ||r||^2,
+//               ||b||^2, r^T r ([R][nblk][4])
+//  qmr_state:   tau = ||r||, theta = 0, rho = r^T r, beta = 0, no pending update
+//  qmr_sigma:   alpha = rho / (q^T t) from the matvec partials
+//  qmr_update_r: r -= alpha t; partials of ||r||^2, r^T r ([R][nblk][4])
+//  qmr_scalar:  rotation, pending update coefficients, convergence on the
+//               quasi-residual bound tau sqrt(k+1) <= tol ||b||, beta
+//  qmr_flush:   apply the last pending update (all RHS)
+template <typename T>
+cudaError_t launch_qmr_init(int64_t n, int R, const cplx_t<T>* b, const cplx_t<T>* ax,
+                            cplx_t<T>* r, cplx_t<T>* q, cplx_t<T>* d, double* partials,
+                            cudaStream_t st);
+cudaError_t launch_qmr_state(int R, int nblk, const double* partials, KState* ks,
+                             int* active, double tol, int max_iter, cudaStream_t st);
+cudaError_t launch_qmr_sigma(int R, int nblk, const double* partials, KState* ks,
+                             int* active, cudaStream_t st);
+template <typename T>
+cudaError_t launch_qmr_update_r(int64_t n, int R, cplx_t<T>* r, const cplx_t<T>* t,
+                                double* partials, const KState* ks, const int* active,
+                                cudaStream_t st);
+cudaError_t launch_qmr_scalar(int R, int nblk, const double* partials, KState* ks,
+                              int* active, cudaStream_t st);
+template <typename T>
+cudaError_t launch_qmr_flush(int64_t n, int R, cplx_t<T>* x, cplx_t<T>* d,
+                             const cplx_t<T>* q, const KState* ks, cudaStream_t st);
 
 // ---- refinement helpers -----------------------------------------------------
 // partials of ||v||^2 per RHS (FP64 vector)

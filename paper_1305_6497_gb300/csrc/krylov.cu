@@ -353,6 +353,221 @@ cudaError_t launch_scalar_rho(int R, int nblk, const double* partials, KState* k
   return cudaGetLastError();
 }
 
+// ---- QMR for complex-symmetric A ------------------------------------------------
+// The DDA matrix is complex symmetric (A = A^T), so the Lanczos process can
+// run on the bilinear form x^T y with a single sequence of vectors and one
+// matvec per iteration; the iterate minimises the quasi-residual (Freund 1992,
+// coupled two-term recurrences of Freund & Nachtigal 1994; the guide's
+// QMRCCG option, Sec. "Choice of Iterative Algorithm").  Per iteration k:
+//   t = A q, sigma = q^T t, alpha = rho / sigma, r <- r - alpha t,
+//   theta' = ||r|| / tau, c^2 = 1 / (1 + theta'^2), tau <- tau theta' c,
+//   d <- c^2 theta^2 d + c^2 alpha q, x <- x + d, rho' = r^T r,
+//   beta = rho' / rho, q <- r + beta q,
+// and ||b - A x_k|| <= tau_k sqrt(k + 1) bounds the true residual.  The
+// d/x/q updates of one iteration run in the next iteration's first FFT pass;
+// the last one is applied by k_qmr_flush.
+template <typename T>
+__global__ void k_qmr_init(int64_t n, const cplx_t<T>* __restrict__ b,
+                           const cplx_t<T>* __restrict__ ax, cplx_t<T>* __restrict__ r,
+                           cplx_t<T>* __restrict__ q, cplx_t<T>* __restrict__ d,
+                           double* partials) {
+  using C = cplx_t<T>;
+  const int64_t off = (int64_t)blockIdx.y * n;
+  ChunkAcc<T, 4> acc;
+  GRID_LOOP(i, n) {
+    const C bi = b[off + i];
+    C ri = bi;
+    if (ax) ri = csub(bi, ax[off + i]);
+    r[off + i] = ri;
+    q[off + i] = mk<C>(0, 0);
+    d[off + i] = mk<C>(0, 0);
+    acc.add(0, ri.x * ri.x + ri.y * ri.y);
+    acc.add(1, bi.x * bi.x + bi.y * bi.y);
+    acc.add(2, ri.x * ri.x - ri.y * ri.y);
+    acc.add(3, (T)2 * ri.x * ri.y);
+    acc.step();
+  }
+  acc.flush();
+  write_partials<4>(acc.tot, partials);
+}
+
+template <typename T>
+cudaError_t launch_qmr_init(int64_t n, int R, const cplx_t<T>* b, const cplx_t<T>* ax,
+                            cplx_t<T>* r, cplx_t<T>* q, cplx_t<T>* d, double* partials,
+                            cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_qmr_init<T><<<g, kThreads, 0, st>>>(n, b, ax, r, q, d, partials);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_qmr_state(int nblk, const double* partials, KState* ks, int* active,
+                            double tol, int max_iter) {
+  const int r = blockIdx.x;
+  double tot[4];
+  sum_partials<4>(partials, nblk, r, tot);
+  if (threadIdx.x == 0) {
+    KState k;
+    k.rnorm2 = tot[0];
+    k.bnorm2 = tot[1];
+    k.rho = make_double2(tot[2], tot[3]);
+    k.rho_old = make_double2(1.0, 0.0);
+    k.alpha = make_double2(0.0, 0.0);
+    k.omega = make_double2(0.0, 0.0);
+    k.beta = make_double2(0.0, 0.0);  // first pass: q = r + 0 q = r
+    k.tau = sqrt(tot[0]);
+    k.theta = 0.0;
+    k.qa1 = make_double2(0.0, 0.0);   // no pending update yet
+    k.qa2 = make_double2(0.0, 0.0);
+    k.tol2 = tol * tol;
+    k.iters = 0;
+    k.max_iter = max_iter;
+    k.active_unused = 0;
+    const bool done = !(k.rnorm2 > k.tol2 * k.bnorm2);
+    k.status = done ? KS_CONV : KS_RUN;
+    if (!isfinite(k.rnorm2) || !finite2(k.rho)) k.status = KS_BREAKDOWN;
+    else if (!done && k.rho.x == 0.0 && k.rho.y == 0.0) k.status = KS_BREAKDOWN;
+    ks[r] = k;
+    active[r] = k.status == KS_RUN ? 1 : 0;
+  }
+}
+
+cudaError_t launch_qmr_state(int R, int nblk, const double* partials, KState* ks,
+                             int* active, double tol, int max_iter, cudaStream_t st) {
+  k_qmr_state<<<R, kThreads, 0, st>>>(nblk, partials, ks, active, tol, max_iter);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_qmr_sigma(int nblk, const double* partials, KState* ks, int* active) {
+  const int r = blockIdx.x;
+  if (!active[r]) return;
+  double tot[2];
+  sum_partials<2>(partials, nblk, r, tot);
+  if (threadIdx.x == 0) {
+    const double2 sigma = make_double2(tot[0], tot[1]);
+    KState& k = ks[r];
+    if (!(sigma.x != 0.0 || sigma.y != 0.0) || !finite2(sigma)) {
+      // this iteration's first pass already applied the pending update
+      k.qa1 = make_double2(0.0, 0.0);
+      k.qa2 = make_double2(0.0, 0.0);
+      k.status = KS_BREAKDOWN;
+      active[r] = 0;
+      return;
+    }
+    k.alpha = cdiv(k.rho, sigma);
+  }
+}
+
+cudaError_t launch_qmr_sigma(int R, int nblk, const double* partials, KState* ks,
+                             int* active, cudaStream_t st) {
+  k_qmr_sigma<<<R, kThreads, 0, st>>>(nblk, partials, ks, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_qmr_update_r(int64_t n, cplx_t<T>* __restrict__ r,
+                               const cplx_t<T>* __restrict__ t, double* partials,
+                               const KState* __restrict__ ks, const int* __restrict__ active) {
+  using C = cplx_t<T>;
+  const int rr = blockIdx.y;
+  if (!active[rr]) return;
+  const C alpha = from_d2<C>(ks[rr].alpha);
+  const int64_t off = (int64_t)rr * n;
+  ChunkAcc<T, 4> acc;
+  GRID_LOOP(i, n) {
+    const C ri = csub(r[off + i], cmul(alpha, t[off + i]));
+    r[off + i] = ri;
+    acc.add(0, ri.x * ri.x + ri.y * ri.y);
+    acc.add(1, ri.x * ri.x - ri.y * ri.y);
+    acc.add(2, (T)2 * ri.x * ri.y);
+    acc.step();
+  }
+  acc.flush();
+  write_partials<4>(acc.tot, partials);
+}
+
+template <typename T>
+cudaError_t launch_qmr_update_r(int64_t n, int R, cplx_t<T>* r, const cplx_t<T>* t,
+                                double* partials, const KState* ks, const int* active,
+                                cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_qmr_update_r<T><<<g, kThreads, 0, st>>>(n, r, t, partials, ks, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_qmr_scalar(int nblk, const double* partials, KState* ks, int* active) {
+  const int r = blockIdx.x;
+  if (!active[r]) return;
+  double tot[4];
+  sum_partials<4>(partials, nblk, r, tot);
+  if (threadIdx.x == 0) {
+    KState& k = ks[r];
+    const double rn2 = tot[0];
+    const double2 rho_new = make_double2(tot[1], tot[2]);
+    const double th = sqrt(rn2) / k.tau;
+    const double c2 = 1.0 / (1.0 + th * th);
+    const double tau = k.tau * th * sqrt(c2);
+    k.qa1 = make_double2(c2 * k.theta * k.theta, 0.0);
+    k.qa2 = make_double2(c2 * k.alpha.x, c2 * k.alpha.y);
+    k.theta = th;
+    k.tau = tau;
+    k.rnorm2 = rn2;
+    k.iters += 1;
+    if (!isfinite(rn2) || !isfinite(tau)) {
+      k.qa1 = make_double2(0.0, 0.0);
+      k.qa2 = make_double2(0.0, 0.0);
+      k.status = KS_BREAKDOWN; active[r] = 0; return;
+    }
+    if (tau * tau * (k.iters + 1) <= k.tol2 * k.bnorm2) {
+      k.status = KS_CONV; active[r] = 0; return;
+    }
+    if (!finite2(rho_new) || (rho_new.x == 0.0 && rho_new.y == 0.0)) {
+      k.status = KS_BREAKDOWN; active[r] = 0; return;
+    }
+    if (k.iters >= k.max_iter) {
+      k.status = KS_NOCONV; active[r] = 0; return;
+    }
+    k.beta = cdiv(rho_new, k.rho);
+    k.rho_old = k.rho;
+    k.rho = rho_new;
+  }
+}
+
+cudaError_t launch_qmr_scalar(int R, int nblk, const double* partials, KState* ks,
+                              int* active, cudaStream_t st) {
+  k_qmr_scalar<<<R, kThreads, 0, st>>>(nblk, partials, ks, active);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_qmr_flush(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __restrict__ d,
+                            const cplx_t<T>* __restrict__ q, const KState* __restrict__ ks) {
+  using C = cplx_t<T>;
+  const int rr = blockIdx.y;
+  const double2 a1d = ks[rr].qa1, a2d = ks[rr].qa2;
+  if (a1d.x == 0.0 && a1d.y == 0.0 && a2d.x == 0.0 && a2d.y == 0.0) return;
+  const C a1 = from_d2<C>(a1d), a2 = from_d2<C>(a2d);
+  const int64_t off = (int64_t)rr * n;
+  GRID_LOOP(i, n) {
+    const C dn = cadd(cmul(a1, d[off + i]), cmul(a2, q[off + i]));
+    d[off + i] = dn;
+    x[off + i] = cadd(x[off + i], dn);
+  }
+}
+
+template <typename T>
+cudaError_t launch_qmr_flush(int64_t n, int R, cplx_t<T>* x, cplx_t<T>* d,
+                             const cplx_t<T>* q, const KState* ks, cudaStream_t st) {
+  dim3 g(reduce_blocks(n), R);
+  k_qmr_flush<T><<<g, kThreads, 0, st>>>(n, x, d, q, ks);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // ---- refinement helpers -------------------------------------------------------------
 __global__ void k_norm2(int64_t n, const double2* __restrict__ v, double* partials) {
   const int64_t off = (int64_t)blockIdx.y * n;
@@ -534,7 +749,15 @@ cudaError_t launch_box_to_sites(int64_t N, int64_t nbox, int R, const int64_t* s
   template cudaError_t launch_update_xr<T>(int64_t, int, cplx_t<T>*, cplx_t<T>*,             \
                                            const cplx_t<T>*, const cplx_t<T>*,               \
                                            const cplx_t<T>*, const cplx_t<T>*, double*,      \
-                                           const KState*, const int*, cudaStream_t);
+                                           const KState*, const int*, cudaStream_t);   \
+  template cudaError_t launch_qmr_init<T>(int64_t, int, const cplx_t<T>*, const cplx_t<T>*,  \
+                                          cplx_t<T>*, cplx_t<T>*, cplx_t<T>*, double*,       \
+                                          cudaStream_t);                                     \
+  template cudaError_t launch_qmr_update_r<T>(int64_t, int, cplx_t<T>*, const cplx_t<T>*,    \
+                                              double*, const KState*, const int*,            \
+                                              cudaStream_t);                                 \
+  template cudaError_t launch_qmr_flush<T>(int64_t, int, cplx_t<T>*, cplx_t<T>*,             \
+                                           const cplx_t<T>*, const KState*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

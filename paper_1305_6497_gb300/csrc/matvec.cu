@@ -26,14 +26,19 @@ namespace dda {
 // Prologue of the first pass, fused with a BiCGSTAB vector update:
 //   XIN_PLAIN : transform x as given;
 //   XIN_P     : p <- r + beta (p - omega v), stored back, then transformed;
-//   XIN_S     : s <- r - alpha v, stored, then transformed.
-enum { XIN_PLAIN = 0, XIN_P = 1, XIN_S = 2 };
+//   XIN_S     : s <- r - alpha v, stored, then transformed;
+//   XIN_Q     : the QMR step left pending by the previous iteration,
+//               d <- a1 d + a2 q, x <- x + d, then q <- r + beta q, stored
+//               and transformed (all with the old q).
+enum { XIN_PLAIN = 0, XIN_P = 1, XIN_S = 2, XIN_Q = 3 };
 
 template <typename T> struct XinArgs {
   const cplx_t<T>* r;
-  cplx_t<T>* pv;          // p (XIN_P, read and written) or s (XIN_S, written)
+  cplx_t<T>* pv;          // p (XIN_P), s (XIN_S) or q (XIN_Q)
   const cplx_t<T>* v;
   const KState* ks;
+  cplx_t<T>* d;           // XIN_Q: QMR direction and iterate
+  cplx_t<T>* x;
 };
 
 template <typename T, int MODE>
@@ -50,12 +55,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_fwd(OpVie
   const int row0 = blockIdx.x * nlines;
   const int ps = nlines + 1;
   const int64_t off = (int64_t)r * rows * nx;
-  C c1 = mk<C>(0, 0), c2 = mk<C>(0, 0);
+  C c1 = mk<C>(0, 0), c2 = mk<C>(0, 0), c3 = mk<C>(0, 0);
   if (MODE == XIN_P) {
     c1 = mk<C>(xa.ks[r].beta.x, xa.ks[r].beta.y);
     c2 = mk<C>(xa.ks[r].omega.x, xa.ks[r].omega.y);
   } else if (MODE == XIN_S) {
     c1 = mk<C>(xa.ks[r].alpha.x, xa.ks[r].alpha.y);
+  } else if (MODE == XIN_Q) {
+    c1 = mk<C>(xa.ks[r].beta.x, xa.ks[r].beta.y);
+    c2 = mk<C>(xa.ks[r].qa1.x, xa.ks[r].qa1.y);
+    c3 = mk<C>(xa.ks[r].qa2.x, xa.ks[r].qa2.y);
   }
   // the CTA's rows are one contiguous chunk of the box vector
   const int nin = min(nlines, rows - row0) * nx;
@@ -70,6 +79,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_fwd(OpVie
         val = in[g];
       } else if (MODE == XIN_P) {
         val = cadd(xa.r[g], cmul(c1, csub(xa.pv[g], cmul(c2, xa.v[g]))));
+        xa.pv[g] = val;
+      } else if (MODE == XIN_Q) {
+        const C q = xa.pv[g];
+        const C dn = cadd(cmul(c2, xa.d[g]), cmul(c3, q));
+        xa.d[g] = dn;
+        xa.x[g] = cadd(xa.x[g], dn);
+        val = cadd(xa.r[g], cmul(c1, q));
         xa.pv[g] = val;
       } else {
         val = csub(xa.r[g], cmul(c1, xa.v[g]));
@@ -366,7 +382,8 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
 //   XOUT_PLAIN : none;
 //   XOUT_RV    : <rhat, y>              (y = v = A p)
 //   XOUT_TS    : <y, x>, <y, y>         (y = t = A s, x = s)
-enum { XOUT_PLAIN = 0, XOUT_RV = 1, XOUT_TS = 2 };
+//   XOUT_QT    : x^T y, unconjugated    (y = t = A q, x = q; QMR)
+enum { XOUT_PLAIN = 0, XOUT_RV = 1, XOUT_TS = 2, XOUT_QT = 3 };
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_inv(OpView<T> op, const cplx_t<T>* __restrict__ buf,
@@ -436,12 +453,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_inv(OpVie
         acc.add(1, out.x * xv.y - out.y * xv.x);
         acc.add(2, out.x * out.x + out.y * out.y);
         acc.step();
+      } else if (MODE == XOUT_QT) {
+        acc.add(0, xv.x * out.x - xv.y * out.y);
+        acc.add(1, xv.x * out.y + xv.y * out.x);
+        acc.step();
       }
     }
   }
   if (MODE != XOUT_PLAIN) {
     acc.flush();
-    if (MODE == XOUT_RV) {
+    if (MODE == XOUT_RV || MODE == XOUT_QT) {
       double v2[2] = {acc.tot[0], acc.tot[1]};
       write_partials<2>(v2, partials);
     } else {
@@ -499,8 +520,9 @@ cudaError_t configure_matvec_kernels(const MatvecLaunch& L) {
   (void)L;
   cudaError_t e;
   const void* xk[] = {(const void*)k_fft_x_fwd<T, XIN_PLAIN>, (const void*)k_fft_x_fwd<T, XIN_P>,
-                      (const void*)k_fft_x_fwd<T, XIN_S>, (const void*)k_fft_x_inv<T, XOUT_PLAIN>,
-                      (const void*)k_fft_x_inv<T, XOUT_RV>, (const void*)k_fft_x_inv<T, XOUT_TS>};
+                      (const void*)k_fft_x_fwd<T, XIN_S>, (const void*)k_fft_x_fwd<T, XIN_Q>,
+                      (const void*)k_fft_x_inv<T, XOUT_PLAIN>, (const void*)k_fft_x_inv<T, XOUT_RV>,
+                      (const void*)k_fft_x_inv<T, XOUT_TS>, (const void*)k_fft_x_inv<T, XOUT_QT>};
   for (const void* k : xk) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
@@ -610,6 +632,17 @@ cudaError_t launch_matvec_s(const OpView<T>& op, const MatvecLaunch& L, int R,
                             const cudaEvent_t* ev) {
   XinArgs<T> xa{r, s_vec, v, ks};
   return matvec_passes<T, XIN_S, XOUT_TS>(op, L, R, s_vec, t_vec, scratch, active, st, ev, xa,
+                                          nullptr, partials);
+}
+
+template <typename T>
+cudaError_t launch_matvec_q(const OpView<T>& op, const MatvecLaunch& L, int R,
+                            const cplx_t<T>* r, cplx_t<T>* q, cplx_t<T>* d, cplx_t<T>* x,
+                            cplx_t<T>* t_vec, cplx_t<T>* scratch, const KState* ks,
+                            double* partials, const int* active, cudaStream_t st,
+                            const cudaEvent_t* ev) {
+  XinArgs<T> xa{r, q, nullptr, ks, d, x};
+  return matvec_passes<T, XIN_Q, XOUT_QT>(op, L, R, q, t_vec, scratch, active, st, ev, xa,
                                           nullptr, partials);
 }
 
@@ -772,7 +805,12 @@ template cudaError_t configure_matvec_kernels<double>(const MatvecLaunch&);
   template cudaError_t launch_matvec_s<T>(const OpView<T>&, const MatvecLaunch&, int,       \
                                           const cplx_t<T>*, const cplx_t<T>*, cplx_t<T>*,   \
                                           cplx_t<T>*, cplx_t<T>*, const KState*, double*,   \
-                                          const int*, cudaStream_t, const cudaEvent_t*);
+                                          const int*, cudaStream_t, const cudaEvent_t*);    \
+  template cudaError_t launch_matvec_q<T>(const OpView<T>&, const MatvecLaunch&, int,       \
+                                          const cplx_t<T>*, cplx_t<T>*, cplx_t<T>*,         \
+                                          cplx_t<T>*, cplx_t<T>*, cplx_t<T>*,               \
+                                          const KState*, double*, const int*, cudaStream_t, \
+                                          const cudaEvent_t*);
 INST_KRY(float)
 INST_KRY(double)
 #undef INST_KRY

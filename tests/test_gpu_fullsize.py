@@ -55,13 +55,14 @@ def test_sphere64_matvec_sampled_rows(B):
     _sampled_rows_check(B, W.c2_sphere64(), 48, 1)
 
 
+@pytest.mark.parametrize("solver", ["bicgstab", "qmr"])
 @pytest.mark.parametrize("precision", ["fp32_refined", "fp64"])
-def test_sphere64_solve_matches_oracle(B, precision):
+def test_sphere64_solve_matches_oracle(B, precision, solver):
     w = W.c2_sphere64()
     g = GOLD["sphere64"]
     t = B.Target(w.occ, w.comp, w.m, method=w.method)
     out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=2, tol=1e-8, max_iter=5000,
-                  precision=precision, want_P=False)
+                  precision=precision, want_P=False, solver=solver)
     t.close()
     assert out["status"] == B.DDA_OK
     for l in range(2):
@@ -79,12 +80,13 @@ def test_ellipsoid_matvec_sampled_rows(B):
     _sampled_rows_check(B, W.c3_ellipsoid(), 24, 2)
 
 
-def test_ellipsoid_64_rhs_batched(B):
+@pytest.mark.parametrize("solver", ["bicgstab", "qmr"])
+def test_ellipsoid_64_rhs_batched(B, solver):
     """1:2:3 ellipsoid, FCD, 32 orientations x 2 polarizations in one batch."""
     w = W.c3_ellipsoid()
     t = B.Target(w.occ, w.comp, w.m, method="FCD")
     out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=2, tol=1e-8, max_iter=5000,
-                  precision="fp32_refined", want_P=False)
+                  precision="fp32_refined", want_P=False, solver=solver)
     t.close()
     assert out["status"] == B.DDA_OK
     assert len(out["Qext"]) == 64

@@ -155,3 +155,78 @@ def test_invalid_arguments_are_rejected(B):
     with pytest.raises(B.DDAError):
         t.solve(3.5, [1, 0, 0], [0, 1, 0])   # FCD needs kd < pi
     t.close()
+
+
+# ---- QMR for complex-symmetric A (the guide's QMRCCG option) ------------------------
+@pytest.mark.parametrize("method", ["LDR", "FCD"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+def test_qmr_small_ellipsoid(B, method, precision):
+    w = W.small_ellipsoid(6, 10, 12, m=1.5 + 0.1j, kd=0.4, method=method)
+    ref = _oracle(w)
+    t = B.Target(w.occ, w.comp, w.m, method=method)
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=2, tol=1e-10, precision=precision,
+                  dirs=w.dirs, solver="qmr")
+    assert out["status"] == B.DDA_OK
+    _check(out, ref)
+    assert np.all(out["resid"] <= 1e-10 * 1.01)
+    assert np.abs(out["famp"][0] - ref["famp"]).max() < 1e-6 * np.abs(ref["famp"]).max()
+    if precision == "fp64":
+        # one matvec per iteration (plus the final true-residual matvec)
+        assert out["matvecs"] == int(np.sum(out["iters"])) + 2
+    t.close()
+
+
+def test_qmr_batched_orientations_and_two_materials(B):
+    w = W.small_ellipsoid(8, 6, 7, m=1.7 + 0.1j, kd=0.5, method="FCD", n_orient=4, seed=9)
+    t = B.Target(w.occ, w.comp, w.m, method="FCD")
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-10, precision="fp32_refined",
+                  dirs=w.dirs, solver="qmr")
+    for i in range(4):
+        _check(out, _oracle(w, i), r0=2 * i)
+    t.close()
+    w = W.two_material_brick()
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-10, dirs=w.dirs, solver="qmr")
+    _check(out, _oracle(w))
+    t.close()
+
+
+def test_qmr_and_bicgstab_agree_and_qmr_needs_fewer_matvecs(B):
+    w = W.c1_sphere16()
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    a = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-8, precision="fp64")
+    q = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-8, precision="fp64", solver="qmr")
+    assert np.allclose(a["Qext"], q["Qext"], rtol=1e-6, atol=0)
+    assert np.all(q["resid"] <= 1e-8)
+    assert q["matvecs"] < a["matvecs"]
+    # switching back and forth reuses nothing stale (graphs are per solver)
+    a2 = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-8, precision="fp64")
+    assert np.array_equal(a["Qext"], a2["Qext"])
+    t.close()
+
+
+def test_qmr_warm_start_and_noconv(B):
+    w = W.small_ellipsoid(6, 6, 6, m=1.5 + 0.1j, kd=0.4, method="CM")
+    t = B.Target(w.occ, w.comp, w.m, method="CM")
+    a = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-9, solver="qmr")
+    b = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-8, P0=a["P"], solver="qmr")
+    assert np.all(b["iters"] == 0)
+    out = t.solve(w.kd, w.khat, w.e01, tol=1e-14, max_iter=3, precision="fp64", solver="qmr")
+    assert out["status"] == B.DDA_ERR_NOCONV
+    assert np.all(out["iters"] == 3)
+    assert np.all(np.isfinite(out["Qext"]))
+    with pytest.raises(KeyError):
+        t.solve(w.kd, w.khat, w.e01, solver="gmres")
+    t.close()
+
+
+def test_unknown_solver_code_is_rejected_by_the_library(B):
+    import ctypes as ct
+    w = W.small_ellipsoid(4, 4, 4, m=1.5 + 0.1j, kd=0.4, method="LDR")
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    prm, keep, _ = B._params(w.kd, w.khat, w.e01, None, 2, 1e-8, 10, "fp64", 0.0, None, None)
+    prm.solver = 7
+    res = B.SolveResult()
+    assert B.lib.dda_solve(t.h, ct.byref(prm), ct.byref(res)) == B.DDA_ERR_INVALID_ARG
+    assert "solver" in B.dda_last_error()
+    t.close()
