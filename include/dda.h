@@ -236,6 +236,32 @@ dda_status dda_target_schedule(const dda_target* t, int precision, int* out5);
 /* Kernels launched by this library since the process started (all threads). */
 int64_t dda_launch_count(void);
 
+/* Near field (the guide's NRFLD option, Sec. "Near-Field Calculations"): the
+ * field of the solved dipoles in and around the target, on an extended box.
+ * The box adds round(ext[2a] * n_a) lattice layers below and round(ext[2a+1] *
+ * n_a) above the target's box along axis a (ext = r1..r6 of the guide: -x, +x,
+ * -y, +y, -z, +z; each in [0, 64]); every axis of the result is at most 1024.
+ * dda_nearfield_box returns the extended dimensions dims[3] = (nx', ny', nz')
+ * and the target's offset lo[3] inside them (sizing only, no GPU work). */
+dda_status dda_nearfield_box(const dda_target* t, const double* ext, int* dims, int* lo);
+
+/* Fields on every site of the extended box for the incidences in p (kd, n_inc,
+ * khat, e01, npol as given to dda_solve; the other fields of p are ignored):
+ *  P       : [n_rhs][N][3][2] dipole moments returned by dda_solve (host).
+ *  E_sca   : field radiated by all dipoles except the one at the site,
+ *            sum_{l != j} G(r_j - r_l) P_l (G as in the solve: point dipole, or
+ *            the filtered tensor for FCD).
+ *  E_inc   : the incident wave at the site (phase origin: the target's centre).
+ *  E_macro : macroscopic field, 3/(eps_j + 2) (E_inc + E_sca) on target sites
+ *            (eps_j = m_j^2, eq. macro_vs_micro), E_inc + E_sca in vacuum.
+ * Outputs are caller-allocated HOST arrays [n_rhs][3][nz'][ny'][nx'][2]
+ * (component-major, x fastest); NULL skips one.  At target sites a converged
+ * P satisfies P_j = alpha_j (E_inc + E_sca)_j up to the solve's tolerance.
+ * The extended box (its own Green-tensor transform, FP64 workspace) is kept
+ * on the target and reused while ext and kd stay the same. */
+dda_status dda_nearfield(dda_target* t, const dda_solve_params* p, const double* P,
+                         const double* ext, double* E_inc, double* E_sca, double* E_macro);
+
 /* Number of occupied sites N of a target (-1 for NULL). */
 int64_t dda_target_num_dipoles(const dda_target* t);
 

@@ -25,6 +25,9 @@ Contents, each citing the passage it follows:
                               Iterative Algorithm")
   cross_sections           -- Q_ext, Q_abs, Q_sca (Sec. "What Does It Calculate?")
   scattering_amplitudes    -- f_ml (eq. f_ml_def)
+  nearfield_box, nearfield -- E_inc, E_sca and E_macro in and around the target
+                              on an extended box (Sec. "Near-Field Calculations",
+                              eq. macro_vs_micro)
 
 Readings where the guide is silent or garbled are stated at each function and
 collected in the design notes.  Parity of ``polarizability('LDR')``'s three
@@ -499,4 +502,74 @@ def solve_target(occ, comp, m_list, kd, khat, yhat, e01, method="LDR", npol=2,
     d_all = np.concatenate([np.zeros((1, 2)), np.asarray(dirs if dirs is not None
                                                           else np.zeros((0, 2)))])
     out["famp"] = scattering_amplitudes(out["P"], pos, kd, khat, yhat, d_all)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Near field (Sec. "Near-Field Calculations")
+# --------------------------------------------------------------------------
+def nearfield_box(shape_zyx, ext):
+    """Extended box of the NRFLD option: the target's box (nz, ny, nx) grown by
+    r1 n_x sites below and r2 n_x above along x, r3, r4 along y, r5, r6 along z
+    (Sec. "Additional Nearfield Calculation?"), each rounded to the nearest
+    integer (halves away from zero).  Returns (dims (nx', ny', nz'), lo (x, y, z))."""
+    nz, ny, nx = shape_zyx
+    n = (nx, ny, nz)
+    lo, dims = [], []
+    for a in range(3):
+        rl, rh = float(ext[2 * a]), float(ext[2 * a + 1])
+        l = int(math.floor(rl * n[a] + 0.5))
+        h = int(math.floor(rh * n[a] + 0.5))
+        lo.append(l)
+        dims.append(n[a] + l + h)
+    return tuple(dims), tuple(lo)
+
+
+def nearfield(occ, comp, m_list, kd, khat, e, method, P, ext, points=None):
+    """Fields of the dipoles P [N, 3] (target sites in flat-index order) at the
+    sites of the extended box, by direct summation:
+
+      E_sca(r) = sum over target sites l with r_l != r of G(r - r_l) P_l
+                 (G = green_point, or green_fcd for FCD: the tensor of the solve),
+      E_inc(r) = e exp(i k khat . r), with r measured from the target's centre,
+      E_macro  = 3 / (eps + 2) (E_inc + E_sca) on target sites of refractive
+                 index m (eps = m^2, eq. macro_vs_micro), E_inc + E_sca in vacuum.
+
+    Returns a dict of arrays [3, nz', ny', nx'] (or [n_points, 3] for the flat
+    indices `points` of the extended box), plus dims and lo.
+    """
+    dims, lo = nearfield_box(occ.shape, ext)
+    nxe, nye, nze = dims
+    nz, ny, nx = occ.shape
+    flat, pos = site_positions(occ)
+    comp_sites = comp.reshape(-1)[flat]
+    G = green(method)
+    allpts = np.arange(nxe * nye * nze) if points is None else np.asarray(points)
+    ix = allpts % nxe
+    iy = (allpts // nxe) % nye
+    iz = allpts // (nxe * nye)
+    r = np.stack([ix - lo[0] - 0.5 * (nx - 1), iy - lo[1] - 0.5 * (ny - 1),
+                  iz - lo[2] - 0.5 * (nz - 1)], axis=1).astype(np.float64)
+    esca = np.zeros((len(allpts), 3), np.complex128)
+    for s0 in range(0, len(allpts), 64):
+        rb = r[s0:s0 + 64]
+        dr = rb[:, None, :] - pos[None, :, :]
+        same = np.all(dr == 0.0, axis=-1)
+        dr[same] = 1.0
+        T = G(dr, kd)
+        T[same] = 0.0
+        esca[s0:s0 + 64] = np.einsum("bnij,nj->bi", T, P)
+    einc = incident_field(r, kd, khat, e)
+    # composition at each point (0 = vacuum)
+    inside = (ix >= lo[0]) & (ix < lo[0] + nx) & (iy >= lo[1]) & (iy < lo[1] + ny) & \
+             (iz >= lo[2]) & (iz < lo[2] + nz)
+    cpt = np.zeros(len(allpts), np.int64)
+    cpt[inside] = comp[iz[inside] - lo[2], iy[inside] - lo[1], ix[inside] - lo[0]]
+    fac = np.ones(len(allpts), np.complex128)
+    for c, m in enumerate(m_list, start=1):
+        fac[cpt == c] = 3.0 / (complex(m) ** 2 + 2.0)
+    emacro = fac[:, None] * (einc + esca)
+    out = dict(dims=dims, lo=lo, comp=cpt)
+    for k, v in (("E_inc", einc), ("E_sca", esca), ("E_macro", emacro)):
+        out[k] = v if points is not None else v.T.reshape(3, nze, nye, nxe)
     return out

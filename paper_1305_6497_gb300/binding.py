@@ -86,6 +86,10 @@ def _load():
     lib.dda_matvec_noalloc.argtypes = [vp, ct.c_double, _dp, _dp, ct.c_void_p, ct.c_void_p,
                                        ct.c_int, ct.c_void_p]
     lib.dda_matvec_noalloc.restype = ct.c_int
+    lib.dda_nearfield_box.argtypes = [vp, _dp, _ip, _ip]
+    lib.dda_nearfield_box.restype = ct.c_int
+    lib.dda_nearfield.argtypes = [vp, ct.POINTER(SolveParams), _dp, _dp, _dp, _dp, _dp]
+    lib.dda_nearfield.restype = ct.c_int
     return lib
 
 
@@ -250,6 +254,38 @@ def dda_solve(h, kd, khat, e01, yhat=None, npol=2, tol=1e-8, max_iter=2000,
     return out
 
 
+def dda_nearfield_box(h, ext):
+    """(dims, lo): extended box (nx', ny', nz') and the target's offset in it."""
+    e = np.ascontiguousarray(ext, np.float64)
+    if e.shape != (6,):
+        raise ValueError("ext must hold 6 values (-x, +x, -y, +y, -z, +z)")
+    dims = (ct.c_int * 3)()
+    lo = (ct.c_int * 3)()
+    _check(lib.dda_nearfield_box(h, _ptr(e), dims, lo))
+    return tuple(dims), tuple(lo)
+
+
+def dda_nearfield(h, kd, khat, e01, P, ext, npol=2, want=("E_inc", "E_sca", "E_macro")):
+    """Near field of the dipoles P (as returned by dda_solve for the same
+    incidences) on the extended box.  Arrays have shape (n_rhs, 3, nz', ny', nx')."""
+    prm, keep, n_inc = _params(kd, khat, e01, None, npol, 1e-8, 1, "fp64", 0.0, None, None)
+    dims, lo = dda_nearfield_box(h, ext)
+    R = n_inc * npol
+    P = np.ascontiguousarray(P, np.complex128)
+    N = dda_target_num_dipoles(h)
+    if P.shape != (R, N, 3):
+        raise ValueError(f"P must have shape {(R, N, 3)}")
+    e = np.ascontiguousarray(ext, np.float64)
+    shape = (R, 3, dims[2], dims[1], dims[0])
+    out = {k: np.empty(shape, np.complex128) if k in want else None
+           for k in ("E_inc", "E_sca", "E_macro")}
+    _check(lib.dda_nearfield(h, ct.byref(prm), _ptr(P.view(np.float64)), _ptr(e),
+                             *[None if out[k] is None else _ptr(out[k].view(np.float64))
+                               for k in ("E_inc", "E_sca", "E_macro")]))
+    out["dims"], out["lo"] = dims, lo
+    return out
+
+
 class Target:
     """Owning wrapper around a dda_target handle."""
 
@@ -288,6 +324,9 @@ class Target:
 
     def hbm_bytes(self, kd, khat, e01, **kw):
         return dda_solve_hbm_bytes(self.h, kd, khat, e01, **kw)
+
+    def nearfield(self, kd, khat, e01, P, ext, **kw):
+        return dda_nearfield(self.h, kd, khat, e01, P, ext, **kw)
 
     def autotune(self, kd, n_rhs):
         dda_autotune(self.h, kd, n_rhs)

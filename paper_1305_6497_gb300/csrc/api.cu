@@ -273,6 +273,9 @@ struct dda_target {
   Profiler prof;
   IterGraph graphs[2];  // FP32, FP64 (for the solver that ran last)
   int schedule_gen = 0;  // bumped when the launch schedule changes
+  // near field: the target embedded in an extended box (vacant around it)
+  dda_target* nf = nullptr;
+  int nf_lo[3] = {0, 0, 0}, nf_n[3] = {0, 0, 0};
 };
 
 static int64_t octant_size(const dda_target* t) {
@@ -647,6 +650,66 @@ static void krylov(int solver, dda_target* t, const OpView<T>& op, const MatvecL
 }
 
 // ---------------------------------------------------------------------------
+// Near field on an extended box (the guide's NRFLD option, Sec. "Near-Field
+// Calculations"): the solved dipoles radiate into a box that adds
+// round(r_i n) vacant layers on each side of the target's box.
+// ---------------------------------------------------------------------------
+static dda_status nearfield_box(const dda_target* t, const double* ext, int n[3], int lo[3]) {
+  if (!ext) return fail(DDA_ERR_INVALID_ARG, "ext is NULL");
+  const int nb[3] = {t->nx, t->ny, t->nz};
+  for (int a = 0; a < 3; ++a) {
+    const double rl = ext[2 * a], rh = ext[2 * a + 1];
+    if (!(rl >= 0.0) || !(rh >= 0.0) || !std::isfinite(rl) || !std::isfinite(rh) ||
+        rl > 64.0 || rh > 64.0)
+      return fail(DDA_ERR_INVALID_ARG, "ext values must be finite, in [0, 64]");
+    lo[a] = (int)std::lround(rl * nb[a]);
+    const int hi = (int)std::lround(rh * nb[a]);
+    n[a] = nb[a] + lo[a] + hi;
+    if (n[a] > 1024) return fail(DDA_ERR_INVALID_ARG, "extended box exceeds 1024 sites per axis");
+  }
+  return DDA_OK;
+}
+
+// exp(i kd u x) at the extended box's sites, x measured from the solved target's
+// origin (its box centroid): x = i - lo - (n_target - 1)/2
+static void axis_phase_ext(int n_ext, int lo, int n_tgt, double kd, double u,
+                           std::vector<double2>& out) {
+  for (int i = 0; i < n_ext; ++i) {
+    const double arg = kd * u * ((i - lo) - 0.5 * (n_tgt - 1));
+    out.push_back(make_double2(std::cos(arg), std::sin(arg)));
+  }
+}
+
+static dda_status ensure_nearfield_target(dda_target* t, const int n[3], const int lo[3]) {
+  if (t->nf && t->nf_n[0] == n[0] && t->nf_n[1] == n[1] && t->nf_n[2] == n[2] &&
+      t->nf_lo[0] == lo[0] && t->nf_lo[1] == lo[1] && t->nf_lo[2] == lo[2]) {
+    t->nf->method = t->method;
+    return DDA_OK;
+  }
+  if (t->nf) dda_target_destroy(t->nf);
+  t->nf = nullptr;
+  std::vector<uint8_t> c0(t->nbox);
+  CK(cudaMemcpy(c0.data(), t->comp.p, t->nbox, cudaMemcpyDeviceToHost));
+  const int64_t nb = (int64_t)n[0] * n[1] * n[2];
+  std::vector<uint8_t> c1(nb, 0);
+  for (int z = 0; z < t->nz; ++z)
+    for (int y = 0; y < t->ny; ++y)
+      for (int x = 0; x < t->nx; ++x)
+        c1[((int64_t)(z + lo[2]) * n[1] + (y + lo[1])) * n[0] + (x + lo[0])] =
+            c0[((int64_t)z * t->ny + y) * t->nx + x];
+  std::vector<double> m;
+  for (const cd& v : t->m) { m.push_back(v.real()); m.push_back(v.imag()); }
+  dda_target* f = nullptr;
+  const dda_status s = dda_target_create(n[0], n[1], n[2], c1.data(), c1.data(), t->ncomp,
+                                         m.data(), &f);
+  if (s != DDA_OK) return s;
+  f->method = t->method;
+  t->nf = f;
+  for (int a = 0; a < 3; ++a) { t->nf_n[a] = n[a]; t->nf_lo[a] = lo[a]; }
+  return DDA_OK;
+}
+
+// ---------------------------------------------------------------------------
 // workspace sizing
 // ---------------------------------------------------------------------------
 static int64_t workspace_bytes(const dda_target* t, int R, dda_precision prec, int ndir) {
@@ -746,6 +809,8 @@ dda_status dda_target_grid(const dda_target* t, int* Lx, int* Ly, int* Lz) {
 
 void dda_target_destroy(dda_target* t) {
   if (!t) return;
+  if (t->nf) dda_target_destroy(t->nf);
+  t->nf = nullptr;
   cudaSetDevice(t->device);
   if (t->stream) cudaStreamSynchronize(t->stream);
   t->ws.release_all();
@@ -1352,6 +1417,90 @@ std::vector<int> schedule_of(const MatvecLaunch& L) {
 }  // namespace
 
 extern "C" {
+
+dda_status dda_nearfield_box(const dda_target* t, const double* ext, int* dims, int* lo) {
+  g_last_error.clear();
+  if (!t || !dims || !lo) return fail(DDA_ERR_INVALID_ARG, "null argument");
+  return nearfield_box(t, ext, dims, lo);
+}
+
+dda_status dda_nearfield(dda_target* t, const dda_solve_params* p, const double* P,
+                         const double* ext, double* E_inc, double* E_sca, double* E_macro) {
+  g_last_error.clear();
+  if (!t || !p || !P) return fail(DDA_ERR_INVALID_ARG, "null argument");
+  dda_status s = check_kd(t, p->kd);
+  if (s != DDA_OK) return s;
+  if (p->n_inc < 1 || !p->khat || !p->e01) return fail(DDA_ERR_INVALID_ARG, "need n_inc >= 1, khat, e01");
+  if (p->npol != 1 && p->npol != 2) return fail(DDA_ERR_INVALID_ARG, "npol must be 1 or 2");
+  const int R = p->n_inc * p->npol;
+  if (R > 4096) return fail(DDA_ERR_INVALID_ARG, "at most 4096 right-hand sides");
+  int n[3], lo[3];
+  s = nearfield_box(t, ext, n, lo);
+  if (s != DDA_OK) return s;
+  std::vector<Incidence> incs(p->n_inc);
+  for (int i = 0; i < p->n_inc; ++i) {
+    s = make_incidence(p, i, incs[i]);
+    if (s != DDA_OK) return s;
+  }
+  try {
+    CK(cudaSetDevice(t->device));
+    s = ensure_nearfield_target(t, n, lo);
+    if (s != DDA_OK) return s;
+    dda_target* f = t->nf;
+    cudaStream_t st = f->stream;
+    build_green(f, p->kd, t->method == DDA_POL_FCD ? 1 : 0);
+    ensure_workspace(f, R, DDA_PREC_FP64, 0);
+    Workspace& w = f->ws;
+    const int64_t N = f->N, nb = f->nbox;
+    // dipoles of the solved target, in the extended box
+    CK(cudaMemcpyAsync(w.sitebuf.p, P, sizeof(double2) * 3 * N * R, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(w.x64.p, 0, sizeof(double2) * 3 * nb * R, st));
+    CK(launch_sites_to_box(N, nb, R, f->site.as<int64_t>(), w.sitebuf.as<double2>(),
+                           w.x64.as<double2>(), st));
+    // E_sca = sum_{l != j} G(r_j - r_l) P_l on every site
+    OpView<double> op = make_view<double>(f, f->g64.p, w.ainv64.p, f->tw64.p);
+    CK(launch_field<double>(op, f->L64, R, w.x64.as<double2>(), w.r64.as<double2>(),
+                            w.scr64.as<double2>(), st));
+    // incident wave (phases from the solved target's origin) and macroscopic field
+    std::vector<double2> pol(3 * R), ph;
+    for (int i = 0; i < p->n_inc; ++i)
+      for (int l = 0; l < p->npol; ++l)
+        for (int c = 0; c < 3; ++c)
+          pol[3 * (i * p->npol + l) + c] =
+              make_double2(incs[i].e[l][c].real(), incs[i].e[l][c].imag());
+    const int nt[3] = {t->nx, t->ny, t->nz};
+    for (int a = 0; a < 3; ++a)
+      for (int r = 0; r < R; ++r)
+        axis_phase_ext(n[a], lo[a], nt[a], p->kd, incs[r / p->npol].khat[a], ph);
+    std::vector<double2> fac(t->ncomp + 1);
+    fac[0] = make_double2(1.0, 0.0);
+    for (int c = 1; c <= t->ncomp; ++c) {
+      const cd e = t->m[c - 1] * t->m[c - 1];
+      const cd v = 3.0 / (e + 2.0);
+      fac[c] = make_double2(v.real(), v.imag());
+    }
+    CK(cudaMemcpyAsync(w.pol.p, pol.data(), sizeof(double2) * pol.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w.ph.p, ph.data(), sizeof(double2) * ph.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w.ainv64.p, fac.data(), sizeof(double2) * fac.size(), cudaMemcpyHostToDevice, st));
+    RhsTables tb;
+    tb.pol = w.pol.as<double2>();
+    tb.phx = w.ph.as<double2>();
+    tb.phy = tb.phx + (size_t)R * n[0];
+    tb.phz = tb.phy + (size_t)R * n[1];
+    CK(launch_nearfield_post(n[0], n[1], n[2], f->comp.as<uint8_t>(), tb, R,
+                             w.r64.as<double2>(), w.ainv64.as<double2>(),
+                             E_inc ? w.b64.as<double2>() : nullptr,
+                             E_macro ? w.t64.as<double2>() : nullptr, st));
+    const size_t bytes = sizeof(double2) * 3 * nb * R;
+    if (E_sca) CK(cudaMemcpyAsync(E_sca, w.r64.p, bytes, cudaMemcpyDeviceToHost, st));
+    if (E_inc) CK(cudaMemcpyAsync(E_inc, w.b64.p, bytes, cudaMemcpyDeviceToHost, st));
+    if (E_macro) CK(cudaMemcpyAsync(E_macro, w.t64.p, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  } catch (const CudaFail& e) {
+    return from_cuda(e);
+  }
+  return DDA_OK;
+}
 
 dda_status dda_autotune(dda_target* t, double kd, int n_rhs) {
   g_last_error.clear();

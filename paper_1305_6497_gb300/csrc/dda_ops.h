@@ -35,6 +35,13 @@ cudaError_t launch_matvec(const OpView<T>& op, const MatvecLaunch& L, int R,
                           const int* active, cudaStream_t st,
                           const cudaEvent_t* ev = nullptr);
 
+// y_j = sum_{l != j} G(r_j - r_l) x_l on every box site, vacant ones included:
+// the field radiated by the dipoles x (same five passes, FP64 only).
+template <typename T>
+cudaError_t launch_field(const OpView<T>& op, const MatvecLaunch& L, int R,
+                         const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch,
+                         cudaStream_t st);
+
 // x pass forward only (box rows -> spectral rows), used by the setup transforms.
 template <typename T>
 cudaError_t launch_x_fwd(const OpView<T>& op, const MatvecLaunch& L, int R,
@@ -204,6 +211,13 @@ cudaError_t launch_box_to_sites(int64_t N, int64_t nbox, int R, const int64_t* s
 cudaError_t launch_cross_sections(int nx, int ny, int nz, const uint8_t* comp, RhsTables tb,
                                   int R, const double2* P, const double* wabs, int ncomp1,
                                   double* partials, int nblk, cudaStream_t st);
+// near field on a box: E_inc from the per-RHS tables on every site (phases
+// relative to the solved target's origin), E_tot = E_inc + E_sca, and the
+// macroscopic field fac[comp] * E_tot (fac[0] = 1 for vacant sites).  Outputs
+// may be null; layout [R][3][nbox].
+cudaError_t launch_nearfield_post(int nx, int ny, int nz, const uint8_t* comp, RhsTables tb,
+                                  int R, const double2* esca, const double2* fac,
+                                  double2* einc, double2* emacro, cudaStream_t st);
 // far-field sums F[d][r][3] = sum_j P_j exp(-i k n_d . r_j), partials per block
 cudaError_t launch_farfield(int nx, int ny, int nz, const uint8_t* comp, int R, int D,
                             const double2* P, const double2* fphx, const double2* fphy,

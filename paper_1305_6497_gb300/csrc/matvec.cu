@@ -383,7 +383,9 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
 //   XOUT_RV    : <rhat, y>              (y = v = A p)
 //   XOUT_TS    : <y, x>, <y, y>         (y = t = A s, x = s)
 //   XOUT_QT    : x^T y, unconjugated    (y = t = A q, x = q; QMR)
-enum { XOUT_PLAIN = 0, XOUT_RV = 1, XOUT_TS = 2, XOUT_QT = 3 };
+//   XOUT_FIELD : y = sum_{l != j} G_jl x_l on EVERY box site, occupied or
+//                not (the field the dipoles radiate; near-field output)
+enum { XOUT_PLAIN = 0, XOUT_RV = 1, XOUT_TS = 2, XOUT_QT = 3, XOUT_FIELD = 4 };
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_inv(OpView<T> op, const cplx_t<T>* __restrict__ buf,
@@ -440,7 +442,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_inv(OpVie
     const int cm = op.comp[site];
     C out = mk<C>(0, 0);
     const C xv = sx[e];
-    if (cm) out = csub(cmul(ai[cm], xv), s[p * ps + line]);
+    if (MODE == XOUT_FIELD) out = s[p * ps + line];
+    else if (cm) out = csub(cmul(ai[cm], xv), s[p * ps + line]);
     yr[e] = out;
     {
       if (MODE == XOUT_RV) {
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_inv(OpVie
       }
     }
   }
-  if (MODE != XOUT_PLAIN) {
+  if (MODE != XOUT_PLAIN && MODE != XOUT_FIELD) {
     acc.flush();
     if (MODE == XOUT_RV || MODE == XOUT_QT) {
       double v2[2] = {acc.tot[0], acc.tot[1]};
@@ -522,7 +525,8 @@ cudaError_t configure_matvec_kernels(const MatvecLaunch& L) {
   const void* xk[] = {(const void*)k_fft_x_fwd<T, XIN_PLAIN>, (const void*)k_fft_x_fwd<T, XIN_P>,
                       (const void*)k_fft_x_fwd<T, XIN_S>, (const void*)k_fft_x_fwd<T, XIN_Q>,
                       (const void*)k_fft_x_inv<T, XOUT_PLAIN>, (const void*)k_fft_x_inv<T, XOUT_RV>,
-                      (const void*)k_fft_x_inv<T, XOUT_TS>, (const void*)k_fft_x_inv<T, XOUT_QT>};
+                      (const void*)k_fft_x_inv<T, XOUT_TS>, (const void*)k_fft_x_inv<T, XOUT_QT>,
+                      (const void*)k_fft_x_inv<T, XOUT_FIELD>};
   for (const void* k : xk) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
@@ -605,6 +609,14 @@ cudaError_t launch_matvec(const OpView<T>& op, const MatvecLaunch& L, int R,
                           const int* active, cudaStream_t st, const cudaEvent_t* ev) {
   return matvec_passes<T, XIN_PLAIN, XOUT_PLAIN>(op, L, R, x, y, scratch, active, st, ev,
                                                  XinArgs<T>{}, nullptr, nullptr);
+}
+
+template <typename T>
+cudaError_t launch_field(const OpView<T>& op, const MatvecLaunch& L, int R,
+                         const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch,
+                         cudaStream_t st) {
+  return matvec_passes<T, XIN_PLAIN, XOUT_FIELD>(op, L, R, x, y, scratch, nullptr, st,
+                                                 nullptr, XinArgs<T>{}, nullptr, nullptr);
 }
 
 template <typename T>
@@ -818,6 +830,8 @@ INST_KRY(double)
 template cudaError_t launch_matvec<float>(const OpView<float>&, const MatvecLaunch&, int,
                                           const float2*, float2*, float2*, const int*,
                                           cudaStream_t, const cudaEvent_t*);
+template cudaError_t launch_field<double>(const OpView<double>&, const MatvecLaunch&, int,
+                                          const double2*, double2*, double2*, cudaStream_t);
 template cudaError_t launch_matvec<double>(const OpView<double>&, const MatvecLaunch&, int,
                                            const double2*, double2*, double2*, const int*,
                                            cudaStream_t, const cudaEvent_t*);

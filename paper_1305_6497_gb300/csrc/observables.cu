@@ -95,4 +95,45 @@ cudaError_t launch_farfield(int nx, int ny, int nz, const uint8_t* comp, int R, 
   return cudaGetLastError();
 }
 
+// ---- near field (the guide's NRFLD option, Sec. "Near-Field Calculations") ---------
+// E_sca is the field of all dipoles at each box site without the site's own
+// dipole; the total microscopic field is E_inc + E_sca, and inside the target
+// the macroscopic field is E_macro = 3 / (eps + 2) E_micro (eq. macro_vs_micro),
+// in vacuum the two are equal.
+__global__ void k_nearfield_post(int nx, int ny, int nz, const uint8_t* __restrict__ comp,
+                                 RhsTables tb, const double2* __restrict__ esca,
+                                 const double2* __restrict__ fac, double2* __restrict__ einc,
+                                 double2* __restrict__ emacro) {
+  const int r = blockIdx.y;
+  const int64_t nbox = (int64_t)nx * ny * nz;
+  GRID_LOOP(i, nbox) {
+    const int ix = (int)(i % nx);
+    const int64_t q = i / nx;
+    const int iy = (int)(q % ny), iz = (int)(q / ny);
+    const double2 ph = cmul(cmul(tb.phx[(int64_t)r * nx + ix], tb.phy[(int64_t)r * ny + iy]),
+                            tb.phz[(int64_t)r * nz + iz]);
+    const double2 f = fac[comp[i]];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int64_t o = ((int64_t)r * 3 + c) * nbox + i;
+      const double2 ei = cmul(tb.pol[r * 3 + c], ph);
+      if (einc) einc[o] = ei;
+      if (emacro) {
+        const double2 es = esca[o];
+        emacro[o] = cmul(f, make_double2(ei.x + es.x, ei.y + es.y));
+      }
+    }
+  }
+}
+
+cudaError_t launch_nearfield_post(int nx, int ny, int nz, const uint8_t* comp, RhsTables tb,
+                                  int R, const double2* esca, const double2* fac,
+                                  double2* einc, double2* emacro, cudaStream_t st) {
+  const int64_t nbox = (int64_t)nx * ny * nz;
+  dim3 g(reduce_blocks(nbox), R);
+  k_nearfield_post<<<g, kThreads, 0, st>>>(nx, ny, nz, comp, tb, esca, fac, einc, emacro);
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace dda
