@@ -254,13 +254,19 @@ dda_status dda_nearfield_box(const dda_target* t, const double* ext, int* dims, 
  *  E_inc   : the incident wave at the site (phase origin: the target's centre).
  *  E_macro : macroscopic field, 3/(eps_j + 2) (E_inc + E_sca) on target sites
  *            (eps_j = m_j^2, eq. macro_vs_micro), E_inc + E_sca in vacuum.
+ *  B_inc   : magnetic field of the incident wave, khat x E_inc (Gaussian units).
+ *  B_sca   : magnetic field of all dipoles except the site's own (the guide's
+ *            NRFLD = 2), sum_{l != j} h(r_j - r_l) x P_l with h = -i k g'(r) rhat
+ *            for the scalar Green function g of the solve (point e^{ikr}/r,
+ *            or the filtered one for FCD); B = H for mu = 1.
  * Outputs are caller-allocated HOST arrays [n_rhs][3][nz'][ny'][nx'][2]
  * (component-major, x fastest); NULL skips one.  At target sites a converged
  * P satisfies P_j = alpha_j (E_inc + E_sca)_j up to the solve's tolerance.
  * The extended box (its own Green-tensor transform, FP64 workspace) is kept
  * on the target and reused while ext and kd stay the same. */
 dda_status dda_nearfield(dda_target* t, const dda_solve_params* p, const double* P,
-                         const double* ext, double* E_inc, double* E_sca, double* E_macro);
+                         const double* ext, double* E_inc, double* E_sca, double* E_macro,
+                         double* B_inc, double* B_sca);
 
 /* Number of occupied sites N of a target (-1 for NULL). */
 int64_t dda_target_num_dipoles(const dda_target* t);

@@ -25,9 +25,9 @@ Contents, each citing the passage it follows:
                               Iterative Algorithm")
   cross_sections           -- Q_ext, Q_abs, Q_sca (Sec. "What Does It Calculate?")
   scattering_amplitudes    -- f_ml (eq. f_ml_def)
-  nearfield_box, nearfield -- E_inc, E_sca and E_macro in and around the target
-                              on an extended box (Sec. "Near-Field Calculations",
-                              eq. macro_vs_micro)
+  nearfield_box, nearfield -- E_inc, E_sca, E_macro, B_inc, B_sca in and
+                              around the target on an extended box (Sec.
+                              "Near-Field Calculations", eq. macro_vs_micro)
 
 Readings where the guide is silent or garbled are stated at each function and
 collected in the design notes.  Parity of ``polarizability('LDR')``'s three
@@ -224,6 +224,21 @@ def green_fcd(dr: np.ndarray, kd: float) -> np.ndarray:
 def green(kind: str):
     """Interaction tensor for a polarizability method: FCD uses the filtered one."""
     return green_fcd if kind == "FCD" else green_point
+
+
+def magnetic_vector(dr: np.ndarray, kd: float, kind: str = "LDR") -> np.ndarray:
+    """h(r) with B(r) = h(r) x P for a dipole P at the origin (Gaussian units,
+    mu = 1): the vector potential of an oscillating dipole is A = -i k P g, so
+    B = curl A = -i k g'(r) rhat x P.  g = e^{ikr}/r (g' = e^{ikr}(ikr - 1)/r^2),
+    or the filtered g_F for FCD.  dr [..., 3] nonzero; returns [..., 3]."""
+    dr = np.asarray(dr, dtype=np.float64)
+    r = np.sqrt(np.sum(dr * dr, axis=-1))
+    k = float(kd)
+    if kind == "FCD":
+        _, g1, _ = filtered_scalar_green(r, kd)
+    else:
+        g1 = np.exp(1j * k * r) * (1j * k * r - 1.0) / r ** 2
+    return np.asarray(-1j * k * g1)[..., None] * (dr / r[..., None])
 
 
 # --------------------------------------------------------------------------
@@ -533,7 +548,9 @@ def nearfield(occ, comp, m_list, kd, khat, e, method, P, ext, points=None):
                  (G = green_point, or green_fcd for FCD: the tensor of the solve),
       E_inc(r) = e exp(i k khat . r), with r measured from the target's centre,
       E_macro  = 3 / (eps + 2) (E_inc + E_sca) on target sites of refractive
-                 index m (eps = m^2, eq. macro_vs_micro), E_inc + E_sca in vacuum.
+                 index m (eps = m^2, eq. macro_vs_micro), E_inc + E_sca in vacuum,
+      B_sca(r) = sum over target sites l with r_l != r of h(r - r_l) x P_l,
+      B_inc    = khat x E_inc (the plane wave's magnetic field).
 
     Returns a dict of arrays [3, nz', ny', nx'] (or [n_points, 3] for the flat
     indices `points` of the extended box), plus dims and lo.
@@ -551,6 +568,7 @@ def nearfield(occ, comp, m_list, kd, khat, e, method, P, ext, points=None):
     r = np.stack([ix - lo[0] - 0.5 * (nx - 1), iy - lo[1] - 0.5 * (ny - 1),
                   iz - lo[2] - 0.5 * (nz - 1)], axis=1).astype(np.float64)
     esca = np.zeros((len(allpts), 3), np.complex128)
+    bsca = np.zeros((len(allpts), 3), np.complex128)
     for s0 in range(0, len(allpts), 64):
         rb = r[s0:s0 + 64]
         dr = rb[:, None, :] - pos[None, :, :]
@@ -559,7 +577,11 @@ def nearfield(occ, comp, m_list, kd, khat, e, method, P, ext, points=None):
         T = G(dr, kd)
         T[same] = 0.0
         esca[s0:s0 + 64] = np.einsum("bnij,nj->bi", T, P)
+        hv = magnetic_vector(dr, kd, method)
+        hv[same] = 0.0
+        bsca[s0:s0 + 64] = np.cross(hv, P[None, :, :]).sum(axis=1)
     einc = incident_field(r, kd, khat, e)
+    binc = np.cross(np.asarray(khat, np.float64)[None, :], einc)
     # composition at each point (0 = vacuum)
     inside = (ix >= lo[0]) & (ix < lo[0] + nx) & (iy >= lo[1]) & (iy < lo[1] + ny) & \
              (iz >= lo[2]) & (iz < lo[2] + nz)
@@ -570,6 +592,7 @@ def nearfield(occ, comp, m_list, kd, khat, e, method, P, ext, points=None):
         fac[cpt == c] = 3.0 / (complex(m) ** 2 + 2.0)
     emacro = fac[:, None] * (einc + esca)
     out = dict(dims=dims, lo=lo, comp=cpt)
-    for k, v in (("E_inc", einc), ("E_sca", esca), ("E_macro", emacro)):
+    for k, v in (("E_inc", einc), ("E_sca", esca), ("E_macro", emacro), ("B_inc", binc),
+                 ("B_sca", bsca)):
         out[k] = v if points is not None else v.T.reshape(3, nze, nye, nxe)
     return out

@@ -88,7 +88,8 @@ def _load():
     lib.dda_matvec_noalloc.restype = ct.c_int
     lib.dda_nearfield_box.argtypes = [vp, _dp, _ip, _ip]
     lib.dda_nearfield_box.restype = ct.c_int
-    lib.dda_nearfield.argtypes = [vp, ct.POINTER(SolveParams), _dp, _dp, _dp, _dp, _dp]
+    lib.dda_nearfield.argtypes = [vp, ct.POINTER(SolveParams), _dp, _dp, _dp, _dp, _dp, _dp,
+                                  _dp]
     lib.dda_nearfield.restype = ct.c_int
     return lib
 
@@ -277,11 +278,14 @@ def dda_nearfield(h, kd, khat, e01, P, ext, npol=2, want=("E_inc", "E_sca", "E_m
         raise ValueError(f"P must have shape {(R, N, 3)}")
     e = np.ascontiguousarray(ext, np.float64)
     shape = (R, 3, dims[2], dims[1], dims[0])
-    out = {k: np.empty(shape, np.complex128) if k in want else None
-           for k in ("E_inc", "E_sca", "E_macro")}
+    keys = ("E_inc", "E_sca", "E_macro", "B_inc", "B_sca")
+    bad = set(want) - set(keys)
+    if bad:
+        raise ValueError(f"unknown near-field outputs {sorted(bad)}")
+    out = {k: np.empty(shape, np.complex128) if k in want else None for k in keys}
     _check(lib.dda_nearfield(h, ct.byref(prm), _ptr(P.view(np.float64)), _ptr(e),
                              *[None if out[k] is None else _ptr(out[k].view(np.float64))
-                               for k in ("E_inc", "E_sca", "E_macro")]))
+                               for k in keys]))
     out["dims"], out["lo"] = dims, lo
     return out
 

@@ -267,6 +267,11 @@ struct dda_target {
   double green_kd = 0.0;
   int green_filtered = -1;
   DevBuf g64, g32;
+  // transform of the magnetic vector h (near-field B), built on demand
+  bool have_h = false;
+  double h_kd = 0.0;
+  int h_filtered = -1;
+  DevBuf h64;
   MatvecLaunch L32{}, L64{};
   bool kernels_configured = false;
   Workspace ws;
@@ -308,18 +313,18 @@ static OpView<T> make_view(const dda_target* t, const void* ghat, const void* ai
   return v;
 }
 
-static void build_green(dda_target* t, double kd, int filtered) {
-  if (t->have_green && t->green_kd == kd && t->green_filtered == filtered) return;
+// Fill a tensor on the full grid (kind: see launch_green_fill), transform it
+// (FP64, unpruned) and keep one octant in g64 (and g32 when given).
+static void build_transform(dda_target* t, double kd, int kind, DevBuf& g64, DevBuf* g32) {
   const int64_t M = (int64_t)t->Lx * t->Ly * t->Lz;
   const int64_t H = octant_size(t);
-  t->have_green = false;
   DevBuf full, tmp;
   try {
     full.ensure(sizeof(double2) * 6 * M);
     tmp.ensure(sizeof(double2) * 6 * M);
-    t->g64.ensure(sizeof(double2) * 6 * H);
-    t->g32.ensure(sizeof(float2) * 6 * H);
-    CK(launch_green_fill(t->nx, t->ny, t->nz, t->Lx, t->Ly, t->Lz, kd, filtered,
+    g64.ensure(sizeof(double2) * 6 * H);
+    if (g32) g32->ensure(sizeof(float2) * 6 * H);
+    CK(launch_green_fill(t->nx, t->ny, t->nz, t->Lx, t->Ly, t->Lz, kd, kind,
                          full.as<double2>(), t->stream));
     // the full grid seen as a "box" of 2 RHS x 3 components: nothing is pruned
     OpView<double> op = make_view<double>(t, nullptr, nullptr, t->tw64.p);
@@ -333,8 +338,8 @@ static void build_green(dda_target* t, double kd, int filtered) {
     CK(launch_fft3d_full(op, L, 6, full.as<double2>(), tmp.as<double2>(), t->stream));
     const int* pos = t->perm.as<int>() + (t->Lx + t->Ly + t->Lz);
     CK(launch_green_octant(t->Lx, t->Ly, t->Lz, pos, pos + t->Lx, pos + t->Lx + t->Ly,
-                           tmp.as<double2>(), t->g64.as<double2>(), t->g32.as<float2>(),
-                           t->stream));
+                           tmp.as<double2>(), g64.as<double2>(),
+                           g32 ? g32->as<float2>() : nullptr, t->stream));
     CK(cudaStreamSynchronize(t->stream));
   } catch (...) {
     full.release();
@@ -343,9 +348,24 @@ static void build_green(dda_target* t, double kd, int filtered) {
   }
   full.release();
   tmp.release();
+}
+
+static void build_green(dda_target* t, double kd, int filtered) {
+  if (t->have_green && t->green_kd == kd && t->green_filtered == filtered) return;
+  t->have_green = false;
+  build_transform(t, kd, filtered, t->g64, &t->g32);
   t->have_green = true;
   t->green_kd = kd;
   t->green_filtered = filtered;
+}
+
+static void build_magnetic(dda_target* t, double kd, int filtered) {
+  if (t->have_h && t->h_kd == kd && t->h_filtered == filtered) return;
+  t->have_h = false;
+  build_transform(t, kd, filtered | 2, t->h64, nullptr);
+  t->have_h = true;
+  t->h_kd = kd;
+  t->h_filtered = filtered;
 }
 
 // ---------------------------------------------------------------------------
@@ -816,7 +836,7 @@ void dda_target_destroy(dda_target* t) {
   t->ws.release_all();
   t->comp.release(); t->site.release(); t->tw64.release(); t->tw32.release();
   t->perm.release();
-  t->g64.release(); t->g32.release();
+  t->g64.release(); t->g32.release(); t->h64.release();
   t->prof.destroy();
   t->graphs[0].reset();
   t->graphs[1].reset();
@@ -1425,7 +1445,8 @@ dda_status dda_nearfield_box(const dda_target* t, const double* ext, int* dims, 
 }
 
 dda_status dda_nearfield(dda_target* t, const dda_solve_params* p, const double* P,
-                         const double* ext, double* E_inc, double* E_sca, double* E_macro) {
+                         const double* ext, double* E_inc, double* E_sca, double* E_macro,
+                         double* B_inc, double* B_sca) {
   g_last_error.clear();
   if (!t || !p || !P) return fail(DDA_ERR_INVALID_ARG, "null argument");
   dda_status s = check_kd(t, p->kd);
@@ -1472,6 +1493,9 @@ dda_status dda_nearfield(dda_target* t, const dda_solve_params* p, const double*
     for (int a = 0; a < 3; ++a)
       for (int r = 0; r < R; ++r)
         axis_phase_ext(n[a], lo[a], nt[a], p->kd, incs[r / p->npol].khat[a], ph);
+    std::vector<double> kh(3 * R);
+    for (int r = 0; r < R; ++r)
+      for (int c = 0; c < 3; ++c) kh[3 * r + c] = incs[r / p->npol].khat[c];
     std::vector<double2> fac(t->ncomp + 1);
     fac[0] = make_double2(1.0, 0.0);
     for (int c = 1; c <= t->ncomp; ++c) {
@@ -1482,19 +1506,30 @@ dda_status dda_nearfield(dda_target* t, const dda_solve_params* p, const double*
     CK(cudaMemcpyAsync(w.pol.p, pol.data(), sizeof(double2) * pol.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(w.ph.p, ph.data(), sizeof(double2) * ph.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(w.ainv64.p, fac.data(), sizeof(double2) * fac.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w.sums.p, kh.data(), sizeof(double) * kh.size(), cudaMemcpyHostToDevice, st));
     RhsTables tb;
     tb.pol = w.pol.as<double2>();
     tb.phx = w.ph.as<double2>();
     tb.phy = tb.phx + (size_t)R * n[0];
     tb.phz = tb.phy + (size_t)R * n[1];
     CK(launch_nearfield_post(n[0], n[1], n[2], f->comp.as<uint8_t>(), tb, R,
-                             w.r64.as<double2>(), w.ainv64.as<double2>(),
+                             w.r64.as<double2>(), w.ainv64.as<double2>(), w.sums.as<double>(),
                              E_inc ? w.b64.as<double2>() : nullptr,
-                             E_macro ? w.t64.as<double2>() : nullptr, st));
+                             E_macro ? w.t64.as<double2>() : nullptr,
+                             B_inc ? w.v64.as<double2>() : nullptr, st));
     const size_t bytes = sizeof(double2) * 3 * nb * R;
     if (E_sca) CK(cudaMemcpyAsync(E_sca, w.r64.p, bytes, cudaMemcpyDeviceToHost, st));
     if (E_inc) CK(cudaMemcpyAsync(E_inc, w.b64.p, bytes, cudaMemcpyDeviceToHost, st));
     if (E_macro) CK(cudaMemcpyAsync(E_macro, w.t64.p, bytes, cudaMemcpyDeviceToHost, st));
+    if (B_inc) CK(cudaMemcpyAsync(B_inc, w.v64.p, bytes, cudaMemcpyDeviceToHost, st));
+    if (B_sca) {
+      // B_sca = sum_l h(r_j - r_l) x P_l with the magnetic vector's transform
+      build_magnetic(f, p->kd, t->method == DDA_POL_FCD ? 1 : 0);
+      OpView<double> oph = make_view<double>(f, f->h64.p, w.ainv64.p, f->tw64.p);
+      CK(launch_field<double>(oph, f->L64, R, w.x64.as<double2>(), w.s64.as<double2>(),
+                              w.scr64.as<double2>(), st, true));
+      CK(cudaMemcpyAsync(B_sca, w.s64.p, bytes, cudaMemcpyDeviceToHost, st));
+    }
     CK(cudaStreamSynchronize(st));
   } catch (const CudaFail& e) {
     return from_cuda(e);

@@ -36,11 +36,13 @@ cudaError_t launch_matvec(const OpView<T>& op, const MatvecLaunch& L, int R,
                           const cudaEvent_t* ev = nullptr);
 
 // y_j = sum_{l != j} G(r_j - r_l) x_l on every box site, vacant ones included:
-// the field radiated by the dipoles x (same five passes, FP64 only).
+// the field radiated by the dipoles x (same five passes, FP64 only).  With
+// magnetic, op.ghat holds the transform of h (components 0..2) and the
+// product is h x x (the magnetic field B of the dipoles).
 template <typename T>
 cudaError_t launch_field(const OpView<T>& op, const MatvecLaunch& L, int R,
                          const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch,
-                         cudaStream_t st);
+                         cudaStream_t st, bool magnetic = false);
 
 // x pass forward only (box rows -> spectral rows), used by the setup transforms.
 template <typename T>
@@ -49,13 +51,15 @@ cudaError_t launch_x_fwd(const OpView<T>& op, const MatvecLaunch& L, int R,
 
 // ---- Green tensor ----------------------------------------------------------
 // Fill the 6 components of G on the full FFT grid (FP64), parity-mirrored.
+// kind: bit 0 = filtered (FCD) scalar Green function; bit 1 = the magnetic
+// vector h (B = h x P) in components 0..2 instead of G (3..5 stay zero).
 cudaError_t launch_green_fill(int nx, int ny, int nz, int Lx, int Ly, int Lz, double kd,
-                              int filtered, double2* grid6, cudaStream_t st);
+                              int kind, double2* grid6, cudaStream_t st);
 // Forward 3-D FFT of `count` full grids in place (FP64, unpruned).
 cudaError_t launch_fft3d_full(const OpView<double>& op, const MatvecLaunch& L, int count,
                               double2* grids, double2* tmp, cudaStream_t st);
 // Copy the octant of the transformed grids (frequency k of an axis sits at
-// position pos[k]), scaled by 1/(Lx Ly Lz), to FP64 and FP32.
+// position pos[k]), scaled by 1/(Lx Ly Lz), to FP64 and FP32 (g32 may be null).
 cudaError_t launch_green_octant(int Lx, int Ly, int Lz, const int* posx, const int* posy,
                                 const int* posz, const double2* grid6, double2* g64,
                                 float2* g32, cudaStream_t st);
@@ -213,11 +217,12 @@ cudaError_t launch_cross_sections(int nx, int ny, int nz, const uint8_t* comp, R
                                   double* partials, int nblk, cudaStream_t st);
 // near field on a box: E_inc from the per-RHS tables on every site (phases
 // relative to the solved target's origin), E_tot = E_inc + E_sca, and the
-// macroscopic field fac[comp] * E_tot (fac[0] = 1 for vacant sites).  Outputs
-// may be null; layout [R][3][nbox].
+// macroscopic field fac[comp] * E_tot (fac[0] = 1 for vacant sites), and
+// B_inc = khat x E_inc (khat: [R][3]).  Outputs may be null; layout [R][3][nbox].
 cudaError_t launch_nearfield_post(int nx, int ny, int nz, const uint8_t* comp, RhsTables tb,
                                   int R, const double2* esca, const double2* fac,
-                                  double2* einc, double2* emacro, cudaStream_t st);
+                                  const double* khat, double2* einc, double2* emacro,
+                                  double2* binc, cudaStream_t st);
 // far-field sums F[d][r][3] = sum_j P_j exp(-i k n_d . r_j), partials per block
 cudaError_t launch_farfield(int nx, int ny, int nz, const uint8_t* comp, int R, int D,
                             const double2* P, const double2* fphx, const double2* fphy,

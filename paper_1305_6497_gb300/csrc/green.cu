@@ -75,6 +75,46 @@ __device__ void sici(double x, double& si, double& ci) {
   si = kPiHalf + e1.y;
 }
 
+// The scalar Green function at r > 0 and its first two radial derivatives:
+// point g = e^{ikr}/r, or the filtered g_F (FCD).
+__device__ void scalar_green(double r, double k, int filtered, double2& g, double2& g1,
+                             double2& g2) {
+  const double kr = k * r;
+  double skr, ckr;
+  sincos(kr, &skr, &ckr);
+  const double ir = 1.0 / r, ir2 = ir * ir, ir3 = ir2 * ir;
+  if (!filtered) {
+    const double2 e = make_double2(ckr, skr);  // e^{ikr}
+    g = cscale(e, ir);
+    g1 = cscale(cmul(e, make_double2(-1.0, kr)), ir2);                        // (ikr - 1)/r^2
+    g2 = cscale(cmul(e, make_double2(2.0 - kr * kr, -2.0 * kr)), ir3);        // (2 - 2ikr - k^2r^2)/r^3
+    return;
+  }
+  const double kf = 3.14159265358979323846;  // pi / d
+  const double a = kf - k, b = kf + k;
+  double sia, cia, sib, cib;
+  sici(a * r, sia, cia);
+  sici(b * r, sib, cib);
+  double sar, car, sbr, cbr;
+  sincos(a * r, &sar, &car);
+  sincos(b * r, &sbr, &cbr);
+  const double S = sia + sib, Cc = cia - cib;
+  const double S1 = (sar + sbr) / r, C1 = (car - cbr) / r;
+  const double S2 = (a * car + b * cbr) / r - S1 / r;
+  const double C2 = (-a * sar + b * sbr) / r - C1 / r;
+  const double ip = 0.31830988618379067154;  // 1/pi
+  // h = r g, h', h''
+  const double2 h = make_double2(ip * (ckr * S + skr * Cc), skr);
+  const double2 h1 = make_double2(ip * (-k * skr * S + ckr * S1 + k * ckr * Cc + skr * C1),
+                                  k * ckr);
+  const double2 h2 = make_double2(ip * (-k * k * ckr * S - 2.0 * k * skr * S1 + ckr * S2 -
+                                        k * k * skr * Cc + 2.0 * k * ckr * C1 + skr * C2),
+                                  -k * k * skr);
+  g = cscale(h, ir);
+  g1 = csub(cscale(h1, ir), cscale(h, ir2));
+  g2 = cadd(csub(cscale(h2, ir), cscale(h1, 2.0 * ir2)), cscale(h, 2.0 * ir3));
+}
+
 // Tensor at offset (dx, dy, dz) != 0 : out[0..5] = xx, xy, xz, yy, yz, zz
 __device__ void green_tensor(double dx, double dy, double dz, double k, int filtered,
                              double2 out[6]) {
@@ -82,39 +122,18 @@ __device__ void green_tensor(double dx, double dy, double dz, double k, int filt
   const double r = sqrt(r2);
   const double n[3] = {dx / r, dy / r, dz / r};
   double2 A, B;
-  const double kr = k * r;
-  double skr, ckr;
-  sincos(kr, &skr, &ckr);
   if (!filtered) {
+    const double kr = k * r;
+    double skr, ckr;
+    sincos(kr, &skr, &ckr);
     const double inv3 = 1.0 / (r2 * r);
     const double2 e = make_double2(ckr * inv3, skr * inv3);  // e^{ikr}/r^3
     A = cmul(e, make_double2(kr * kr - 1.0, kr));
     B = cmul(e, make_double2(3.0 - kr * kr, -3.0 * kr));
   } else {
-    const double kf = 3.14159265358979323846;  // pi / d
-    const double a = kf - k, b = kf + k;
-    double sia, cia, sib, cib;
-    sici(a * r, sia, cia);
-    sici(b * r, sib, cib);
-    double sar, car, sbr, cbr;
-    sincos(a * r, &sar, &car);
-    sincos(b * r, &sbr, &cbr);
-    const double S = sia + sib, Cc = cia - cib;
-    const double S1 = (sar + sbr) / r, C1 = (car - cbr) / r;
-    const double S2 = (a * car + b * cbr) / r - S1 / r;
-    const double C2 = (-a * sar + b * sbr) / r - C1 / r;
-    const double ip = 0.31830988618379067154;  // 1/pi
-    // h = r g, h', h''
-    const double2 h = make_double2(ip * (ckr * S + skr * Cc), skr);
-    const double2 h1 = make_double2(ip * (-k * skr * S + ckr * S1 + k * ckr * Cc + skr * C1),
-                                    k * ckr);
-    const double2 h2 = make_double2(ip * (-k * k * ckr * S - 2.0 * k * skr * S1 + ckr * S2 -
-                                          k * k * skr * Cc + 2.0 * k * ckr * C1 + skr * C2),
-                                    -k * k * skr);
-    const double ir = 1.0 / r, ir2 = ir * ir, ir3 = ir2 * ir;
-    const double2 g = cscale(h, ir);
-    const double2 g1 = csub(cscale(h1, ir), cscale(h, ir2));
-    const double2 g2 = cadd(csub(cscale(h2, ir), cscale(h1, 2.0 * ir2)), cscale(h, 2.0 * ir3));
+    double2 g, g1, g2;
+    scalar_green(r, k, 1, g, g1, g2);
+    const double ir = 1.0 / r;
     A = cadd(cscale(g, k * k), cscale(g1, ir));
     B = csub(g2, cscale(g1, ir));
   }
@@ -124,6 +143,21 @@ __device__ void green_tensor(double dx, double dy, double dz, double k, int filt
   out[3] = cadd(A, cscale(B, n[1] * n[1]));
   out[4] = cscale(B, n[1] * n[2]);
   out[5] = cadd(A, cscale(B, n[2] * n[2]));
+}
+
+// Magnetic field of a dipole P at offset r (Gaussian units): B = h(r) x P with
+// h = -i k g'(r) rhat (from B = curl A, A = -i k P g), i.e. for the point
+// dipole h = k^2 (e^{ikr}/r)(1 + i/(kr)) rhat; FCD uses the filtered g_F.
+// out[0..2] = h_x, h_y, h_z.
+__device__ void magnetic_vector(double dx, double dy, double dz, double k, int filtered,
+                                double2 out[3]) {
+  const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  double2 g, g1, g2;
+  scalar_green(r, k, filtered, g, g1, g2);
+  const double2 m = make_double2(k * g1.y, -k * g1.x);  // -i k g'
+  out[0] = cscale(m, dx / r);
+  out[1] = cscale(m, dy / r);
+  out[2] = cscale(m, dz / r);
 }
 
 // One thread per non-negative offset (dx, dy, dz) in the box; writes the up to
@@ -139,8 +173,18 @@ __global__ void k_green_fill(int nx, int ny, int nz, int Lx, int Ly, int Lz, dou
     const int dy = (int)(q % ny), dz = (int)(q / ny);
     if (dx == 0 && dy == 0 && dz == 0) continue;
     double2 g[6];
-    green_tensor((double)dx, (double)dy, (double)dz, k, filtered, g);
-    const int par[6][3] = {{0, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 0, 0}, {0, 1, 1}, {0, 0, 0}};
+    const bool mag = (filtered & 2) != 0;
+    if (mag) {
+      magnetic_vector((double)dx, (double)dy, (double)dz, k, filtered & 1, g);
+      g[3] = g[4] = g[5] = make_double2(0.0, 0.0);
+    } else {
+      green_tensor((double)dx, (double)dy, (double)dz, k, filtered & 1, g);
+    }
+    // parity of each component under the reflection of x, y, z: G xx..zz, or
+    // h_x, h_y, h_z (odd in their own axis) for the magnetic vector
+    const int pg[6][3] = {{0, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 0, 0}, {0, 1, 1}, {0, 0, 0}};
+    const int ph[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const int (*par)[3] = mag ? ph : pg;
     for (int mz = 0; mz < 2; ++mz) {
       if (mz && dz == 0) continue;
       const int iz = mz ? Lz - dz : dz;
@@ -254,7 +298,7 @@ __global__ void k_green_octant(int Lx, int Ly, int Lz, const int* __restrict__ p
     const double2 v = full[c * M + ((int64_t)posz[hz] * Ly + posy[hy]) * Lx + posx[hx]];
     const double2 w = make_double2(v.x * inv, v.y * inv);
     g64[6 * o + c] = w;  // the six components of a point side by side
-    g32[6 * o + c] = make_float2((float)w.x, (float)w.y);
+    if (g32) g32[6 * o + c] = make_float2((float)w.x, (float)w.y);
   }
 }
 

@@ -221,7 +221,32 @@ template <> struct G6<double> {
 // it transforms each component in registers and leaves it in place, multiplies
 // position by position, and transforms back -- no barrier is needed between
 // these steps because no other thread touches those positions.
-template <typename T, int R, int TILE, bool GS>
+// w = Ghat(k) v (symmetric, components xx..zz), or w = hhat(k) x v (CROSS:
+// components 0..2 hold hhat, each odd in its own axis)
+template <typename T, bool CROSS>
+__device__ __forceinline__ void spectral_mul(cplx_t<T> (&g)[6], bool fx, bool fy, bool fz,
+                                             cplx_t<T>* w, int stride) {
+  using C = cplx_t<T>;
+  const C a = w[0], bb = w[stride], c = w[2 * stride];
+  if (CROSS) {
+    if (fx) { g[0].x = -g[0].x; g[0].y = -g[0].y; }
+    if (fy) { g[1].x = -g[1].x; g[1].y = -g[1].y; }
+    if (fz) { g[2].x = -g[2].x; g[2].y = -g[2].y; }
+    w[0] = csub(cmul(g[1], c), cmul(g[2], bb));
+    w[stride] = csub(cmul(g[2], a), cmul(g[0], c));
+    w[2 * stride] = csub(cmul(g[0], bb), cmul(g[1], a));
+    return;
+  }
+  // odd components change sign under the reflection of an odd axis
+  if (fx != fy) { g[1].x = -g[1].x; g[1].y = -g[1].y; }
+  if (fx != fz) { g[2].x = -g[2].x; g[2].y = -g[2].y; }
+  if (fy != fz) { g[4].x = -g[4].x; g[4].y = -g[4].y; }
+  w[0] = cadd(cadd(cmul(g[0], a), cmul(g[1], bb)), cmul(g[2], c));
+  w[stride] = cadd(cadd(cmul(g[1], a), cmul(g[3], bb)), cmul(g[4], c));
+  w[2 * stride] = cadd(cadd(cmul(g[2], a), cmul(g[4], bb)), cmul(g[5], c));
+}
+
+template <typename T, int R, int TILE, bool GS, bool CROSS>
 __device__ __forceinline__ void z_mid(cplx_t<T>* s, int ps, int ncol, int col0, bool fy,
                                       int hy, const cplx_t<T>* gs, const OpView<T>& op) {
   using C = cplx_t<T>;
@@ -254,15 +279,7 @@ __device__ __forceinline__ void z_mid(cplx_t<T>* s, int ps, int ncol, int col0, 
           const int hx = fx ? op.Lx - kx : kx;
           G6<T>::load(op.ghat + 6 * (((int64_t)hz * op.Hy + hy) * op.Hx + hx), g);
         }
-        // odd components change sign under the reflection of an odd axis
-        if (fx != fy) { g[1].x = -g[1].x; g[1].y = -g[1].y; }
-        if (fx != fz) { g[2].x = -g[2].x; g[2].y = -g[2].y; }
-        if (fy != fz) { g[4].x = -g[4].x; g[4].y = -g[4].y; }
-        C* w = q + i * ps;
-        const C a = w[0], bb = w[TILE], c = w[2 * TILE];
-        w[0] = cadd(cadd(cmul(g[0], a), cmul(g[1], bb)), cmul(g[2], c));
-        w[TILE] = cadd(cadd(cmul(g[1], a), cmul(g[3], bb)), cmul(g[4], c));
-        w[2 * TILE] = cadd(cadd(cmul(g[2], a), cmul(g[4], bb)), cmul(g[5], c));
+        spectral_mul<T, CROSS>(g, fx, fy, fz, q + i * ps, TILE);
       }
     }
 #pragma unroll
@@ -305,7 +322,7 @@ __device__ __forceinline__ void ghat_tile_async(const OpView<T>& op, cplx_t<T>* 
 // grid: (column tiles, Ly, R).  Shared memory: Lz x ps, lines c * TILE + t,
 // then (GS) the Ghat tile (16-byte aligned); without GS the multiply reads
 // Ghat from global memory (long z lines, where the tile would not fit).
-template <typename T, int TILE, bool GS>
+template <typename T, int TILE, bool GS, bool CROSS = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __restrict__ active) {
   using C = cplx_t<T>;
@@ -343,7 +360,7 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
   if (P.nstage >= 1) {
     // the plan puts a radix <= 8 last
     DDA_RADIX_DISPATCH_SMALL(P.radix[last],
-                             (z_mid<T, RR, TILE, GS>(s, ps, ncol, col0, fy, hy, gs, op)));
+                             (z_mid<T, RR, TILE, GS, CROSS>(s, ps, ncol, col0, fy, hy, gs, op)));
   } else {  // Lz = 1: multiply only
     for (int t = threadIdx.x; t < ncol; t += blockDim.x) {
       const int kx = op.kx_at[col0 + t];
@@ -351,14 +368,7 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
       C g[6];
       if (GS) G6<T>::load_smem(gs + 6 * t, g);
       else G6<T>::load(op.ghat + 6 * ((int64_t)hy * op.Hx + (fx ? Lx - kx : kx)), g);
-      if (fx != fy) { g[1].x = -g[1].x; g[1].y = -g[1].y; }
-      if (fx) { g[2].x = -g[2].x; g[2].y = -g[2].y; }
-      if (fy) { g[4].x = -g[4].x; g[4].y = -g[4].y; }
-      C* w = s + t;
-      const C a = w[0], bb = w[TILE], c = w[2 * TILE];
-      w[0] = cadd(cadd(cmul(g[0], a), cmul(g[1], bb)), cmul(g[2], c));
-      w[TILE] = cadd(cadd(cmul(g[1], a), cmul(g[3], bb)), cmul(g[4], c));
-      w[2 * TILE] = cadd(cadd(cmul(g[2], a), cmul(g[4], bb)), cmul(g[5], c));
+      spectral_mul<T, CROSS>(g, fx, fy, false, s + t, TILE);
     }
     __syncthreads();
   }
@@ -545,10 +555,24 @@ cudaError_t configure_matvec_kernels(const MatvecLaunch& L) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
   }
+  if constexpr (sizeof(T) == 8) {  // magnetic near field (FP64 only)
+    const void* zc[] = {(const void*)k_fft_z_mul<T, 16, true, true>,
+                        (const void*)k_fft_z_mul<T, 8, true, true>,
+                        (const void*)k_fft_z_mul<T, 4, true, true>,
+                        (const void*)k_fft_z_mul<T, 2, true, true>,
+                        (const void*)k_fft_z_mul<T, 16, false, true>,
+                        (const void*)k_fft_z_mul<T, 8, false, true>,
+                        (const void*)k_fft_z_mul<T, 4, false, true>,
+                        (const void*)k_fft_z_mul<T, 2, false, true>};
+    for (const void* k : zc) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return e;
+    }
+  }
   return e;
 }
 
-template <typename T, int XIN, int XOUT>
+template <typename T, int XIN, int XOUT, bool CROSS = false>
 static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int R,
                                  const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch,
                                  const int* active, cudaStream_t st, const cudaEvent_t* ev,
@@ -573,7 +597,7 @@ static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int
   {
     dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
 #define DDA_ZL(TT, GG) \
-  k_fft_z_mul<T, TT, GG><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active)
+  k_fft_z_mul<T, TT, GG, CROSS><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active)
     if (L.z_gs) {
       switch (L.z_tile) {
         case 16: DDA_ZL(16, true); break;
@@ -614,7 +638,11 @@ cudaError_t launch_matvec(const OpView<T>& op, const MatvecLaunch& L, int R,
 template <typename T>
 cudaError_t launch_field(const OpView<T>& op, const MatvecLaunch& L, int R,
                          const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool magnetic) {
+  if (magnetic)
+    return matvec_passes<T, XIN_PLAIN, XOUT_FIELD, true>(op, L, R, x, y, scratch, nullptr, st,
+                                                         nullptr, XinArgs<T>{}, nullptr,
+                                                         nullptr);
   return matvec_passes<T, XIN_PLAIN, XOUT_FIELD>(op, L, R, x, y, scratch, nullptr, st,
                                                  nullptr, XinArgs<T>{}, nullptr, nullptr);
 }
@@ -831,7 +859,8 @@ template cudaError_t launch_matvec<float>(const OpView<float>&, const MatvecLaun
                                           const float2*, float2*, float2*, const int*,
                                           cudaStream_t, const cudaEvent_t*);
 template cudaError_t launch_field<double>(const OpView<double>&, const MatvecLaunch&, int,
-                                          const double2*, double2*, double2*, cudaStream_t);
+                                          const double2*, double2*, double2*, cudaStream_t,
+                                          bool);
 template cudaError_t launch_matvec<double>(const OpView<double>&, const MatvecLaunch&, int,
                                            const double2*, double2*, double2*, const int*,
                                            cudaStream_t, const cudaEvent_t*);

@@ -100,10 +100,12 @@ cudaError_t launch_farfield(int nx, int ny, int nz, const uint8_t* comp, int R, 
 // dipole; the total microscopic field is E_inc + E_sca, and inside the target
 // the macroscopic field is E_macro = 3 / (eps + 2) E_micro (eq. macro_vs_micro),
 // in vacuum the two are equal.
+// The incident magnetic field of the plane wave is B_inc = khat x E_inc.
 __global__ void k_nearfield_post(int nx, int ny, int nz, const uint8_t* __restrict__ comp,
                                  RhsTables tb, const double2* __restrict__ esca,
-                                 const double2* __restrict__ fac, double2* __restrict__ einc,
-                                 double2* __restrict__ emacro) {
+                                 const double2* __restrict__ fac, const double* __restrict__ khat,
+                                 double2* __restrict__ einc, double2* __restrict__ emacro,
+                                 double2* __restrict__ binc) {
   const int r = blockIdx.y;
   const int64_t nbox = (int64_t)nx * ny * nz;
   GRID_LOOP(i, nbox) {
@@ -113,14 +115,24 @@ __global__ void k_nearfield_post(int nx, int ny, int nz, const uint8_t* __restri
     const double2 ph = cmul(cmul(tb.phx[(int64_t)r * nx + ix], tb.phy[(int64_t)r * ny + iy]),
                             tb.phz[(int64_t)r * nz + iz]);
     const double2 f = fac[comp[i]];
+    double2 ei[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int64_t o = ((int64_t)r * 3 + c) * nbox + i;
-      const double2 ei = cmul(tb.pol[r * 3 + c], ph);
-      if (einc) einc[o] = ei;
+      ei[c] = cmul(tb.pol[r * 3 + c], ph);
+      if (einc) einc[o] = ei[c];
       if (emacro) {
         const double2 es = esca[o];
-        emacro[o] = cmul(f, make_double2(ei.x + es.x, ei.y + es.y));
+        emacro[o] = cmul(f, make_double2(ei[c].x + es.x, ei[c].y + es.y));
+      }
+    }
+    if (binc) {
+      const double* k = khat + 3 * r;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        binc[((int64_t)r * 3 + c) * nbox + i] =
+            csub(cscale(ei[c2], k[c1]), cscale(ei[c1], k[c2]));
       }
     }
   }
@@ -128,10 +140,12 @@ __global__ void k_nearfield_post(int nx, int ny, int nz, const uint8_t* __restri
 
 cudaError_t launch_nearfield_post(int nx, int ny, int nz, const uint8_t* comp, RhsTables tb,
                                   int R, const double2* esca, const double2* fac,
-                                  double2* einc, double2* emacro, cudaStream_t st) {
+                                  const double* khat, double2* einc, double2* emacro,
+                                  double2* binc, cudaStream_t st) {
   const int64_t nbox = (int64_t)nx * ny * nz;
   dim3 g(reduce_blocks(nbox), R);
-  k_nearfield_post<<<g, kThreads, 0, st>>>(nx, ny, nz, comp, tb, esca, fac, einc, emacro);
+  k_nearfield_post<<<g, kThreads, 0, st>>>(nx, ny, nz, comp, tb, esca, fac, khat, einc,
+                                           emacro, binc);
   note_launch();
   return cudaGetLastError();
 }

@@ -2,7 +2,8 @@
 
 The oracle evaluates the same dipoles P (the GPU solve's) at every site of
 the extended box, so the comparison isolates the near-field computation:
-E_sca and E_macro to 1e-10 of the largest value, E_inc to 1e-13.  With a
+E_sca, E_macro and B_sca to 1e-10 of the largest value, E_inc and B_inc to
+1e-13.  With a
 converged P the identity P_j = alpha_j (E_inc + E_sca)_j holds at target sites
 to the solve's tolerance.
 """
@@ -32,7 +33,8 @@ def test_nearfield_matches_oracle_on_the_whole_extended_box(B, method):
     ext = [0.4, 0.6, 0.3, 0.2, 0.5, 0.5]
     t = B.Target(w.occ, w.comp, w.m, method=method)
     sol = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-11, precision="fp64")
-    nf = t.nearfield(w.kd, w.khat, w.e01, sol["P"], ext)
+    nf = t.nearfield(w.kd, w.khat, w.e01, sol["P"], ext,
+                     want=("E_inc", "E_sca", "E_macro", "B_inc", "B_sca"))
     assert nf["dims"] == O.nearfield_box(w.occ.shape, ext)[0]
     flat, _ = O.site_positions(w.occ)
     for i in range(2):
@@ -43,6 +45,8 @@ def test_nearfield_matches_oracle_on_the_whole_extended_box(B, method):
             assert _max_rel(nf["E_sca"][r], ref["E_sca"]) < 1e-10
             assert np.abs(nf["E_inc"][r] - ref["E_inc"]).max() < 1e-13
             assert _max_rel(nf["E_macro"][r], ref["E_macro"]) < 1e-10
+            assert _max_rel(nf["B_sca"][r], ref["B_sca"]) < 1e-10
+            assert np.abs(nf["B_inc"][r] - ref["B_inc"]).max() < 1e-13
             # identity at target sites
             (nx, ny, nz), (lx, ly, lz) = nf["dims"], nf["lo"]
             tz, ty, tx = w.occ.shape
@@ -75,6 +79,11 @@ def test_nearfield_sphere32_sampled_points_and_cache(B):
         assert _max_rel(got, ref["E_sca"]) < 1e-10
         got = nf["E_macro"][l].reshape(3, -1)[:, pts].T
         assert _max_rel(got, ref["E_macro"]) < 1e-10
+    nb = t.nearfield(kd, khat, e01, sol["P"], ext, want=("B_sca",))
+    for l, e in enumerate((e1, e2)):
+        ref = O.nearfield(occ, comp, m, kd, khat[0], e, "LDR", sol["P"][l], ext, points=pts)
+        got = nb["B_sca"][l].reshape(3, -1)[:, pts].T
+        assert _max_rel(got, ref["B_sca"]) < 1e-10
     # the extended box is cached: a second call gives identical fields
     nf2 = t.nearfield(kd, khat, e01, sol["P"], ext, want=("E_sca",))
     assert np.array_equal(nf2["E_sca"], nf["E_sca"]) and nf2["E_inc"] is None

@@ -109,3 +109,47 @@ def test_far_outside_a_small_target_the_field_is_its_total_dipole():
     nrm = r / rr
     dip = (3 * nrm * np.dot(nrm, ptot) - ptot) / rr ** 3
     assert np.abs(E - dip).max() < 0.02 * np.abs(dip).max()
+
+
+def test_single_dipole_magnetic_field_is_the_textbook_one():
+    """B = k^2 (n x p) (e^{ikr}/r)(1 - 1/(ikr)) for a point dipole (Jackson's
+    dipole fields in Gaussian units), and B -> n x E in the far zone."""
+    occ = np.ones((1, 1, 1), np.uint8)
+    kd = 0.9
+    p = np.array([[0.3 + 0.1j, -0.2j, 0.5]])
+    nf = O.nearfield(occ, occ.copy(), [1.5], kd, [0, 0, 1], [1, 0, 0], "CM", p, [2, 3, 1, 2, 2, 1])
+    (nx, ny, nz), (lx, ly, lz) = nf["dims"], nf["lo"]
+    pv = p[0]
+    worst = 0.0
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                r = np.array([x - lx, y - ly, z - lz], float)
+                rr = np.linalg.norm(r)
+                if rr == 0:
+                    assert np.all(nf["B_sca"][:, z, y, x] == 0)
+                    continue
+                n = r / rr
+                ref = kd ** 2 * np.cross(n, pv) * np.exp(1j * kd * rr) / rr * (1 - 1 / (1j * kd * rr))
+                worst = max(worst, np.abs(nf["B_sca"][:, z, y, x] - ref).max() / np.abs(ref).max())
+    assert worst < 1e-12
+    # plane wave: B_inc = khat x E_inc
+    assert np.allclose(nf["B_inc"][1], nf["E_inc"][0], atol=1e-15)   # z x x = y
+    # far zone: B = n x E up to O(1/(kr))
+    rr = 400.0
+    n = np.array([0.6, 0.0, 0.8])
+    E = O.green_point(rr * n, kd) @ pv
+    B = np.cross(O.magnetic_vector(rr * n, kd), pv)
+    assert np.abs(B - np.cross(n, E)).max() < 3.0 / (kd * rr) * np.abs(B).max()
+
+
+def test_filtered_magnetic_vector_tends_to_the_point_one_far_away():
+    for r in (15.0, 30.0):
+        dr = np.array([r * 0.6, r * 0.0, r * 0.8])
+        hp = O.magnetic_vector(dr, 0.4, "LDR")
+        hf = O.magnetic_vector(dr, 0.4, "FCD")
+        assert np.abs(hf - hp).max() < 0.05 * np.abs(hp).max()
+        # a genuine filter: the two differ near the source
+    hp = O.magnetic_vector(np.array([1.0, 0, 0]), 0.4, "LDR")
+    hf = O.magnetic_vector(np.array([1.0, 0, 0]), 0.4, "FCD")
+    assert np.abs(hf - hp).max() > 0.05 * np.abs(hp).max()
