@@ -229,9 +229,18 @@ const char* dda_last_error(void);
  * Without this call the library uses a fixed rule. */
 dda_status dda_autotune(dda_target* t, double kd, int n_rhs);
 
-/* The schedule in use: out5 = {x lines, y tile, z tile, z row pitch, z stages
- * Ghat in shared memory (0/1)} for DDA_PREC_FP64 or (otherwise) FP32. */
-dda_status dda_target_schedule(const dda_target* t, int precision, int* out5);
+/* The schedule in use: out8 = {x lines, y tile, z tile, z row pitch, z stages
+ * Ghat in shared memory (0/1), threads per CTA of the x, y and z passes} for
+ * DDA_PREC_FP64 or (otherwise) FP32. */
+dda_status dda_target_schedule(const dda_target* t, int precision, int* out8);
+
+/* Set the schedule of DDA_PREC_FP64 or (otherwise) FP32 explicitly, in the
+ * layout dda_target_schedule returns (for instance one saved from an earlier
+ * dda_autotune).  Values outside x lines 1..64, y tile 1..64, z tile 2/4/8/16,
+ * z pitch 3*tile..3*tile+8, z staging 0/1, threads 32..256 (multiples of 32),
+ * or needing more than 200 KB of shared memory: DDA_ERR_INVALID_ARG.  The
+ * schedule changes tiling and launch shape only, not the arithmetic. */
+dda_status dda_set_schedule(dda_target* t, int precision, const int* in8);
 
 /* Kernels launched by this library since the process started (all threads). */
 int64_t dda_launch_count(void);

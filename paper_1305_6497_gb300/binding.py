@@ -83,6 +83,8 @@ def _load():
     lib.dda_autotune.restype = ct.c_int
     lib.dda_target_schedule.argtypes = [vp, ct.c_int, _ip]
     lib.dda_target_schedule.restype = ct.c_int
+    lib.dda_set_schedule.argtypes = [vp, ct.c_int, _ip]
+    lib.dda_set_schedule.restype = ct.c_int
     lib.dda_matvec_noalloc.argtypes = [vp, ct.c_double, _dp, _dp, ct.c_void_p, ct.c_void_p,
                                        ct.c_int, ct.c_void_p]
     lib.dda_matvec_noalloc.restype = ct.c_int
@@ -168,10 +170,19 @@ def dda_autotune(h, kd: float, n_rhs: int) -> None:
 
 
 def dda_target_schedule(h, precision="fp32") -> dict:
-    out = (ct.c_int * 5)()
+    out = (ct.c_int * 8)()
     _check(lib.dda_target_schedule(h, PREC[precision], out))
     return dict(x_lines=out[0], y_tile=out[1], z_tile=out[2], z_pitch=out[3],
-                z_stage_ghat=out[4])
+                z_stage_ghat=out[4], x_threads=out[5], y_threads=out[6], z_threads=out[7])
+
+
+SCHEDULE_KEYS = ("x_lines", "y_tile", "z_tile", "z_pitch", "z_stage_ghat", "x_threads",
+                 "y_threads", "z_threads")
+
+
+def dda_set_schedule(h, schedule: dict, precision="fp32") -> None:
+    vals = (ct.c_int * 8)(*[int(schedule[k]) for k in SCHEDULE_KEYS])
+    _check(lib.dda_set_schedule(h, PREC[precision], vals))
 
 
 def dda_matvec_noalloc(h, kd: float, x_dev_ptr: int, y_dev_ptr: int, khat=None, e=None,
@@ -331,6 +342,12 @@ class Target:
 
     def nearfield(self, kd, khat, e01, P, ext, **kw):
         return dda_nearfield(self.h, kd, khat, e01, P, ext, **kw)
+
+    def set_schedule(self, schedule, precision="fp32"):
+        dda_set_schedule(self.h, schedule, precision)
+
+    def schedule(self, precision="fp32"):
+        return dda_target_schedule(self.h, precision)
 
     def autotune(self, kd, n_rhs):
         dda_autotune(self.h, kd, n_rhs)

@@ -1368,8 +1368,9 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
 // ---------------------------------------------------------------------------
 // Schedule autotuning with a process-wide cache (optionally persisted in the
 // file named by DDA_TUNE_FILE: one line per key, "key : x_lines y_tile z_tile
-// z_pitch z_stage").
+// z_pitch z_stage x_threads y_threads z_threads").
 // ---------------------------------------------------------------------------
+constexpr int kScheduleLen = 8;
 #include <fstream>
 #include <map>
 #include <mutex>
@@ -1403,7 +1404,7 @@ void tune_load_locked() {
     while (v >> x) vals.push_back(x);
     std::string key = line.substr(0, c);
     while (!key.empty() && key.back() == ' ') key.pop_back();
-    if (vals.size() == 5) g_tune[key] = vals;
+    if (vals.size() == (size_t)kScheduleLen) g_tune[key] = vals;
   }
 }
 
@@ -1412,12 +1413,17 @@ void tune_store_locked(const std::string& key, const std::vector<int>& v) {
   const char* f = std::getenv("DDA_TUNE_FILE");
   if (!f) return;
   std::ofstream out(f, std::ios::app);
-  out << key << " : " << v[0] << ' ' << v[1] << ' ' << v[2] << ' ' << v[3] << ' ' << v[4] << '\n';
+  out << key << " :";
+  for (int x : v) out << ' ' << x;
+  out << '\n';
 }
 
 template <typename T>
 void apply_schedule(const dda_target* t, MatvecLaunch& L, const std::vector<int>& v) {
   using C = cplx_t<T>;
+  L.x_threads = v[5];
+  L.y_threads = v[6];
+  L.z_threads = v[7];
   L.x_lines = v[0];
   L.x_smem = (size_t)t->Lx * (v[0] + 1) * sizeof(C);
   L.xinv_smem = L.x_smem + (size_t)2 * v[0] * t->nx * sizeof(C);
@@ -1432,7 +1438,8 @@ void apply_schedule(const dda_target* t, MatvecLaunch& L, const std::vector<int>
 }
 
 std::vector<int> schedule_of(const MatvecLaunch& L) {
-  return {L.x_lines, L.y_tile, L.z_tile, L.z_ps, L.z_gs ? 1 : 0};
+  return {L.x_lines, L.y_tile, L.z_tile, L.z_ps, L.z_gs ? 1 : 0,
+          L.x_threads, L.y_threads, L.z_threads};
 }
 }  // namespace
 
@@ -1585,11 +1592,43 @@ dda_status dda_autotune(dda_target* t, double kd, int n_rhs) {
   return DDA_OK;
 }
 
-dda_status dda_target_schedule(const dda_target* t, int precision, int* out5) {
-  if (!t || !out5) return fail(DDA_ERR_INVALID_ARG, "null argument");
+dda_status dda_set_schedule(dda_target* t, int precision, const int* in8) {
+  g_last_error.clear();
+  if (!t || !in8) return fail(DDA_ERR_INVALID_ARG, "null argument");
+  const int xl = in8[0], yt = in8[1], zt = in8[2], zp = in8[3], zg = in8[4];
+  const bool f64 = precision == DDA_PREC_FP64;
+  const size_t cs = f64 ? sizeof(double2) : sizeof(float2);
+  if (xl < 1 || xl > 64 || yt < 1 || yt > 64 || (zt != 2 && zt != 4 && zt != 8 && zt != 16) ||
+      zp < 3 * zt || zp > 3 * zt + 8 || (zg != 0 && zg != 1))
+    return fail(DDA_ERR_INVALID_ARG, "schedule: x lines 1..64, y tile 1..64, z tile 2/4/8/16, "
+                                     "z pitch 3*tile..3*tile+8, z staging 0/1");
+  for (int i = 5; i < 8; ++i)
+    if (in8[i] < 32 || in8[i] > 256 || in8[i] % 32)
+      return fail(DDA_ERR_INVALID_ARG, "schedule: threads per CTA must be 32..256, multiple of 32");
+  const size_t xinv = (size_t)t->Lx * (xl + 1) * cs + (size_t)2 * xl * t->nx * cs;
+  const size_t ysm = (size_t)t->Ly * yt * cs;
+  const size_t zsm = (((size_t)t->Lz * zp * cs + 15) & ~(size_t)15) +
+                     (zg ? (size_t)6 * (t->Lz / 2 + 1) * zt * cs : 0);
+  if (xinv > 200 * 1024 || ysm > 200 * 1024 || zsm > 200 * 1024)
+    return fail(DDA_ERR_INVALID_ARG, "schedule: a pass would need more than 200 KB of shared memory");
+  try {
+    CK(cudaSetDevice(t->device));
+    configure(t);
+    const std::vector<int> v(in8, in8 + kScheduleLen);
+    if (f64) apply_schedule<double>(t, t->L64, v);
+    else apply_schedule<float>(t, t->L32, v);
+    ++t->schedule_gen;
+  } catch (const CudaFail& e) {
+    return from_cuda(e);
+  }
+  return DDA_OK;
+}
+
+dda_status dda_target_schedule(const dda_target* t, int precision, int* out8) {
+  if (!t || !out8) return fail(DDA_ERR_INVALID_ARG, "null argument");
   const MatvecLaunch& L = precision == DDA_PREC_FP64 ? t->L64 : t->L32;
   const std::vector<int> v = schedule_of(L);
-  for (int i = 0; i < 5; ++i) out5[i] = v[i];
+  for (int i = 0; i < kScheduleLen; ++i) out8[i] = v[i];
   return DDA_OK;
 }
 

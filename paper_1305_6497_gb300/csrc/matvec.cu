@@ -780,44 +780,53 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
   const int reps = 3;
   const size_t kMax = 200 * 1024;
   MatvecLaunch best = L;
+  // Thread counts are tuned with the tiles: a CTA's stages have different
+  // numbers of butterflies (e.g. 128-point lines as 16 x 8), and threads left
+  // without one wait at the stage's barrier.
   // x passes (forward and inverse together)
   {
     float bt = time_pass<T>(op, best, 0, R, x, y, scratch, st, e0, e1, reps) +
                time_pass<T>(op, best, 4, R, x, y, scratch, st, e0, e1, reps);
-    for (int nl : {2, 4, 8, 16, 32, 64}) {
-      MatvecLaunch c = best;
-      fill_x<T>(op, c, nl);
-      if (c.xinv_smem > kMax || nl > 3 * op.nz * op.ny) continue;
-      const float tt = time_pass<T>(op, c, 0, R, x, y, scratch, st, e0, e1, reps) +
-                       time_pass<T>(op, c, 4, R, x, y, scratch, st, e0, e1, reps);
-      if (tt < bt) { bt = tt; best = c; }
-    }
+    for (int nl : {2, 4, 8, 16, 32, 64})
+      for (int th : {64, 128, 256}) {
+        MatvecLaunch c = best;
+        fill_x<T>(op, c, nl);
+        c.x_threads = th;
+        if (c.xinv_smem > kMax || nl > 3 * op.nz * op.ny) continue;
+        const float tt = time_pass<T>(op, c, 0, R, x, y, scratch, st, e0, e1, reps) +
+                         time_pass<T>(op, c, 4, R, x, y, scratch, st, e0, e1, reps);
+        if (tt < bt) { bt = tt; best = c; }
+      }
   }
   // y passes
   {
     float bt = time_pass<T>(op, best, 1, R, x, y, scratch, st, e0, e1, reps) +
                time_pass<T>(op, best, 3, R, x, y, scratch, st, e0, e1, reps);
-    for (int tile : {2, 4, 8, 16, 32}) {
-      MatvecLaunch c = best;
-      fill_y<T>(op, c, tile);
-      if (c.y_smem > kMax) continue;
-      const float tt = time_pass<T>(op, c, 1, R, x, y, scratch, st, e0, e1, reps) +
-                       time_pass<T>(op, c, 3, R, x, y, scratch, st, e0, e1, reps);
-      if (tt < bt) { bt = tt; best = c; }
-    }
+    for (int tile : {2, 4, 8, 16, 32})
+      for (int th : {64, 128, 256}) {
+        MatvecLaunch c = best;
+        fill_y<T>(op, c, tile);
+        c.y_threads = th;
+        if (c.y_smem > kMax) continue;
+        const float tt = time_pass<T>(op, c, 1, R, x, y, scratch, st, e0, e1, reps) +
+                         time_pass<T>(op, c, 3, R, x, y, scratch, st, e0, e1, reps);
+        if (tt < bt) { bt = tt; best = c; }
+      }
   }
   // z pass
   {
     float bt = time_pass<T>(op, best, 2, R, x, y, scratch, st, e0, e1, reps);
     for (int tile : {2, 4, 8, 16})
       for (int gs = 0; gs < 2; ++gs)
-        for (int pad = 0; pad < 4; ++pad) {
-          MatvecLaunch c = best;
-          fill_z<T>(op, c, tile, pad, gs != 0);
-          if (c.z_smem > kMax) continue;
-          const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps);
-          if (tt < bt) { bt = tt; best = c; }
-        }
+        for (int pad = 0; pad < 4; ++pad)
+          for (int th : {128, 256}) {
+            MatvecLaunch c = best;
+            fill_z<T>(op, c, tile, pad, gs != 0);
+            c.z_threads = th;
+            if (c.z_smem > kMax) continue;
+            const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps);
+            if (tt < bt) { bt = tt; best = c; }
+          }
   }
   (void)sizeof(C);
   cudaEventDestroy(e0);

@@ -20,10 +20,39 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
     y0 = t.matvec(0.4, x)
     sched = t.autotune(0.4, 2)
     for p in ("fp32", "fp64"):
-        assert set(sched[p]) == {"x_lines", "y_tile", "z_tile", "z_pitch", "z_stage_ghat"}
+        assert set(sched[p]) == set(B.SCHEDULE_KEYS)
     y1 = t.matvec(0.4, x)
     assert np.abs(y1 - y0).max() <= 1e-12 * np.abs(y0).max()
     ainv = O.site_alpha_inverse(comp.reshape(-1)[flat], [1.5 + 0.1j], "CM", 0.4)
     ref = O.matvec_direct(x, pos, ainv, 0.4, "CM", rows=np.arange(0, len(flat), 97))
     assert np.abs(y1[::97] - ref).max() <= 1e-10 * np.abs(ref).max()
+    t.close()
+
+
+@pytest.mark.parametrize("threads", [32, 64, 128, 256])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_every_thread_count_gives_the_same_product(threads, precision):
+    """Explicit schedules with every thread count the tuner may pick (and odd
+    line/tile counts) must reproduce the default schedule's product."""
+    from paper_1305_6497_gb300 import binding as B
+    occ, comp = tg.ellipsoid(13, 18, 22)
+    flat, pos = O.site_positions(occ)
+    x = O.box_to_sites(W.random_polarization(occ, 5)[0], flat)
+    t = B.Target(occ, comp, [1.5 + 0.1j], method="LDR")
+    kh, e = [1.0, 0, 0], [0, 1.0, 0]
+    y0 = t.matvec(0.4, x, kh, e, precision)
+    for xl, yt, zt, gs in ((3, 5, 2, 0), (16, 8, 8, 1), (64, 32, 16, 0)):
+        t.set_schedule(dict(x_lines=xl, y_tile=yt, z_tile=zt, z_pitch=3 * zt + 1,
+                            z_stage_ghat=gs, x_threads=threads, y_threads=threads,
+                            z_threads=threads), precision)
+        assert t.schedule(precision)["z_threads"] == threads
+        y1 = t.matvec(0.4, x, kh, e, precision)
+        tol = 1e-12 if precision == "fp64" else 1e-6
+        assert np.abs(y1 - y0).max() <= tol * np.abs(y0).max(), (xl, yt, zt, gs)
+    with pytest.raises(B.DDAError):
+        t.set_schedule(dict(x_lines=8, y_tile=8, z_tile=3, z_pitch=9, z_stage_ghat=0,
+                            x_threads=64, y_threads=64, z_threads=64), precision)
+    with pytest.raises(B.DDAError):
+        t.set_schedule(dict(x_lines=8, y_tile=8, z_tile=8, z_pitch=24, z_stage_ghat=0,
+                            x_threads=48, y_threads=64, z_threads=64), precision)
     t.close()
