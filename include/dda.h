@@ -86,7 +86,10 @@ typedef enum {
  *  QMR      : quasi-minimal residual for complex-symmetric A (Freund 1992),
  *             the guide's QMRCCG: one matvec per iteration on the bilinear
  *             form x^T y (A = A^T for the DDA matrix); stops when the bound
- *             tau_k sqrt(k+1) >= ||E - A P_k|| reaches tol ||E||.
+ *             tau_k sqrt(k+1) >= ||E - A P_k|| reaches tol ||E||.  Where
+ *             r^T r vanishes (|r^T r| <= 1e-10 ||r||^2 in FP64, 1e-5 in FP32;
+ *             e.g. circularly polarized light, E . E = 0) it cannot go on; those
+ *             right-hand sides are finished by BiCGSTAB from QMR's iterate.
  * Either way the reported residual is the FP64 true residual of the result. */
 typedef enum { DDA_SOLVER_BICGSTAB = 0, DDA_SOLVER_QMR = 1 } dda_solver;
 
@@ -186,7 +189,7 @@ typedef struct {
   double* famp;    /* [n_inc][n_dirs+1][2 (m)][npol (l)][2] scattering amplitudes
                       f_ml (Sec. "Scattering by Finite Targets: The Mueller Matrix", eq. f_ml_def);
                       direction 0 is forward                                         */
-  int* iters;      /* [n_rhs] BiCGSTAB iterations (inner iterations when refined)   */
+  int* iters;      /* [n_rhs] Krylov iterations (inner iterations when refined)     */
   double* resid;   /* [n_rhs] final FP64 true relative residual ||E - A P|| / ||E||  */
   int* sweeps;     /* [n_rhs] FP64 refinement sweeps (1 when not refined)           */
   double t_setup_ms;   /* Green-tensor transform build in this call (0 if cached) */
@@ -276,6 +279,81 @@ dda_status dda_nearfield_box(const dda_target* t, const double* ext, int* dims, 
 dda_status dda_nearfield(dda_target* t, const dda_solve_params* p, const double* P,
                          const double* ext, double* E_inc, double* E_sca, double* E_macro,
                          double* B_inc, double* B_sca);
+
+/* ---- Scattering matrices and averages (Sec. "Averaging over Scattering
+ * Directions", "Scattering by Finite Targets: The Mueller Matrix",
+ * "Orientational Averaging").  Host-side helpers; no GPU needed except for
+ * dda_orient_average. ---------------------------------------------------- */
+
+/* The guide's set of scattering directions for averages over scattering angle
+ * at size parameter x = k a_eff and ETASCA eta (theta at equal steps of
+ * s = theta + theta/(theta + theta0), theta0 = 2 pi/(1 + x); N_phi(j) equally
+ * spaced azimuths from 0) and the solid angle Omega of each (they sum to 4 pi).
+ * Writes min(n, capacity) entries of theta_phi [n][2] (radians, Lab Frame) and
+ * omega [n] (either may be NULL) and returns n; -1 for x <= 0 or eta < 1e-3. */
+int64_t dda_scattering_directions(double x, double eta, int64_t capacity, double* theta_phi,
+                                  double* omega);
+
+/* Amplitude matrix S_1..S_4 and Mueller matrix S_ij (Bohren & Huffman) from the
+ * f_ml that dda_solve returns, for n directions:
+ *  f       : [n][2 (m)][2 (l)][2] f_ml of the two incident polarizations.
+ *  e01_lab : [3][2] incident polarization 1 in the Lab Frame (x component 0;
+ *            normalised here); e02 = x_LF x e01^*.
+ *  phi_s   : [n] azimuth of each direction's scattering plane (radians).
+ *  S       : [n][4][2] S_1..S_4, or NULL;  M : [n][4][4] S_ij row-major, or NULL.
+ * DDA_ERR_INVALID_ARG for a null input with n > 0 or an e01_lab along x_LF. */
+dda_status dda_mueller(int64_t n, const double* f, const double* e01_lab, const double* phi_s,
+                       double* S, double* M);
+
+/* Orientation samples (Sec. "Sampling in Theta, Phi, and beta"): range = (beta
+ * min, max, Theta min, max, Phi min, max) radians, n = (NBETA, NTHETA, NPHI),
+ * each 1..4096.  beta and Phi at interval midpoints; Theta uniform in
+ * cos(Theta) (midpoints for even NTHETA, end points for odd).  Weights: wbeta
+ * [NBETA] = 1/NBETA; wthetaphi [NTHETA][NPHI] = 1/(NTHETA NPHI) for even
+ * NTHETA, Simpson weights (1, 4, 2, ..., 4, 1)/(3 (NTHETA - 1) NPHI) for odd
+ * (each set sums to 1). */
+dda_status dda_orientation_grid(const double* range, const int* n, double* beta, double* theta,
+                                double* phi, double* wbeta, double* wthetaphi);
+
+typedef struct {
+  double kd;
+  double range[6];          /* beta, Theta, Phi (min, max), radians                     */
+  int n[3];                 /* NBETA, NTHETA, NPHI                                      */
+  const double* e01_lab;    /* [3][2] incident polarization 1, Lab Frame; NULL = y_LF    */
+  double tol;
+  int max_iter;
+  dda_precision precision;
+  int solver;               /* dda_solver                                               */
+  double eta;               /* > 0: averages over scattering directions (ETASCA)        */
+  int n_sel;                /* Lab-Frame directions for the Mueller matrix              */
+  const double* sel;        /* [n_sel][2] (theta_s, phi_s) radians                      */
+  int max_rhs;              /* right-hand sides per batched solve; 0 = all at once      */
+} dda_orient_params;
+
+typedef struct {
+  /* orientation averages for incident polarization l = 0 (e01), 1 (e02)               */
+  double Qext[2], Qabs[2], Qsca[2];   /* Q_sca = Q_ext - Q_abs                         */
+  double Qpha[2];                     /* (2 pi/k^2) Re f_ll(0) / (pi a_eff^2)          */
+  double Qsca_int[2];                 /* quadrature of dC_sca/dOmega (eta > 0)         */
+  double g[2][3];                     /* <n_LF> weighted by dC_sca/dOmega: g(1..3)     */
+  double cos2[2];                     /* <cos^2 theta_s>                               */
+  double Qbk[2];                      /* dC_sca/dOmega(theta = pi) / (pi a_eff^2)      */
+  double* mueller;                    /* [n_sel][4][4] averaged S_ij, caller's; or NULL */
+  int n_orient;                       /* orientations solved (NBETA NTHETA NPHI)       */
+  int64_t n_sca;                      /* directions in the angular averages            */
+  int64_t iters;                      /* Krylov iterations, all right-hand sides       */
+  double t_solve_ms;                  /* sum of the solves' device times               */
+} dda_orient_result;
+
+/* Average over target orientations (Sec. "Orientational Averaging"): every
+ * (beta, Theta, Phi) of the grid is an incidence of a batched solve (k along
+ * x_LF, polarizations e01_lab and x_LF x e01_lab^*, written in the Target Frame
+ * through the orientation), weighted by wbeta * wthetaphi.  Each orientation
+ * is solved: the guide's shortcut of combining two polarizations for other Phi
+ * holds only when alpha does not depend on the polarization (LDR's does).
+ * g and <cos^2> are averaged with weights Q_sca_int.  Returns the first
+ * non-OK status of the solves (DDA_ERR_NOCONV keeps the averages). */
+dda_status dda_orient_average(dda_target* t, const dda_orient_params* p, dda_orient_result* r);
 
 /* Number of occupied sites N of a target (-1 for NULL). */
 int64_t dda_target_num_dipoles(const dda_target* t);

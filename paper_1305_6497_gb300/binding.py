@@ -41,6 +41,21 @@ class SolveResult(ct.Structure):
                 ("kernel_ms", ct.c_double * 10), ("kernel_calls", ct.c_int64 * 10),
                 ("launches", ct.c_int64)]
 
+class OrientParams(ct.Structure):
+    _fields_ = [("kd", ct.c_double), ("range", ct.c_double * 6), ("n", ct.c_int * 3),
+                ("e01_lab", _dp), ("tol", ct.c_double), ("max_iter", ct.c_int),
+                ("precision", ct.c_int), ("solver", ct.c_int), ("eta", ct.c_double),
+                ("n_sel", ct.c_int), ("sel", _dp), ("max_rhs", ct.c_int)]
+
+
+class OrientResult(ct.Structure):
+    _fields_ = [("Qext", ct.c_double * 2), ("Qabs", ct.c_double * 2), ("Qsca", ct.c_double * 2),
+                ("Qpha", ct.c_double * 2), ("Qsca_int", ct.c_double * 2),
+                ("g", (ct.c_double * 3) * 2), ("cos2", ct.c_double * 2),
+                ("Qbk", ct.c_double * 2), ("mueller", _dp), ("n_orient", ct.c_int),
+                ("n_sca", ct.c_int64), ("iters", ct.c_int64), ("t_solve_ms", ct.c_double)]
+
+
 PASSES = ("x_fwd", "y_fwd", "z_mul", "y_inv", "x_inv")
 
 
@@ -88,6 +103,14 @@ def _load():
     lib.dda_matvec_noalloc.argtypes = [vp, ct.c_double, _dp, _dp, ct.c_void_p, ct.c_void_p,
                                        ct.c_int, ct.c_void_p]
     lib.dda_matvec_noalloc.restype = ct.c_int
+    lib.dda_scattering_directions.argtypes = [ct.c_double, ct.c_double, ct.c_int64, _dp, _dp]
+    lib.dda_scattering_directions.restype = ct.c_int64
+    lib.dda_mueller.argtypes = [ct.c_int64, _dp, _dp, _dp, _dp, _dp]
+    lib.dda_mueller.restype = ct.c_int
+    lib.dda_orientation_grid.argtypes = [_dp, _ip, _dp, _dp, _dp, _dp, _dp]
+    lib.dda_orientation_grid.restype = ct.c_int
+    lib.dda_orient_average.argtypes = [vp, ct.POINTER(OrientParams), ct.POINTER(OrientResult)]
+    lib.dda_orient_average.restype = ct.c_int
     lib.dda_nearfield_box.argtypes = [vp, _dp, _ip, _ip]
     lib.dda_nearfield_box.restype = ct.c_int
     lib.dda_nearfield.argtypes = [vp, ct.POINTER(SolveParams), _dp, _dp, _dp, _dp, _dp, _dp,
@@ -301,6 +324,66 @@ def dda_nearfield(h, kd, khat, e01, P, ext, npol=2, want=("E_inc", "E_sca", "E_m
     return out
 
 
+def dda_scattering_directions(x, eta):
+    """(theta [n], phi [n], omega [n]) of the averaging direction set."""
+    n = lib.dda_scattering_directions(float(x), float(eta), 0, None, None)
+    if n < 0:
+        raise DDAError(DDA_ERR_INVALID_ARG, "x must be > 0 and eta >= 1e-3")
+    tp = np.empty((n, 2))
+    om = np.empty(n)
+    lib.dda_scattering_directions(float(x), float(eta), n, _ptr(tp), _ptr(om))
+    return tp[:, 0].copy(), tp[:, 1].copy(), om
+
+
+def dda_mueller(f, e01_lab, phi_s):
+    """f [n, 2 (m), 2 (l)] complex, e01_lab [3] complex, phi_s [n] ->
+    (S [n, 4] complex S_1..S_4, M [n, 4, 4])."""
+    f = np.ascontiguousarray(f, np.complex128)
+    n = f.shape[0]
+    e = np.ascontiguousarray(e01_lab, np.complex128)
+    ph = np.ascontiguousarray(phi_s, np.float64)
+    S = np.empty((n, 4), np.complex128)
+    M = np.empty((n, 4, 4))
+    _check(lib.dda_mueller(n, _ptr(f.view(np.float64)), _ptr(e.view(np.float64)), _ptr(ph),
+                           _ptr(S.view(np.float64)), _ptr(M)))
+    return S, M
+
+
+def dda_orientation_grid(beta, nbeta, theta, ntheta, phi, nphi):
+    rng = np.array([beta[0], beta[1], theta[0], theta[1], phi[0], phi[1]], np.float64)
+    n = (ct.c_int * 3)(nbeta, ntheta, nphi)
+    b, t, p = np.empty(nbeta), np.empty(ntheta), np.empty(nphi)
+    wb, wa = np.empty(nbeta), np.empty((ntheta, nphi))
+    _check(lib.dda_orientation_grid(_ptr(rng), n, _ptr(b), _ptr(t), _ptr(p), _ptr(wb), _ptr(wa)))
+    return b, t, p, wb, wa
+
+
+def dda_orient_average(h, kd, beta=(0.0, 0.0), nbeta=1, theta=(0.0, 0.0), ntheta=1,
+                       phi=(0.0, 0.0), nphi=1, e01_lab=(0, 1, 0), tol=1e-8, max_iter=2000,
+                       precision="fp32_refined", solver="bicgstab", eta=0.0, sel=(),
+                       max_rhs=0) -> dict:
+    """Orientation-averaged efficiencies, angular averages and Mueller matrix."""
+    e = np.ascontiguousarray(e01_lab, np.complex128)
+    sl = np.ascontiguousarray(np.asarray(sel, np.float64).reshape(-1, 2))
+    prm = OrientParams(kd=float(kd), e01_lab=_ptr(e.view(np.float64)), tol=float(tol),
+                       max_iter=int(max_iter), precision=PREC[precision],
+                       solver=SOLVER[solver], eta=float(eta), n_sel=sl.shape[0],
+                       sel=_ptr(sl) if sl.shape[0] else None, max_rhs=int(max_rhs))
+    prm.range[:] = [beta[0], beta[1], theta[0], theta[1], phi[0], phi[1]]
+    prm.n[:] = [nbeta, ntheta, nphi]
+    mu = np.empty((sl.shape[0], 4, 4))
+    res = OrientResult(mueller=_ptr(mu) if sl.shape[0] else None)
+    st = lib.dda_orient_average(h, ct.byref(prm), ct.byref(res))
+    _check(st, (DDA_ERR_NOCONV,))
+    out = {k: np.array(getattr(res, k)[:]) for k in ("Qext", "Qabs", "Qsca", "Qpha",
+                                                      "Qsca_int", "cos2", "Qbk")}
+    out["g"] = np.array([list(res.g[0]), list(res.g[1])])
+    out["mueller"] = mu
+    out.update(status=st, n_orient=res.n_orient, n_sca=res.n_sca, iters=res.iters,
+               t_solve_ms=res.t_solve_ms)
+    return out
+
+
 class Target:
     """Owning wrapper around a dda_target handle."""
 
@@ -339,6 +422,9 @@ class Target:
 
     def hbm_bytes(self, kd, khat, e01, **kw):
         return dda_solve_hbm_bytes(self.h, kd, khat, e01, **kw)
+
+    def orient_average(self, kd, **kw):
+        return dda_orient_average(self.h, kd, **kw)
 
     def nearfield(self, kd, khat, e01, P, ext, **kw):
         return dda_nearfield(self.h, kd, khat, e01, P, ext, **kw)

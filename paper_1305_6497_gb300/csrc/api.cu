@@ -582,7 +582,11 @@ static void qmr(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R
   } else {
     CK(launch_qmr_init<T>(n, R, V.b, nullptr, V.r, q, d, part, st));
   }
-  CK(launch_qmr_state(R, nblk, part, ks, act, tol, max_iter, st));
+  // r^T r at the rounding level of the vectors' precision is numerically zero:
+  // a relative 1e-10 in FP64, 1e-5 in FP32 (where the products of FP32 values
+  // leave |r^T r| ~ 1e-7 ||r||^2 even when it vanishes exactly)
+  const double rho_floor = sizeof(T) == 4 ? 1e-5 : 1e-10;
+  CK(launch_qmr_state(R, nblk, part, ks, act, tol, max_iter, rho_floor, st));
   std::vector<int> hact(R);
   CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -658,15 +662,31 @@ static void qmr(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R
   }
 }
 
-// Krylov solve with the requested method.
+// Krylov solve with the requested method.  QMR's bilinear Lanczos process
+// breaks down when r^T r vanishes for r != 0 (circularly polarized incident
+// light makes E . E = 0 at every site); such right-hand sides are finished by
+// BiCGSTAB from QMR's last iterate (the others are already converged there
+// and take no further iterations).
 template <typename T>
 static void krylov(int solver, dda_target* t, const OpView<T>& op, const MatvecLaunch& L,
                    int R, const Vecs<T>& V, bool x_nonzero, double tol, int max_iter,
                    std::vector<int>& its, std::vector<int>& status, int64_t& matvecs) {
-  if (solver == DDA_SOLVER_QMR)
-    qmr<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
-  else
+  if (solver != DDA_SOLVER_QMR) {
     bicgstab<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
+    return;
+  }
+  qmr<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
+  bool broke = false;
+  int left = max_iter;
+  for (int r = 0; r < R; ++r)
+    if (status[r] == KS_BREAKDOWN) { broke = true; left = std::min(left, max_iter - its[r]); }
+  if (!broke || left < 1) return;
+  std::vector<int> its2, st2;
+  bicgstab<T>(t, op, L, R, V, true, tol, left, its2, st2, matvecs);
+  for (int r = 0; r < R; ++r) {
+    its[r] += its2[r];
+    status[r] = st2[r];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -743,7 +763,9 @@ static int64_t workspace_bytes(const dda_target* t, int R, dda_precision prec, i
   b += ns * 16;  // FP64 scratch (final/true residual matvec)
   if (f32) b += 8 * nv * 8 + ns * 8;
   const int nblk = std::max(reduce_blocks(3 * t->nbox), 3 * t->nz * t->ny);
-  b += (int64_t)std::max(4 * R, 6 * R * (ndir + 1)) * nblk * 8;
+  // Krylov partials [R][nblk][4]; far field, one incidence at a time: [2][ndir+1][fblk][6]
+  const int fblk = std::min(reduce_blocks(t->nbox), 304);
+  b += std::max((int64_t)4 * R * nblk, (int64_t)12 * (ndir + 1) * fblk) * 8;
   b += (int64_t)R * (sizeof(KState) + 64) + (int64_t)R * (t->nx + t->ny + t->nz + 8) * 16;
   b += (int64_t)(ndir + 1) * (t->nx + t->ny + t->nz) * 16 + t->N * (int64_t)R * 48;
   return b;
@@ -770,12 +792,13 @@ static void ensure_workspace(dda_target* t, int R, dda_precision prec, int ndir)
   const int rows = 3 * t->nz * t->ny;
   const int nblk = std::max({reduce_blocks(3 * t->nbox), (rows + t->L32.x_lines - 1) / t->L32.x_lines,
                              (rows + t->L64.x_lines - 1) / t->L64.x_lines});
-  w.partials.ensure((size_t)std::max(4 * R, 6 * R * (ndir + 1)) * nblk * 8);
+  const int fblk = std::min(reduce_blocks(t->nbox), 304);
+  w.partials.ensure((size_t)std::max((int64_t)4 * R * nblk, (int64_t)12 * (ndir + 1) * fblk) * 8);
   w.ks.ensure(sizeof(KState) * R);
   w.active.ensure(sizeof(int) * R);
   w.active_outer.ensure(sizeof(int) * R);
   w.norms.ensure(sizeof(double) * R);
-  w.sums.ensure(sizeof(double) * 6 * (size_t)std::max(R, R * (ndir + 1)));
+  w.sums.ensure(sizeof(double) * 6 * (size_t)std::max(R, 2 * (ndir + 1)));
   w.pol.ensure(sizeof(double2) * 3 * R);
   w.ph.ensure(sizeof(double2) * (size_t)R * (t->nx + t->ny + t->nz));
   w.ainv64.ensure(sizeof(double2) * (size_t)R * (t->ncomp + 1));
@@ -1740,6 +1763,149 @@ dda_status dda_matvec_noalloc(dda_target* t, double kd, const double* khat, cons
     return from_cuda(f);
   }
   return DDA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Orientation averages (Sec. "Orientational Averaging")
+// ---------------------------------------------------------------------------
+#include "scattering.h"
+
+extern "C" {
+
+dda_status dda_orient_average(dda_target* t, const dda_orient_params* p, dda_orient_result* r) {
+  g_last_error.clear();
+  if (!t || !p || !r) return fail(DDA_ERR_INVALID_ARG, "null argument");
+  for (int a = 0; a < 3; ++a)
+    if (p->n[a] < 1 || p->n[a] > 4096) return fail(DDA_ERR_INVALID_ARG, "NBETA, NTHETA, NPHI must be 1..4096");
+  if (p->n_sel < 0 || (p->n_sel > 0 && !p->sel)) return fail(DDA_ERR_INVALID_ARG, "bad sel");
+  if (p->max_rhs < 0) return fail(DDA_ERR_INVALID_ARG, "max_rhs must be >= 0");
+  dda_status s = check_kd(t, p->kd);
+  if (s != DDA_OK) return s;
+  const double pi = 3.14159265358979323846;
+  // incident polarization in the Lab Frame
+  cd el[3] = {0.0, 1.0, 0.0};
+  if (p->e01_lab)
+    for (int c = 0; c < 3; ++c) el[c] = cd(p->e01_lab[2 * c], p->e01_lab[2 * c + 1]);
+  double en = std::norm(el[0]) + std::norm(el[1]) + std::norm(el[2]);
+  if (!(en > 0.0) || std::abs(el[0]) > 1e-6 * std::sqrt(en))
+    return fail(DDA_ERR_INVALID_ARG, "e01_lab must be nonzero and transverse to x_LF");
+  for (int c = 0; c < 3; ++c) el[c] /= std::sqrt(en);
+  // orientations and weights
+  const int nb = p->n[0], nt = p->n[1], np = p->n[2];
+  std::vector<double> beta(nb), theta(nt), phi(np), wb(nb), wa((size_t)nt * np);
+  dda::orientation_grid(p->range, p->n, beta.data(), theta.data(), phi.data(), wb.data(),
+                        wa.data());
+  struct Ori { double b, th, ph, w; };
+  std::vector<Ori> ori;
+  for (int ib = 0; ib < nb; ++ib)
+    for (int it = 0; it < nt; ++it)
+      for (int ip = 0; ip < np; ++ip)
+        ori.push_back({beta[ib], theta[it], phi[ip], wb[ib] * wa[(size_t)it * np + ip]});
+  // scattering directions: the averaging set, then the selected ones
+  const double aeff = std::cbrt(3.0 * (double)t->N / (4.0 * pi));
+  const double geo = pi * aeff * aeff;
+  std::vector<double> sth, sph, som;
+  if (p->eta > 0) {
+    if (p->eta < 1e-3) return fail(DDA_ERR_INVALID_ARG, "eta must be >= 1e-3");
+    dda::scattering_directions(p->kd * aeff, p->eta, sth, sph, som);
+  }
+  const int64_t nsca = (int64_t)sth.size();
+  const int D = (int)nsca + p->n_sel;
+  std::vector<double> dirs(2 * (size_t)D);
+  for (int64_t i = 0; i < nsca; ++i) { dirs[2 * i] = sth[i]; dirs[2 * i + 1] = sph[i]; }
+  for (int i = 0; i < p->n_sel; ++i) {
+    dirs[2 * (nsca + i)] = p->sel[2 * i];
+    dirs[2 * (nsca + i) + 1] = p->sel[2 * i + 1];
+  }
+  // accumulators
+  double Qe[2] = {0, 0}, Qa[2] = {0, 0}, Qs[2] = {0, 0}, Qp[2] = {0, 0};
+  double Qi[2] = {0, 0}, G[2][3] = {{0, 0, 0}, {0, 0, 0}}, C2[2] = {0, 0}, Qb[2] = {0, 0};
+  std::vector<double> mu((size_t)16 * p->n_sel, 0.0);
+  int64_t iters = 0;
+  double tsolve = 0.0;
+  dda_status worst = DDA_OK;
+  const int per = p->max_rhs > 0 ? std::max(1, p->max_rhs / 2) : (int)ori.size();
+  const double k2 = p->kd * p->kd;
+  for (size_t o0 = 0; o0 < ori.size(); o0 += per) {
+    const int ni = (int)std::min<size_t>(per, ori.size() - o0);
+    std::vector<double> kh(3 * ni), yh(3 * ni), e1(6 * ni);
+    for (int i = 0; i < ni; ++i) {
+      double x[3], y[3], z[3];
+      dda::lab_axes(ori[o0 + i].th, ori[o0 + i].ph, ori[o0 + i].b, x, y, z);
+      for (int c = 0; c < 3; ++c) {
+        kh[3 * i + c] = x[c];
+        yh[3 * i + c] = y[c];
+        const cd e = el[1] * y[c] + el[2] * z[c];
+        e1[6 * i + 2 * c] = e.real();
+        e1[6 * i + 2 * c + 1] = e.imag();
+      }
+    }
+    dda_solve_params sp{};
+    sp.kd = p->kd; sp.n_inc = ni; sp.khat = kh.data(); sp.yhat = yh.data(); sp.e01 = e1.data();
+    sp.npol = 2; sp.tol = p->tol; sp.max_iter = p->max_iter; sp.precision = p->precision;
+    sp.inner_tol = 0.0; sp.n_dirs = D; sp.dirs = D ? dirs.data() : nullptr; sp.P0 = nullptr;
+    sp.profile = 0; sp.solver = p->solver;
+    const int R = 2 * ni;
+    std::vector<double> qe(R), qa(R), qs(R), fa((size_t)ni * (D + 1) * 2 * 2 * 2), rs(R);
+    std::vector<int> it(R), sw(R);
+    dda_solve_result sr{};
+    sr.Qext = qe.data(); sr.Qabs = qa.data(); sr.Qsca = qs.data(); sr.famp = fa.data();
+    sr.iters = it.data(); sr.resid = rs.data(); sr.sweeps = sw.data();
+    s = dda_solve(t, &sp, &sr);
+    if (s != DDA_OK && s != DDA_ERR_NOCONV) return s;
+    if (worst == DDA_OK) worst = s;
+    tsolve += sr.t_solve_ms;
+    for (int i = 0; i < R; ++i) iters += it[i];
+    // famp[i][d][m][l] complex
+    auto F = [&](int i, int d, int m, int l) {
+      const size_t o = ((((size_t)i * (D + 1) + d) * 2 + m) * 2 + l) * 2;
+      return cd(fa[o], fa[o + 1]);
+    };
+    std::vector<cd> f1(nsca), f2(nsca);
+    for (int i = 0; i < ni; ++i) {
+      const double w = ori[o0 + i].w;
+      for (int l = 0; l < 2; ++l) {
+        const int rr = 2 * i + l;
+        Qe[l] += w * qe[rr];
+        Qa[l] += w * qa[rr];
+        Qs[l] += w * qs[rr];
+        Qp[l] += w * (2.0 * pi / k2) * F(i, 0, l, l).real() / geo;
+        if (nsca) {
+          for (int64_t d = 0; d < nsca; ++d) { f1[d] = F(i, 1 + (int)d, 0, l); f2[d] = F(i, 1 + (int)d, 1, l); }
+          const dda::AngularAverages av = dda::angular_averages(
+              nsca, f1.data(), f2.data(), sth.data(), sph.data(), som.data(), p->kd, aeff);
+          Qi[l] += w * av.Qsca;
+          for (int c = 0; c < 3; ++c) G[l][c] += w * av.Qsca * av.g[c];
+          C2[l] += w * av.Qsca * av.cos2;
+          Qb[l] += w * av.Qbk;
+        }
+      }
+      for (int sidx = 0; sidx < p->n_sel; ++sidx) {
+        cd ff[2][2], S4[4];
+        for (int m = 0; m < 2; ++m)
+          for (int l = 0; l < 2; ++l) ff[m][l] = F(i, 1 + (int)nsca + sidx, m, l);
+        dda::amplitude_matrix(ff, el, p->sel[2 * sidx + 1], S4);
+        double M[16];
+        dda::mueller_matrix(S4, M);
+        for (int q = 0; q < 16; ++q) mu[(size_t)16 * sidx + q] += w * M[q];
+      }
+    }
+  }
+  for (int l = 0; l < 2; ++l) {
+    r->Qext[l] = Qe[l]; r->Qabs[l] = Qa[l]; r->Qsca[l] = Qs[l]; r->Qpha[l] = Qp[l];
+    r->Qsca_int[l] = Qi[l];
+    for (int c = 0; c < 3; ++c) r->g[l][c] = Qi[l] > 0 ? G[l][c] / Qi[l] : 0.0;
+    r->cos2[l] = Qi[l] > 0 ? C2[l] / Qi[l] : 0.0;
+    r->Qbk[l] = Qb[l];
+  }
+  if (r->mueller) std::copy(mu.begin(), mu.end(), r->mueller);
+  r->n_orient = (int)ori.size();
+  r->n_sca = nsca;
+  r->iters = iters;
+  r->t_solve_ms = tsolve;
+  return worst;
 }
 
 }  // extern "C"

@@ -75,6 +75,7 @@ struct KState {
   // that each iteration leaves for the next one's first pass
   double tau, theta;
   double2 qa1, qa2;
+  double rho_floor;  // |r^T r| <= rho_floor ||r||^2 counts as a breakdown
 };
 
 enum { KS_RUN = 0, KS_CONV = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3 };
@@ -159,7 +160,8 @@ cudaError_t launch_scalar_rho(int R, int nblk, const double* partials, KState* k
 // QMR building blocks.
 //  qmr_init:    r = b - ax (ax may be null), q = d = 0; partials of ||r||^2,
 //               ||b||^2, r^T r ([R][nblk][4])
-//  qmr_state:   tau = ||r||, theta = 0, rho = r^T r, beta = 0, no pending update
+//  qmr_state:   tau = ||r||, theta = 0, rho = r^T r, beta = 0, no pending update;
+//               |r^T r| <= rho_floor ||r||^2 (now or later) is a breakdown
 //  qmr_sigma:   alpha = rho / (q^T t) from the matvec partials
 //  qmr_update_r: r -= alpha t; partials of ||r||^2, r^T r ([R][nblk][4])
 //  qmr_scalar:  rotation, pending update coefficients, convergence on the
@@ -170,7 +172,8 @@ cudaError_t launch_qmr_init(int64_t n, int R, const cplx_t<T>* b, const cplx_t<T
                             cplx_t<T>* r, cplx_t<T>* q, cplx_t<T>* d, double* partials,
                             cudaStream_t st);
 cudaError_t launch_qmr_state(int R, int nblk, const double* partials, KState* ks,
-                             int* active, double tol, int max_iter, cudaStream_t st);
+                             int* active, double tol, int max_iter, double rho_floor,
+                             cudaStream_t st);
 cudaError_t launch_qmr_sigma(int R, int nblk, const double* partials, KState* ks,
                              int* active, cudaStream_t st);
 template <typename T>

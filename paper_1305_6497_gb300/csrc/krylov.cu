@@ -366,6 +366,7 @@ cudaError_t launch_scalar_rho(int R, int nblk, const double* partials, KState* k
 // and ||b - A x_k|| <= tau_k sqrt(k + 1) bounds the true residual.  The
 // d/x/q updates of one iteration run in the next iteration's first FFT pass;
 // the last one is applied by k_qmr_flush.
+
 template <typename T>
 __global__ void k_qmr_init(int64_t n, const cplx_t<T>* __restrict__ b,
                            const cplx_t<T>* __restrict__ ax, cplx_t<T>* __restrict__ r,
@@ -402,7 +403,7 @@ cudaError_t launch_qmr_init(int64_t n, int R, const cplx_t<T>* b, const cplx_t<T
 }
 
 __global__ void k_qmr_state(int nblk, const double* partials, KState* ks, int* active,
-                            double tol, int max_iter) {
+                            double tol, int max_iter, double rho_floor) {
   const int r = blockIdx.x;
   double tot[4];
   sum_partials<4>(partials, nblk, r, tot);
@@ -423,18 +424,22 @@ __global__ void k_qmr_state(int nblk, const double* partials, KState* ks, int* a
     k.iters = 0;
     k.max_iter = max_iter;
     k.active_unused = 0;
+    k.rho_floor = rho_floor;
     const bool done = !(k.rnorm2 > k.tol2 * k.bnorm2);
     k.status = done ? KS_CONV : KS_RUN;
+    // r^T r can vanish for r != 0 (e.g. circularly polarized E_inc has
+    // E_j . E_j = 0 at every site): the bilinear Lanczos process cannot start
     if (!isfinite(k.rnorm2) || !finite2(k.rho)) k.status = KS_BREAKDOWN;
-    else if (!done && k.rho.x == 0.0 && k.rho.y == 0.0) k.status = KS_BREAKDOWN;
+    else if (!done && hypot(k.rho.x, k.rho.y) <= k.rho_floor * k.rnorm2) k.status = KS_BREAKDOWN;
     ks[r] = k;
     active[r] = k.status == KS_RUN ? 1 : 0;
   }
 }
 
 cudaError_t launch_qmr_state(int R, int nblk, const double* partials, KState* ks,
-                             int* active, double tol, int max_iter, cudaStream_t st) {
-  k_qmr_state<<<R, kThreads, 0, st>>>(nblk, partials, ks, active, tol, max_iter);
+                             int* active, double tol, int max_iter, double rho_floor,
+                             cudaStream_t st) {
+  k_qmr_state<<<R, kThreads, 0, st>>>(nblk, partials, ks, active, tol, max_iter, rho_floor);
   note_launch();
   return cudaGetLastError();
 }
@@ -524,7 +529,7 @@ __global__ void k_qmr_scalar(int nblk, const double* partials, KState* ks, int* 
     if (tau * tau * (k.iters + 1) <= k.tol2 * k.bnorm2) {
       k.status = KS_CONV; active[r] = 0; return;
     }
-    if (!finite2(rho_new) || (rho_new.x == 0.0 && rho_new.y == 0.0)) {
+    if (!finite2(rho_new) || hypot(rho_new.x, rho_new.y) <= k.rho_floor * rn2) {
       k.status = KS_BREAKDOWN; active[r] = 0; return;
     }
     if (k.iters >= k.max_iter) {

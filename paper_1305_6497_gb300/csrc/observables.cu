@@ -8,6 +8,8 @@
 // On the lattice exp(-i k n.r_j) = ex(ix) ey(iy) ez(iz), so the phases come
 // from three short per-axis tables and no transcendental is evaluated per site.
 // All sums are FP64, two-stage and deterministic.
+#include <algorithm>
+
 #include "dda_ops.h"
 #include "reduce.cuh"
 
@@ -57,8 +59,8 @@ cudaError_t launch_cross_sections(int nx, int ny, int nz, const uint8_t* comp, R
 __global__ void k_farfield(int nx, int ny, int nz, const uint8_t* __restrict__ comp,
                            const double2* __restrict__ P, const double2* __restrict__ fphx,
                            const double2* __restrict__ fphy, const double2* __restrict__ fphz,
-                           double* partials) {
-  const int r = blockIdx.y, d = blockIdx.z, R = gridDim.y;
+                           double* partials, int d0) {
+  const int r = blockIdx.y, d = d0 + (int)blockIdx.z, R = gridDim.y;
   const int64_t nbox = (int64_t)nx * ny * nz;
   double acc[6] = {0, 0, 0, 0, 0, 0};
   GRID_LOOP(i, nbox) {
@@ -89,9 +91,12 @@ cudaError_t launch_farfield(int nx, int ny, int nz, const uint8_t* comp, int R, 
                             const double2* P, const double2* fphx, const double2* fphy,
                             const double2* fphz, double* partials, int nblk,
                             cudaStream_t st) {
-  dim3 g(nblk, R, D);
-  k_farfield<<<g, kThreads, 0, st>>>(nx, ny, nz, comp, P, fphx, fphy, fphz, partials);
-  note_launch();
+  // grid.z is limited to 65535 directions per launch
+  for (int d0 = 0; d0 < D; d0 += 65535) {
+    dim3 g(nblk, R, std::min(65535, D - d0));
+    k_farfield<<<g, kThreads, 0, st>>>(nx, ny, nz, comp, P, fphx, fphy, fphz, partials, d0);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 

@@ -230,3 +230,23 @@ def test_unknown_solver_code_is_rejected_by_the_library(B):
     assert B.lib.dda_solve(t.h, ct.byref(prm), ct.byref(res)) == B.DDA_ERR_INVALID_ARG
     assert "solver" in B.dda_last_error()
     t.close()
+
+
+def test_qmr_circular_polarization_falls_back_and_converges(B):
+    """Circularly polarized light has E_j . E_j = 0 at every site, so QMR's
+    bilinear Lanczos process breaks down at once; the library finishes those
+    right-hand sides with BiCGSTAB and the result equals BiCGSTAB's and the
+    oracle's."""
+    w = W.small_ellipsoid(5, 6, 4, m=1.6 + 0.1j, kd=0.5, method="FCD")
+    x, y = np.array([1.0, 0, 0]), np.array([0, 1.0, 0])
+    e = np.array([0, 1, 1j]) / np.sqrt(2)
+    t = B.Target(w.occ, w.comp, w.m, method="FCD")
+    for precision in ("fp64", "fp32_refined"):
+        q = t.solve(w.kd, x, e, yhat=y, tol=1e-10, precision=precision, solver="qmr")
+        b = t.solve(w.kd, x, e, yhat=y, tol=1e-10, precision=precision)
+        assert q["status"] == B.DDA_OK
+        assert np.all(q["resid"] <= 1e-10)
+        assert np.allclose(q["Qext"], b["Qext"], rtol=1e-8)
+    ref = O.solve_target(w.occ, w.comp, w.m, w.kd, x, y, e, "FCD", npol=2, tol=1e-12)
+    assert np.allclose(q["Qext"], ref["Qext"], rtol=1e-6)
+    t.close()
