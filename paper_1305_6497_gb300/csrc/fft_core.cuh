@@ -26,26 +26,46 @@
 namespace dda {
 
 // ---- radix-R DFTs in registers (forward: exp(-2 pi i nk/R); INV: conjugate) --
-template <bool INV, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+// HIN: the upper half of the inputs is known to be zero (zero padding: a
+// transform of n <= L/2 values, first forward stage); HOUT: only the lower
+// half of the outputs is wanted (pruned output, last inverse stage).  The
+// skipped terms are exact zeros or unused results, so the kept outputs are
+// bit-identical to the full transform's.
+template <bool INV, bool HIN = false, bool HOUT = false, typename C>
+__device__ __forceinline__ void dft2(C& a, C& b) {
+  if (HIN) { b = a; return; }
+  if (HOUT) { a = cadd(a, b); return; }
   C t = csub(a, b); a = cadd(a, b); b = t;
 }
 
-template <bool INV, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+template <bool INV, bool HIN = false, bool HOUT = false, typename C>
+__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  if (HIN) {  // a2 = a3 = 0
+    const C d13 = cmul_i<INV>(a1);
+    const C s = a0;
+    if (!HOUT) { a2 = csub(s, a1); a3 = csub(s, d13); }
+    a0 = cadd(s, a1);
+    a1 = cadd(s, d13);
+    return;
+  }
   C s02 = cadd(a0, a2), d02 = csub(a0, a2);
   C s13 = cadd(a1, a3), d13 = cmul_i<INV>(csub(a1, a3));
   a0 = cadd(s02, s13);
-  a2 = csub(s02, s13);
   a1 = cadd(d02, d13);
-  a3 = csub(d02, d13);
+  if (!HOUT) {
+    a2 = csub(s02, s13);
+    a3 = csub(d02, d13);
+  }
 }
 
-template <bool INV, typename C> __device__ __forceinline__ void dft8(C (&a)[8]) {
+template <bool INV, bool HIN = false, bool HOUT = false, typename C>
+__device__ __forceinline__ void dft8(C (&a)[8]) {
   using T = decltype(a[0].x);
   const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
   C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
   C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
-  dft4<INV>(e0, e1, e2, e3);
-  dft4<INV>(o0, o1, o2, o3);
+  dft4<INV, HIN>(e0, e1, e2, e3);
+  dft4<INV, HIN>(o0, o1, o2, o3);
   // W^1 = (1 -/+ i)/sqrt2, W^2 = -/+ i, W^3 = (-1 -/+ i)/sqrt2
   C w1, w3;
   if (INV) {
@@ -56,10 +76,14 @@ template <bool INV, typename C> __device__ __forceinline__ void dft8(C (&a)[8]) 
     w3.x = h * (o3.y - o3.x); w3.y = -h * (o3.x + o3.y);
   }
   C w2 = cmul_i<INV>(o2);
-  a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
-  a[1] = cadd(e1, w1); a[5] = csub(e1, w1);
-  a[2] = cadd(e2, w2); a[6] = csub(e2, w2);
-  a[3] = cadd(e3, w3); a[7] = csub(e3, w3);
+  if (!HOUT) {
+    a[4] = csub(e0, o0); a[5] = csub(e1, w1);
+    a[6] = csub(e2, w2); a[7] = csub(e3, w3);
+  }
+  a[0] = cadd(e0, o0);
+  a[1] = cadd(e1, w1);
+  a[2] = cadd(e2, w2);
+  a[3] = cadd(e3, w3);
 }
 
 template <bool INV, typename C> __device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
@@ -109,8 +133,10 @@ __device__ __forceinline__ C rot(C a, T c, T s) {
 }
 
 // 16 = 4 x 4: DFT4 over n1 for each n2, twiddle w16^(n2 k1), DFT4 over n2;
-// X[k1 + 4 k2] ends in a[k1 + 4 k2].
-template <bool INV, typename C> __device__ __forceinline__ void dft16(C (&a)[16]) {
+// X[k1 + 4 k2] ends in a[k1 + 4 k2].  With HIN the inputs n1 = 2, 3 are zero;
+// with HOUT only k2 = 0, 1 are formed.
+template <bool INV, bool HIN = false, bool HOUT = false, typename C>
+__device__ __forceinline__ void dft16(C (&a)[16]) {
   using T = decltype(a[0].x);
   const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;  // pi/8
   const T h = (T)0.70710678118654752440;
@@ -118,7 +144,7 @@ template <bool INV, typename C> __device__ __forceinline__ void dft16(C (&a)[16]
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2) {
     C b0 = a[n2], b1 = a[4 + n2], b2 = a[8 + n2], b3 = a[12 + n2];
-    dft4<INV>(b0, b1, b2, b3);
+    dft4<INV, HIN>(b0, b1, b2, b3);
     y[n2][0] = b0; y[n2][1] = b1; y[n2][2] = b2; y[n2][3] = b3;
   }
   // twiddles w16^(n2 k1): (1,1)=1, (1,2)=2, (1,3)=3, (2,1)=2, (2,2)=4, (2,3)=6,
@@ -135,8 +161,9 @@ template <bool INV, typename C> __device__ __forceinline__ void dft16(C (&a)[16]
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
     C b0 = y[0][k1], b1 = y[1][k1], b2 = y[2][k1], b3 = y[3][k1];
-    dft4<INV>(b0, b1, b2, b3);
-    a[k1] = b0; a[k1 + 4] = b1; a[k1 + 8] = b2; a[k1 + 12] = b3;
+    dft4<INV, false, HOUT>(b0, b1, b2, b3);
+    a[k1] = b0; a[k1 + 4] = b1;
+    if (!HOUT) { a[k1 + 8] = b2; a[k1 + 12] = b3; }
   }
 }
 
@@ -147,6 +174,16 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C (&v
   else if constexpr (R == 5) dft5<INV>(v);
   else if constexpr (R == 8) dft8<INV>(v);
   else dft16<INV>(v);
+}
+
+// Even radices only: HIN -- v[R/2 ..] are zero; HOUT -- only v[0 .. R/2) wanted.
+template <int R, bool INV, bool HIN, bool HOUT, typename C>
+__device__ __forceinline__ void dft_half(C (&v)[R]) {
+  static_assert(R % 2 == 0, "half transforms need an even radix");
+  if constexpr (R == 2) dft2<INV, HIN, HOUT>(v[0], v[1]);
+  else if constexpr (R == 4) dft4<INV, HIN, HOUT>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<INV, HIN, HOUT>(v);
+  else dft16<INV, HIN, HOUT>(v);
 }
 
 // ---- one in-place stage ------------------------------------------------------
@@ -227,17 +264,33 @@ __device__ void fft_smem(C* s, int nlines, int pstride, const AxisPlan& P,
 // Consecutive threads take consecutive lines, so with lines = consecutive
 // columns of a row-major plane every global access is coalesced.
 
+// With half (needs an even R): the caller guarantees that positions >= L/2 of
+// every input line are zero, so only the lower half of each butterfly's inputs
+// is read and the transform skips the zero terms.
 template <typename C, int R, class LD>
 __device__ __forceinline__ void stage_first_fwd(C* s, int nlines, int ps, int L,
-                                                const C* __restrict__ tw, const LD& ld) {
+                                                const C* __restrict__ tw, const LD& ld,
+                                                bool half = false) {
   const int S = L / R;
   const int nb = nlines * S;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     const int line = b % nlines, j = b / nlines;
     C v[R];
+    if constexpr (R % 2 == 0) {
+      if (half) {
 #pragma unroll
-    for (int i = 0; i < R; ++i) v[i] = ld(line, j + i * S);
-    dft<R, false>(v);
+        for (int i = 0; i < R / 2; ++i) v[i] = ld(line, j + i * S);
+        dft_half<R, false, true, false>(v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = ld(line, j + i * S);
+        dft<R, false>(v);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[i] = ld(line, j + i * S);
+      dft<R, false>(v);
+    }
     if (j > 0) {
 #pragma unroll
       for (int m = 1; m < R; ++m) v[m] = cmul(v[m], __ldg(&tw[j * (R - 1) + (m - 1)]));
@@ -248,9 +301,12 @@ __device__ __forceinline__ void stage_first_fwd(C* s, int nlines, int ps, int L,
   __syncthreads();
 }
 
+// With half (needs an even R): the caller keeps only positions < L/2 of every
+// output line, so each butterfly forms and stores only its lower half.
 template <typename C, int R, class ST>
 __device__ __forceinline__ void stage_last_inv(const C* s, int nlines, int ps, int L,
-                                               const C* __restrict__ tw, const ST& st) {
+                                               const C* __restrict__ tw, const ST& st,
+                                               bool half = false) {
   const int S = L / R;
   const int nb = nlines * S;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -261,6 +317,14 @@ __device__ __forceinline__ void stage_last_inv(const C* s, int nlines, int ps, i
     if (j > 0) {
 #pragma unroll
       for (int m = 1; m < R; ++m) v[m] = cmulc(__ldg(&tw[j * (R - 1) + (m - 1)]), v[m]);
+    }
+    if constexpr (R % 2 == 0) {
+      if (half) {
+        dft_half<R, true, false, true>(v);
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) st(line, j + i * S, v[i]);
+        continue;
+      }
     }
     dft<R, true>(v);
 #pragma unroll
@@ -310,22 +374,26 @@ __device__ __forceinline__ void fft_inner_stages(C* s, int nlines, int ps, const
 
 // Forward transform of lines read from global memory, results written to
 // global memory (needs nstage >= 2).
+// half: the input lines hold at most L/2 values (zero above), see stage_first_fwd.
 template <typename C, class LD, class ST>
 __device__ void fft_global_fwd(C* s, int nlines, int ps, const AxisPlan& P,
-                               const C* __restrict__ tw, const LD& ld, const ST& st) {
-  DDA_RADIX_DISPATCH(P.radix[0], (stage_first_fwd<C, RR>(s, nlines, ps, P.L, tw, ld)));
+                               const C* __restrict__ tw, const LD& ld, const ST& st,
+                               bool half = false) {
+  DDA_RADIX_DISPATCH(P.radix[0], (stage_first_fwd<C, RR>(s, nlines, ps, P.L, tw, ld, half)));
   fft_inner_stages<C, false>(s, nlines, ps, P, tw);
   DDA_RADIX_DISPATCH(P.radix[P.nstage - 1], (stage_last_fwd<C, RR>(s, nlines, ps, P.L, st)));
 }
 
 // Inverse transform of lines read from global memory (digit-reversed), natural
 // order results written to global memory (needs nstage >= 2).
+// half: only the first L/2 outputs of each line are kept, see stage_last_inv.
 template <typename C, class LD, class ST>
 __device__ void fft_global_inv(C* s, int nlines, int ps, const AxisPlan& P,
-                               const C* __restrict__ tw, const LD& ld, const ST& st) {
+                               const C* __restrict__ tw, const LD& ld, const ST& st,
+                               bool half = false) {
   DDA_RADIX_DISPATCH(P.radix[P.nstage - 1], (stage_first_inv<C, RR>(s, nlines, ps, P.L, ld)));
   fft_inner_stages<C, true>(s, nlines, ps, P, tw);
-  DDA_RADIX_DISPATCH(P.radix[0], (stage_last_inv<C, RR>(s, nlines, ps, P.L, tw, st)));
+  DDA_RADIX_DISPATCH(P.radix[0], (stage_last_inv<C, RR>(s, nlines, ps, P.L, tw, st, half)));
 }
 
 }  // namespace dda

@@ -147,8 +147,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_y(OpView<T>
   ColIO<C> in{base, Lx, ncol, INV ? Ly : op.ny};
   ColIO<C> out{base, Lx, ncol, INV ? op.ny : Ly};
   if (op.py.nstage >= 2) {
-    if (INV) fft_global_inv<C>(s, tile, tile, op.py, op.twy, in, out);
-    else fft_global_fwd<C>(s, tile, tile, op.py, op.twy, in, out);
+    // ny of the Ly rows carry data (forward input, inverse output)
+    const bool half = 2 * op.ny <= Ly;
+    if (INV) fft_global_inv<C>(s, tile, tile, op.py, op.twy, in, out, half);
+    else fft_global_fwd<C>(s, tile, tile, op.py, op.twy, in, out, half);
     return;
   }
   // one stage (Ly <= 16) or none: through shared memory
@@ -347,7 +349,8 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
   const AxisPlan& P = op.pz;
   const int last = P.nstage - 1;
   if (P.nstage >= 2) {
-    DDA_RADIX_DISPATCH(P.radix[0], (stage_first_fwd<C, RR>(s, NL, ps, Lz, op.twz, io)));
+    DDA_RADIX_DISPATCH(P.radix[0], (stage_first_fwd<C, RR>(s, NL, ps, Lz, op.twz, io,
+                                                          2 * nz <= Lz)));
     fft_inner_stages<C, false>(s, NL, ps, P, op.twz);
   } else {
     for (int e = threadIdx.x; e < Lz * NL; e += blockDim.x) {
@@ -374,7 +377,8 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
   }
   if (P.nstage >= 2) {
     fft_inner_stages<C, true>(s, NL, ps, P, op.twz);
-    DDA_RADIX_DISPATCH(P.radix[0], (stage_last_inv<C, RR>(s, NL, ps, Lz, op.twz, io)));
+    DDA_RADIX_DISPATCH(P.radix[0], (stage_last_inv<C, RR>(s, NL, ps, Lz, op.twz, io,
+                                                         2 * nz <= Lz)));
   } else {
     for (int e = threadIdx.x; e < Lz * NL; e += blockDim.x) {
       const int p = e / NL, l = e - p * NL;
