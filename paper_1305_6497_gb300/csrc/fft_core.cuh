@@ -187,33 +187,43 @@ __device__ __forceinline__ void dft_half(C (&v)[R]) {
 }
 
 // ---- one in-place stage ------------------------------------------------------
-template <typename C, int R, bool INV>
+// HALF (even R, block B = L only, i.e. the first forward stage or the last
+// inverse one): forward -- positions >= L/2 hold zeros and are not read;
+// inverse -- only positions < L/2 are formed and written.
+template <typename C, int R, bool INV, bool HALF = false>
 __device__ __forceinline__ void fft_stage(C* s, int nlines, int pstride, int L, int B,
                                           unsigned long long sdiv, const C* __restrict__ tw) {
   const int S = B / R;
   const int nb = nlines * (L / R);
+  constexpr int RH = HALF ? R / 2 : R;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     const int line = b % nlines, q = b / nlines;
     const int blk = fast_div(q, sdiv), j = q - blk * S;
     C* base = s + (blk * B + j) * pstride + line;
     C v[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) v[i] = base[i * S * pstride];
     if (!INV) {
-      dft<R, false>(v);
+#pragma unroll
+      for (int i = 0; i < RH; ++i) v[i] = base[i * S * pstride];
+      if constexpr (HALF) dft_half<R, false, true, false>(v);
+      else dft<R, false>(v);
       if (j > 0) {
 #pragma unroll
         for (int m = 1; m < R; ++m) v[m] = cmul(v[m], __ldg(&tw[j * (R - 1) + (m - 1)]));
       }
+#pragma unroll
+      for (int i = 0; i < R; ++i) base[i * S * pstride] = v[i];
     } else {
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[i] = base[i * S * pstride];
       if (j > 0) {
 #pragma unroll
         for (int m = 1; m < R; ++m) v[m] = cmulc(__ldg(&tw[j * (R - 1) + (m - 1)]), v[m]);
       }
-      dft<R, true>(v);
-    }
+      if constexpr (HALF) dft_half<R, true, false, true>(v);
+      else dft<R, true>(v);
 #pragma unroll
-    for (int i = 0; i < R; ++i) base[i * S * pstride] = v[i];
+      for (int i = 0; i < RH; ++i) base[i * S * pstride] = v[i];
+    }
   }
   __syncthreads();
 }
@@ -238,20 +248,42 @@ __device__ __forceinline__ void fft_stage(C* s, int nlines, int pstride, int L, 
     default: { constexpr int RR = 5; BODY; } break;     \
   }
 
-template <typename C, bool INV, int R>
+template <typename C, bool INV, int R, bool HALF = false>
 __device__ __forceinline__ void run_stage(C* s, int nlines, int pstride, const AxisPlan& P,
                                           int st, const C* __restrict__ tw) {
-  fft_stage<C, R, INV>(s, nlines, pstride, P.L, P.blk[st], P.sdiv[st], tw + P.tw_off[st]);
+  fft_stage<C, R, INV, HALF>(s, nlines, pstride, P.L, P.blk[st], P.sdiv[st],
+                             tw + P.tw_off[st]);
+}
+
+template <typename C, bool INV, int R>
+__device__ __forceinline__ void run_stage_half(C* s, int nlines, int pstride,
+                                               const AxisPlan& P, int st,
+                                               const C* __restrict__ tw, bool half) {
+  if constexpr (R % 2 == 0) {
+    if (half) {
+      run_stage<C, INV, R, true>(s, nlines, pstride, P, st, tw);
+      return;
+    }
+  }
+  run_stage<C, INV, R, false>(s, nlines, pstride, P, st, tw);
 }
 
 // Full transform of `nlines` lines in shared memory, in place.  Forward: natural
 // -> digit-reversed; inverse (unnormalized): digit-reversed -> natural.
+// half: forward -- every line has zeros at positions >= L/2 (the caller need
+// not write them); inverse -- only positions < L/2 are wanted (the others are
+// left undefined).
 template <typename C, bool INV>
 __device__ void fft_smem(C* s, int nlines, int pstride, const AxisPlan& P,
-                         const C* __restrict__ tw) {
+                         const C* __restrict__ tw, bool half = false) {
   for (int k = 0; k < P.nstage; ++k) {
     const int st = INV ? P.nstage - 1 - k : k;
-    DDA_RADIX_DISPATCH(P.radix[st], (run_stage<C, INV, RR>(s, nlines, pstride, P, st, tw)));
+    if (st == 0) {  // block L: the stage the pruning applies to
+      DDA_RADIX_DISPATCH(P.radix[0],
+                         (run_stage_half<C, INV, RR>(s, nlines, pstride, P, 0, tw, half)));
+    } else {
+      DDA_RADIX_DISPATCH(P.radix[st], (run_stage<C, INV, RR>(s, nlines, pstride, P, st, tw)));
+    }
   }
 }
 

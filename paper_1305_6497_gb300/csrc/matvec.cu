@@ -94,12 +94,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_fwd(OpVie
     }
     s[p * ps + line] = val;
   }
-  for (int e = threadIdx.x; e < nlines * (Lx - nx); e += blockDim.x) {
+  // padding: with at most Lx/2 values per row (and an even first radix) the
+  // first stage never reads positions >= Lx/2, so only nx .. Lx/2 - 1 are zeroed
+  const bool half = 2 * nx <= Lx && op.px.radix[0] % 2 == 0;
+  const int zend = half ? Lx / 2 : Lx;
+  for (int e = threadIdx.x; e < nlines * (zend - nx); e += blockDim.x) {
     const int line = e % nlines, p = nx + e / nlines;
     s[p * ps + line] = mk<C>(0, 0);
   }
   __syncthreads();
-  fft_smem<C, false>(s, nlines, ps, op.px, op.twx);
+  fft_smem<C, false>(s, nlines, ps, op.px, op.twx, half);
   const int64_t plane_sz = (int64_t)op.Ly * Lx;
   C* dst = buf + (int64_t)r * 3 * op.nz * plane_sz;
 #pragma unroll 4
@@ -441,7 +445,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_inv(OpVie
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
-  fft_smem<C, true>(s, nlines, ps, op.px, op.twx);
+  // only positions < nx <= Lx/2 are used below
+  fft_smem<C, true>(s, nlines, ps, op.px, op.twx, 2 * nx <= Lx);
   const C* ai = op.ainv + (int64_t)r * op.ncomp1;
   C* yr = yout + g0;
   ChunkAcc<T, 4> acc;
