@@ -42,7 +42,7 @@ template <typename T> struct XinArgs {
 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_fwd(OpView<T> op, const cplx_t<T>* __restrict__ in,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpView<T> op, const cplx_t<T>* __restrict__ in,
                             cplx_t<T>* __restrict__ buf, int nlines,
                             const int* __restrict__ active, XinArgs<T> xa) {
   using C = cplx_t<T>;
@@ -66,33 +66,59 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_fwd(OpVie
     c2 = mk<C>(xa.ks[r].qa1.x, xa.ks[r].qa1.y);
     c3 = mk<C>(xa.ks[r].qa2.x, xa.ks[r].qa2.y);
   }
-  // the CTA's rows are one contiguous chunk of the box vector
+  // the CTA's rows are one contiguous chunk of the box vector.  Elements go in
+  // batches of U per thread with every load of a batch issued before any
+  // store (the prologue writes vectors the next elements read from, so
+  // without this split each thread would wait on one element at a time).
   const int nin = min(nlines, rows - row0) * nx;
   const int64_t g0 = off + (int64_t)row0 * nx;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < nlines * nx; e += blockDim.x) {
-    const int line = fast_div(e, op.div_nx), p = e - line * nx;
-    C val = mk<C>(0, 0);
-    if (e < nin) {
-      const int64_t g = g0 + e;
-      if (MODE == XIN_PLAIN) {
-        val = in[g];
-      } else if (MODE == XIN_P) {
-        val = cadd(xa.r[g], cmul(c1, csub(xa.pv[g], cmul(c2, xa.v[g]))));
-        xa.pv[g] = val;
-      } else if (MODE == XIN_Q) {
-        const C q = xa.pv[g];
-        const C dn = cadd(cmul(c2, xa.d[g]), cmul(c3, q));
-        xa.d[g] = dn;
-        xa.x[g] = cadd(xa.x[g], dn);
-        val = cadd(xa.r[g], cmul(c1, q));
-        xa.pv[g] = val;
-      } else {
-        val = csub(xa.r[g], cmul(c1, xa.v[g]));
-        xa.pv[g] = val;
+  constexpr int U = 4;
+  const int total = nlines * nx;
+  for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+    C va[U], vb[U], vc[U], vd[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < nin) {
+        const int64_t g = g0 + e;
+        if (MODE == XIN_PLAIN) {
+          va[u] = in[g];
+        } else if (MODE == XIN_P) {
+          va[u] = xa.r[g]; vb[u] = xa.pv[g]; vc[u] = xa.v[g];
+        } else if (MODE == XIN_Q) {
+          va[u] = xa.r[g]; vb[u] = xa.pv[g]; vc[u] = xa.d[g]; vd[u] = xa.x[g];
+        } else {
+          va[u] = xa.r[g]; vc[u] = xa.v[g];
+        }
       }
     }
-    s[p * ps + line] = val;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e >= total) break;
+      const int line = fast_div(e, op.div_nx), p = e - line * nx;
+      C val = mk<C>(0, 0);
+      if (e < nin) {
+        const int64_t g = g0 + e;
+        if (MODE == XIN_PLAIN) {
+          val = va[u];
+        } else if (MODE == XIN_P) {
+          val = cadd(va[u], cmul(c1, csub(vb[u], cmul(c2, vc[u]))));
+          xa.pv[g] = val;
+        } else if (MODE == XIN_Q) {
+          const C q = vb[u];
+          const C dn = cadd(cmul(c2, vc[u]), cmul(c3, q));
+          xa.d[g] = dn;
+          xa.x[g] = cadd(vd[u], dn);
+          val = cadd(va[u], cmul(c1, q));
+          xa.pv[g] = val;
+        } else {
+          val = csub(va[u], cmul(c1, vc[u]));
+          xa.pv[g] = val;
+        }
+      }
+      s[p * ps + line] = val;
+    }
   }
   // padding: with at most Lx/2 values per row (and an even first radix) the
   // first stage never reads positions >= Lx/2, so only nx .. Lx/2 - 1 are zeroed
@@ -406,7 +432,7 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
 enum { XOUT_PLAIN = 0, XOUT_RV = 1, XOUT_TS = 2, XOUT_QT = 3, XOUT_FIELD = 4 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_inv(OpView<T> op, const cplx_t<T>* __restrict__ buf,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpView<T> op, const cplx_t<T>* __restrict__ buf,
                             const cplx_t<T>* __restrict__ xin, cplx_t<T>* __restrict__ yout,
                             int nlines, const int* __restrict__ active,
                             const cplx_t<T>* __restrict__ rhat, double* __restrict__ partials) {
@@ -450,15 +476,32 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_inv(OpVie
   const C* ai = op.ainv + (int64_t)r * op.ncomp1;
   C* yr = yout + g0;
   ChunkAcc<T, 4> acc;
-#pragma unroll 2
-  for (int e = threadIdx.x; e < nin; e += blockDim.x) {
+  // batches of U elements per thread: the composition bytes of a batch are
+  // read before any output is stored (a byte pointer may alias the output,
+  // which would otherwise serialise every element's load behind the previous
+  // element's store)
+  constexpr int U = 4;
+  for (int e0 = threadIdx.x; e0 < nin; e0 += U * blockDim.x) {
+    int cms[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      cms[u] = 0;
+      if (e < nin && MODE != XOUT_FIELD) {
+        const int line = fast_div(e, op.div_nx), p = e - line * nx;
+        const int row = row0 + line;
+        // row = (c nz + z) ny + y  ->  site (z ny + y) nx + p
+        const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
+        const int z = plane - fast_div(plane, op.div_nz) * op.nz;
+        cms[u] = op.comp[((int64_t)z * op.ny + y) * nx + p];
+      }
+    }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int e = e0 + u * blockDim.x;
+    if (e >= nin) break;
     const int line = fast_div(e, op.div_nx), p = e - line * nx;
-    const int row = row0 + line;
-    // row = (c nz + z) ny + y  ->  site (z ny + y) nx + p
-    const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
-    const int z = plane - fast_div(plane, op.div_nz) * op.nz;
-    const int64_t site = ((int64_t)z * op.ny + y) * nx + p;
-    const int cm = op.comp[site];
+    const int cm = cms[u];
     C out = mk<C>(0, 0);
     const C xv = sx[e];
     if (MODE == XOUT_FIELD) out = s[p * ps + line];
@@ -481,6 +524,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fft_x_inv(OpVie
         acc.step();
       }
     }
+  }
   }
   if (MODE != XOUT_PLAIN && MODE != XOUT_FIELD) {
     acc.flush();
