@@ -841,7 +841,7 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
     float bt = time_pass<T>(op, best, 0, R, x, y, scratch, st, e0, e1, reps) +
                time_pass<T>(op, best, 4, R, x, y, scratch, st, e0, e1, reps);
     for (int nl : {2, 4, 8, 16, 32, 64})
-      for (int th : {64, 128, 256}) {
+      for (int th : {64, 96, 128, 192, 256}) {
         MatvecLaunch c = best;
         fill_x<T>(op, c, nl);
         c.x_threads = th;
@@ -856,7 +856,7 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
     float bt = time_pass<T>(op, best, 1, R, x, y, scratch, st, e0, e1, reps) +
                time_pass<T>(op, best, 3, R, x, y, scratch, st, e0, e1, reps);
     for (int tile : {2, 4, 8, 16, 32})
-      for (int th : {64, 128, 256}) {
+      for (int th : {64, 96, 128, 192, 256}) {
         MatvecLaunch c = best;
         fill_y<T>(op, c, tile);
         c.y_threads = th;
@@ -872,7 +872,7 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
     for (int tile : {2, 4, 8, 16})
       for (int gs = 0; gs < 2; ++gs)
         for (int pad = 0; pad < 4; ++pad)
-          for (int th : {128, 256}) {
+          for (int th : {64, 96, 128, 192, 256}) {
             MatvecLaunch c = best;
             fill_z<T>(op, c, tile, pad, gs != 0);
             c.z_threads = th;
