@@ -76,7 +76,9 @@ typedef enum { DDA_POL_CM = 0, DDA_POL_LDR = 1, DDA_POL_FCD = 2 } dda_pol_method
 typedef enum {
   DDA_PREC_FP64 = 0,
   DDA_PREC_FP32 = 1,
-  DDA_PREC_FP32_REFINED = 2
+  DDA_PREC_FP32_REFINED = 2,
+  DDA_PREC_DF64 = 3      /* dda_matvec only: FP64 vectors, FFT passes in double-float
+                            arithmetic (the refinement's residual operator)        */
 } dda_precision;
 
 /* Krylov method of the solve (the guide's CMETHD choice, Sec. "Choice of
@@ -119,7 +121,8 @@ dda_status dda_set_polarizability(dda_target* t, dda_pol_method method);
  *  khat, e   : incident direction [3] and polarization [3][2] (only LDR reads
  *              them; may be NULL otherwise).
  *  x, y      : [N][3][2] on the occupied sites in flat-index order (host).
- *  precision : DDA_PREC_FP64 or DDA_PREC_FP32 (FP32_REFINED acts as FP32). */
+ *  precision : DDA_PREC_FP64, DDA_PREC_DF64 (FP64 vectors, double-float FFT
+ *              passes) or DDA_PREC_FP32 (FP32_REFINED acts as FP32). */
 dda_status dda_matvec(dda_target* t, double kd, const double* khat, const double* e,
                       const double* x, double* y, dda_precision precision);
 
@@ -177,6 +180,10 @@ typedef struct {
   int profile;           /* nonzero: time each FFT-matvec pass with CUDA events   */
   int solver;            /* dda_solver: DDA_SOLVER_BICGSTAB (0, default) or
                             DDA_SOLVER_QMR; unknown values: DDA_ERR_INVALID_ARG */
+  int fp64_residual;     /* FP32_REFINED only: 0 (default) computes the refinement's
+                            residuals E - A P with FP64 box vectors and FFT passes in
+                            double-float arithmetic (pairs of FP32 values, ~48 bits,
+                            run at FP32 rates); 1 uses FP64 arithmetic throughout */
 } dda_solve_params;
 
 /* Results.  Every array is caller-allocated HOST memory; a NULL pointer means

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libdda.so")
 DDA_OK, DDA_ERR_INVALID_ARG, DDA_ERR_OOM, DDA_ERR_CUDA, DDA_ERR_NOCONV, \
     DDA_ERR_BREAKDOWN, DDA_ERR_TIMEOUT = range(7)
 POL = {"CM": 0, "LDR": 1, "FCD": 2}
-PREC = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
+PREC = {"fp64": 0, "fp32": 1, "fp32_refined": 2, "df64": 3}
 SOLVER = {"bicgstab": 0, "qmr": 1}
 
 _dp = ct.POINTER(ct.c_double)
@@ -30,7 +30,7 @@ class SolveParams(ct.Structure):
                 ("e01", _dp), ("npol", ct.c_int), ("tol", ct.c_double),
                 ("max_iter", ct.c_int), ("precision", ct.c_int), ("inner_tol", ct.c_double),
                 ("n_dirs", ct.c_int), ("dirs", _dp), ("P0", _dp), ("profile", ct.c_int),
-                ("solver", ct.c_int)]
+                ("solver", ct.c_int), ("fp64_residual", ct.c_int)]
 
 
 class SolveResult(ct.Structure):
@@ -220,7 +220,7 @@ def dda_matvec_noalloc(h, kd: float, x_dev_ptr: int, y_dev_ptr: int, khat=None, 
 
 
 def _params(kd, khat, e01, yhat, npol, tol, max_iter, precision, inner_tol, dirs, P0,
-            profile=False, solver="bicgstab"):
+            profile=False, solver="bicgstab", fp64_residual=False):
     keep = []
 
     def arr(a, dtype=np.float64):
@@ -241,7 +241,8 @@ def _params(kd, khat, e01, yhat, npol, tol, max_iter, precision, inner_tol, dirs
                       max_iter=int(max_iter), precision=PREC[precision],
                       inner_tol=float(inner_tol), n_dirs=0 if d is None else d.shape[0],
                       dirs=_ptr(d), P0=None if p0 is None else _ptr(p0.view(np.float64)),
-                      profile=1 if profile else 0, solver=SOLVER[solver])
+                      profile=1 if profile else 0, solver=SOLVER[solver],
+                      fp64_residual=1 if fp64_residual else 0)
     return prm, keep, n_inc
 
 
@@ -253,12 +254,12 @@ def dda_solve_hbm_bytes(h, kd, khat, e01, npol=2, precision="fp64", dirs=None) -
 def dda_solve(h, kd, khat, e01, yhat=None, npol=2, tol=1e-8, max_iter=2000,
               precision="fp64", inner_tol=0.0, dirs=None, P0=None, want_P=True,
               want_famp=True, raise_on_noconv=False, profile=False,
-              solver="bicgstab") -> dict:
+              solver="bicgstab", fp64_residual=False) -> dict:
     """Solve for every incidence x polarization.  Returns a dict of numpy arrays.
     solver: "bicgstab" (two matvecs per iteration) or "qmr" (complex-symmetric
     QMR, one matvec per iteration)."""
     prm, keep, n_inc = _params(kd, khat, e01, yhat, npol, tol, max_iter, precision,
-                               inner_tol, dirs, P0, profile, solver)
+                               inner_tol, dirs, P0, profile, solver, fp64_residual)
     N = dda_target_num_dipoles(h)
     R = n_inc * npol
     D = prm.n_dirs + 1

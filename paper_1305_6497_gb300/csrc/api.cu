@@ -173,11 +173,11 @@ struct Workspace {
   // FP32
   DevBuf x32, r32, rh32, p32, v32, s32, t32, scr32, b32;
   DevBuf partials, ks, active, active_outer, norms, sums;
-  DevBuf pol, ph, ainv64, ainv32, wabs, fph, sitebuf;
+  DevBuf pol, ph, ainv64, ainv32, ainvdf, wabs, fph, sitebuf;
   void release_all() {
     for (DevBuf* b : {&b64, &x64, &r64, &rh64, &p64, &v64, &s64, &t64, &scr64, &x32, &r32,
                       &rh32, &p32, &v32, &s32, &t32, &scr32, &b32, &partials, &ks, &active,
-                      &active_outer, &norms, &sums, &pol, &ph, &ainv64, &ainv32, &wabs, &fph,
+                      &active_outer, &norms, &sums, &pol, &ph, &ainv64, &ainv32, &ainvdf, &wabs, &fph,
                       &sitebuf})
       b->release();
   }
@@ -259,14 +259,14 @@ struct dda_target {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  DevBuf comp, site, tw64, tw32, perm;  // perm: k_at x|y|z, then pos x|y|z
+  DevBuf comp, site, tw64, tw32, twdf, perm;  // perm: k_at x|y|z, then pos x|y|z
   AxisPlan px{}, py{}, pz{};
   int twoff[3] = {0, 0, 0};
   // Green transform cache
   bool have_green = false;
   double green_kd = 0.0;
   int green_filtered = -1;
-  DevBuf g64, g32;
+  DevBuf g64, g32, gdf;  // Ghat octant: FP64, FP32, double-float
   // transform of the magnetic vector h (near-field B), built on demand
   bool have_h = false;
   double h_kd = 0.0;
@@ -354,6 +354,8 @@ static void build_green(dda_target* t, double kd, int filtered) {
   if (t->have_green && t->green_kd == kd && t->green_filtered == filtered) return;
   t->have_green = false;
   build_transform(t, kd, filtered, t->g64, &t->g32);
+  t->gdf.ensure(sizeof(df64c) * 6 * (size_t)octant_size(t));
+  CK(launch_split_df(6 * octant_size(t), t->g64.as<double2>(), t->gdf.as<df64c>(), t->stream));
   t->have_green = true;
   t->green_kd = kd;
   t->green_filtered = filtered;
@@ -803,6 +805,7 @@ static void ensure_workspace(dda_target* t, int R, dda_precision prec, int ndir)
   w.ph.ensure(sizeof(double2) * (size_t)R * (t->nx + t->ny + t->nz));
   w.ainv64.ensure(sizeof(double2) * (size_t)R * (t->ncomp + 1));
   w.ainv32.ensure(sizeof(float2) * (size_t)R * (t->ncomp + 1));
+  w.ainvdf.ensure(sizeof(df64c) * (size_t)R * (t->ncomp + 1));
   w.wabs.ensure(sizeof(double) * (size_t)R * (t->ncomp + 1));
   w.fph.ensure(sizeof(double2) * (size_t)(ndir + 1) * (t->nx + t->ny + t->nz));
   w.sitebuf.ensure(sizeof(double2) * 3 * (size_t)t->N * R);
@@ -817,6 +820,7 @@ static void configure(dda_target* t) {
   t->L64 = plan_matvec<double>(v64);
   CK(configure_matvec_kernels<float>(t->L32));
   CK(configure_matvec_kernels<double>(t->L64));
+  CK(configure_matvec_kernels_df());
   t->kernels_configured = true;
 }
 
@@ -857,9 +861,9 @@ void dda_target_destroy(dda_target* t) {
   cudaSetDevice(t->device);
   if (t->stream) cudaStreamSynchronize(t->stream);
   t->ws.release_all();
-  t->comp.release(); t->site.release(); t->tw64.release(); t->tw32.release();
+  t->comp.release(); t->site.release(); t->tw64.release(); t->tw32.release(); t->twdf.release();
   t->perm.release();
-  t->g64.release(); t->g32.release(); t->h64.release();
+  t->g64.release(); t->g32.release(); t->gdf.release(); t->h64.release();
   t->prof.destroy();
   t->graphs[0].reset();
   t->graphs[1].reset();
@@ -921,6 +925,7 @@ dda_status dda_target_create(int nx, int ny, int nz, const uint8_t* occ, const u
     // plans and twiddles for the three axes, one table per precision
     std::vector<double2> t64;
     std::vector<float2> t32;
+    std::vector<float4> tdf;
     std::vector<int> kat;
     const int Ls[3] = {t->Lx, t->Ly, t->Lz};
     AxisPlan* ps[3] = {&t->px, &t->py, &t->pz};
@@ -937,13 +942,22 @@ dda_status dda_target_create(int nx, int ny, int nz, const uint8_t* occ, const u
       for (size_t i = 0; i < wr.size(); ++i) {
         t64.push_back(make_double2((double)wr[i], (double)wi[i]));
         t32.push_back(make_float2((float)wr[i], (float)wi[i]));
+        // double-float: hi = nearest float, lo = float of the remainder (long double)
+        const float rh = (float)wr[i], ih = (float)wi[i];
+        tdf.push_back(make_float4(rh, (float)(wr[i] - (long double)rh), ih,
+                                  (float)(wi[i] - (long double)ih)));
       }
     }
-    if (t64.empty()) { t64.push_back(make_double2(1, 0)); t32.push_back(make_float2(1, 0)); }
+    if (t64.empty()) {
+      t64.push_back(make_double2(1, 0)); t32.push_back(make_float2(1, 0));
+      tdf.push_back(make_float4(1, 0, 0, 0));
+    }
     t->tw64.ensure(sizeof(double2) * t64.size());
     t->tw32.ensure(sizeof(float2) * t32.size());
+    t->twdf.ensure(sizeof(float4) * tdf.size());
     CK(cudaMemcpy(t->tw64.p, t64.data(), sizeof(double2) * t64.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(t->tw32.p, t32.data(), sizeof(float2) * t32.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t->twdf.p, tdf.data(), sizeof(float4) * tdf.size(), cudaMemcpyHostToDevice));
     kat.insert(kat.end(), posall.begin(), posall.end());
     t->perm.ensure(sizeof(int) * kat.size());
     CK(cudaMemcpy(t->perm.p, kat.data(), sizeof(int) * kat.size(), cudaMemcpyHostToDevice));
@@ -1001,7 +1015,8 @@ dda_status dda_matvec(dda_target* t, double kd, const double* khat, const double
     CK(cudaSetDevice(t->device));
     const int filtered = t->method == DDA_POL_FCD ? 1 : 0;
     build_green(t, kd, filtered);
-    const bool f32 = precision != DDA_PREC_FP64;
+    const bool dfp = precision == DDA_PREC_DF64;
+    const bool f32 = precision != DDA_PREC_FP64 && !dfp;
     ensure_workspace(t, 1, f32 ? DDA_PREC_FP32 : DDA_PREC_FP64, 0);
     configure(t);
     Workspace& w = t->ws;
@@ -1022,7 +1037,18 @@ dda_status dda_matvec(dda_target* t, double kd, const double* khat, const double
     CK(cudaMemsetAsync(w.x64.p, 0, sizeof(double2) * 3 * nbox, st));
     CK(launch_sites_to_box(N, nbox, 1, t->site.as<int64_t>(), w.sitebuf.as<double2>(),
                            w.x64.as<double2>(), st));
-    if (!f32) {
+    if (dfp) {
+      std::vector<float4> aidf(ai.size());
+      for (size_t i = 0; i < ai.size(); ++i) {
+        const df64 re(ai[i].x), im(ai[i].y);
+        aidf[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      }
+      CK(cudaMemcpyAsync(w.ainvdf.p, aidf.data(), sizeof(float4) * aidf.size(),
+                         cudaMemcpyHostToDevice, st));
+      OpView<df64> op = make_view<df64>(t, t->gdf.p, w.ainvdf.p, t->twdf.p);
+      CK(launch_matvec_df(op, t->L64, 1, w.x64.as<double2>(), w.r64.as<double2>(),
+                          reinterpret_cast<df64c*>(w.scr64.p), nullptr, st));
+    } else if (!f32) {
       OpView<double> op = make_view<double>(t, t->g64.p, w.ainv64.p, t->tw64.p);
       CK(launch_matvec<double>(op, t->L64, 1, w.x64.as<double2>(), w.r64.as<double2>(),
                                w.scr64.as<double2>(), nullptr, st));
@@ -1115,6 +1141,12 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
     CK(cudaMemcpyAsync(w.ph.p, ph.data(), sizeof(double2) * ph.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(w.ainv64.p, ai.data(), sizeof(double2) * ai.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(w.ainv32.p, ai32.data(), sizeof(float2) * ai32.size(), cudaMemcpyHostToDevice, st));
+    std::vector<float4> aidf(ai.size());
+    for (size_t i = 0; i < ai.size(); ++i) {
+      const df64 re(ai[i].x), im(ai[i].y);
+      aidf[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    CK(cudaMemcpyAsync(w.ainvdf.p, aidf.data(), sizeof(float4) * aidf.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(w.wabs.p, wabs.data(), sizeof(double) * wabs.size(), cudaMemcpyHostToDevice, st));
     RhsTables tb;
     tb.pol = w.pol.as<double2>();
@@ -1134,6 +1166,18 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
     }
     OpView<double> op64 = make_view<double>(t, t->g64.p, w.ainv64.p, t->tw64.p);
     OpView<float> op32 = make_view<float>(t, t->g32.p, w.ainv32.p, t->tw32.p);
+    OpView<df64> opdf = make_view<df64>(t, t->gdf.p, w.ainvdf.p, t->twdf.p);
+    // the refinement's residuals r = E - A x: FFT passes in double-float
+    // arithmetic (FP64-level accuracy at FP32 rates) unless FP64 is requested
+    const bool df_resid = p->precision == DDA_PREC_FP32_REFINED && !p->fp64_residual;
+    auto resid_matvec = [&](const cudaEvent_t* ev) {
+      if (df_resid)
+        CK(launch_matvec_df(opdf, t->L64, R, w.x64.as<double2>(), w.r64.as<double2>(),
+                            reinterpret_cast<df64c*>(w.scr64.p), nullptr, st, ev));
+      else
+        CK(launch_matvec<double>(op64, t->L64, R, w.x64.as<double2>(), w.r64.as<double2>(),
+                                 w.scr64.as<double2>(), nullptr, st, ev));
+    };
     std::vector<int> its_total(R, 0), sweeps(R, 0), status(R, KS_RUN);
     int64_t matvecs = 0, matvecs64 = 0;
     const int nblk = reduce_blocks(n);
@@ -1183,8 +1227,7 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
         if (first && !x_nonzero) {
           CK(cudaMemcpyAsync(w.r64.p, w.b64.p, sizeof(double2) * n * R, cudaMemcpyDeviceToDevice, st));
         } else {
-          CK(launch_matvec<double>(op64, t->L64, R, w.x64.as<double2>(), w.r64.as<double2>(),
-                                   w.scr64.as<double2>(), nullptr, st, t->prof.resid_set()));
+          resid_matvec(t->prof.resid_set());
           matvecs += R; matvecs64 += R;
           CK(launch_residual(n, R, w.b64.as<double2>(), w.r64.as<double2>(),
                              w.r64.as<double2>(), st));
@@ -1250,8 +1293,7 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
     //      residual already belongs to the final iterate ----
     const bool final_matvec = !resid_fresh;
     if (final_matvec) {
-      CK(launch_matvec<double>(op64, t->L64, R, w.x64.as<double2>(), w.r64.as<double2>(),
-                               w.scr64.as<double2>(), nullptr, st, t->prof.resid_set()));
+      resid_matvec(t->prof.resid_set());
       matvecs += R; matvecs64 += R;
       CK(launch_residual(n, R, w.b64.as<double2>(), w.r64.as<double2>(), w.r64.as<double2>(),
                          st));
@@ -1699,6 +1741,8 @@ dda_status dda_matvec_noalloc(dda_target* t, double kd, const double* khat, cons
   g_last_error.clear();
   if (!t || !x_dev || !y_dev) return fail(DDA_ERR_INVALID_ARG, "null argument");
   if (x_dev == y_dev) return fail(DDA_ERR_INVALID_ARG, "x and y must not alias");
+  if (precision == DDA_PREC_DF64)
+    return fail(DDA_ERR_INVALID_ARG, "DDA_PREC_DF64 is not offered without allocation");
   dda_status s = check_kd(t, kd);
   if (s != DDA_OK) return s;
   const bool f32 = precision != DDA_PREC_FP64;

@@ -20,11 +20,57 @@ namespace dda {
 constexpr int kMaxStages = 12;
 constexpr int kMaxComp = 256;
 
+// ---- double-float ("df64") arithmetic ----------------------------------------
+// A value is the unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi)/2),
+// about 48 significant bits.  FP64 runs at 1/58 of the FP32 rate on this part,
+// so FFT passes that need FP64-level accuracy (the refinement's residual
+// A.x) run in this arithmetic instead.  Sums use Knuth's TwoSum and Dekker's
+// Fast2Sum, products the FMA-based exact product (Dekker; Ogita, Rump & Oishi
+// 2005); the absolute error of a sum is ~2^-48 (|a| + |b|), enough for an FFT.
+// The _rn intrinsics keep the compiler from contracting or reassociating.
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+};
+__device__ __forceinline__ df64 df_fast2sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_fast2sum(s, e);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast2sum(p, e);
+}
+__host__ __device__ __forceinline__ double df_to_double(df64 a) {
+  return (double)a.hi + (double)a.lo;
+}
+struct __align__(16) df64c { df64 x, y; };
+
 // Complex type for a real type.
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = float2; };
 template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<df64> { using type = df64c; };
 template <typename T> using cplx_t = typename Cplx<T>::type;
+
+// Type of the box vectors a matvec reads and writes (the FFT scratch is
+// cplx_t<T>): df64 passes take and return FP64 vectors.
+template <typename T> struct IoT { using type = cplx_t<T>; };
+template <> struct IoT<df64> { using type = double2; };
+template <typename T> using io_t = typename IoT<T>::type;
 
 template <typename C> __host__ __device__ __forceinline__ C mk(double re, double im);
 template <> __host__ __device__ __forceinline__ float2 mk<float2>(double re, double im) {
@@ -32,6 +78,35 @@ template <> __host__ __device__ __forceinline__ float2 mk<float2>(double re, dou
 }
 template <> __host__ __device__ __forceinline__ double2 mk<double2>(double re, double im) {
   return make_double2(re, im);
+}
+template <> __host__ __device__ __forceinline__ df64c mk<df64c>(double re, double im) {
+  df64c r;
+  r.x = df64(re);
+  r.y = df64(im);
+  return r;
+}
+
+// box-vector element <-> FFT element
+template <typename C, typename IO> __device__ __forceinline__ C from_io(IO v) { return v; }
+template <> __device__ __forceinline__ df64c from_io<df64c, double2>(double2 v) {
+  df64c r;
+  r.x = df64(v.x);
+  r.y = df64(v.y);
+  return r;
+}
+template <typename IO, typename C> __device__ __forceinline__ IO to_io(C v) { return v; }
+template <> __device__ __forceinline__ double2 to_io<double2, df64c>(df64c v) {
+  return make_double2(df_to_double(v.x), df_to_double(v.y));
+}
+
+// read-only load of a complex value (tables)
+template <typename C> __device__ __forceinline__ C ldc(const C* p) { return __ldg(p); }
+template <> __device__ __forceinline__ df64c ldc<df64c>(const df64c* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  df64c r;
+  r.x = df64(v.x, v.y);
+  r.y = df64(v.z, v.w);
+  return r;
 }
 
 template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) {

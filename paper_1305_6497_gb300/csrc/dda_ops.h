@@ -44,6 +44,16 @@ cudaError_t launch_field(const OpView<T>& op, const MatvecLaunch& L, int R,
                          const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch,
                          cudaStream_t st, bool magnetic = false);
 
+// y = A x with FP64 box vectors and the FFT passes in double-float arithmetic
+// (scratch: df64c, same size as the FP64 scratch); the schedule of the FP64
+// passes applies (same element size).  FP64-level accuracy at FP32 rates.
+cudaError_t launch_matvec_df(const OpView<df64>& op, const MatvecLaunch& L, int R,
+                             const double2* x, double2* y, df64c* scratch, const int* active,
+                             cudaStream_t st, const cudaEvent_t* ev = nullptr);
+cudaError_t configure_matvec_kernels_df();
+// Ghat octant FP64 -> df64 (n complex values)
+cudaError_t launch_split_df(int64_t n, const double2* in, df64c* out, cudaStream_t st);
+
 // x pass forward only (box rows -> spectral rows), used by the setup transforms.
 template <typename T>
 cudaError_t launch_x_fwd(const OpView<T>& op, const MatvecLaunch& L, int R,

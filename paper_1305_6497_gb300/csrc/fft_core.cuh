@@ -208,7 +208,7 @@ __device__ __forceinline__ void fft_stage(C* s, int nlines, int pstride, int L, 
       else dft<R, false>(v);
       if (j > 0) {
 #pragma unroll
-        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], __ldg(&tw[j * (R - 1) + (m - 1)]));
+        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], ldc(&tw[j * (R - 1) + (m - 1)]));
       }
 #pragma unroll
       for (int i = 0; i < R; ++i) base[i * S * pstride] = v[i];
@@ -217,7 +217,7 @@ __device__ __forceinline__ void fft_stage(C* s, int nlines, int pstride, int L, 
       for (int i = 0; i < R; ++i) v[i] = base[i * S * pstride];
       if (j > 0) {
 #pragma unroll
-        for (int m = 1; m < R; ++m) v[m] = cmulc(__ldg(&tw[j * (R - 1) + (m - 1)]), v[m]);
+        for (int m = 1; m < R; ++m) v[m] = cmulc(ldc(&tw[j * (R - 1) + (m - 1)]), v[m]);
       }
       if constexpr (HALF) dft_half<R, true, false, true>(v);
       else dft<R, true>(v);
@@ -325,7 +325,7 @@ __device__ __forceinline__ void stage_first_fwd(C* s, int nlines, int ps, int L,
     }
     if (j > 0) {
 #pragma unroll
-      for (int m = 1; m < R; ++m) v[m] = cmul(v[m], __ldg(&tw[j * (R - 1) + (m - 1)]));
+      for (int m = 1; m < R; ++m) v[m] = cmul(v[m], ldc(&tw[j * (R - 1) + (m - 1)]));
     }
 #pragma unroll
     for (int m = 0; m < R; ++m) s[(j + m * S) * ps + line] = v[m];
@@ -348,7 +348,7 @@ __device__ __forceinline__ void stage_last_inv(const C* s, int nlines, int ps, i
     for (int m = 0; m < R; ++m) v[m] = s[(j + m * S) * ps + line];
     if (j > 0) {
 #pragma unroll
-      for (int m = 1; m < R; ++m) v[m] = cmulc(__ldg(&tw[j * (R - 1) + (m - 1)]), v[m]);
+      for (int m = 1; m < R; ++m) v[m] = cmulc(ldc(&tw[j * (R - 1) + (m - 1)]), v[m]);
     }
     if constexpr (R % 2 == 0) {
       if (half) {

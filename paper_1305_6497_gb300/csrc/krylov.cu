@@ -676,6 +676,18 @@ cudaError_t launch_accumulate(int64_t n, int R, double2* x64, const float2* d32,
   return cudaGetLastError();
 }
 
+__global__ void k_split_df(int64_t n, const double2* __restrict__ a, df64c* __restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = from_io<df64c>(a[i]);
+}
+
+cudaError_t launch_split_df(int64_t n, const double2* in, df64c* out, cudaStream_t st) {
+  k_split_df<<<reduce_blocks(n), kThreads, 0, st>>>(n, in, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
 __global__ void k_f64_to_f32(int64_t n, const double2* __restrict__ a, float2* __restrict__ b) {
   GRID_LOOP(i, n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }

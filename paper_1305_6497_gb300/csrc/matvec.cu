@@ -13,6 +13,8 @@
 //   x pass  : inverse, Lx -> nx, then y = ainv * P - conv on occupied sites.
 // Inputs that are known to be zero (beyond the box) are never read and outputs
 // outside the box are never written (pruned transforms).
+#include <type_traits>
+
 #include "dda_ops.h"
 #include "fft_core.cuh"
 #include "reduce.cuh"
@@ -42,7 +44,7 @@ template <typename T> struct XinArgs {
 };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpView<T> op, const cplx_t<T>* __restrict__ in,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpView<T> op, const io_t<T>* __restrict__ in,
                             cplx_t<T>* __restrict__ buf, int nlines,
                             const int* __restrict__ active, XinArgs<T> xa) {
   using C = cplx_t<T>;
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpVie
       if (e < nin) {
         const int64_t g = g0 + e;
         if (MODE == XIN_PLAIN) {
-          va[u] = in[g];
+          va[u] = from_io<C>(in[g]);
         } else if (MODE == XIN_P) {
           va[u] = xa.r[g]; vb[u] = xa.pv[g]; vc[u] = xa.v[g];
         } else if (MODE == XIN_Q) {
@@ -235,6 +237,21 @@ template <> struct G6<float> {
     v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
     v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
     v[4] = make_float2(c.x, c.y); v[5] = make_float2(c.z, c.w);
+  }
+};
+template <> struct G6<df64> {
+  static __device__ __forceinline__ void load_smem(const df64c* g, df64c (&v)[6]) {
+    const float4* q = reinterpret_cast<const float4*>(g);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const float4 a = q[i];
+      v[i].x = df64(a.x, a.y);
+      v[i].y = df64(a.z, a.w);
+    }
+  }
+  static __device__ __forceinline__ void load(const df64c* g, df64c (&v)[6]) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = ldc(g + i);
   }
 };
 template <> struct G6<double> {
@@ -433,9 +450,9 @@ enum { XOUT_PLAIN = 0, XOUT_RV = 1, XOUT_TS = 2, XOUT_QT = 3, XOUT_FIELD = 4 };
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpView<T> op, const cplx_t<T>* __restrict__ buf,
-                            const cplx_t<T>* __restrict__ xin, cplx_t<T>* __restrict__ yout,
+                            const io_t<T>* __restrict__ xin, io_t<T>* __restrict__ yout,
                             int nlines, const int* __restrict__ active,
-                            const cplx_t<T>* __restrict__ rhat, double* __restrict__ partials) {
+                            const io_t<T>* __restrict__ rhat, double* __restrict__ partials) {
   using C = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
@@ -449,13 +466,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   const C* src = buf + (int64_t)r * 3 * op.nz * plane_sz;
   // the epilogue's inputs (x, and rhat for XOUT_RV) are contiguous chunks of the
   // box vectors: start copying them now, behind the spectral rows
-  C* sx = s + (size_t)Lx * ps;
-  C* sh = sx + (size_t)nlines * nx;
+  // (box-vector elements: FP64 for df64 passes, same size as C)
+  using IO = io_t<T>;
+  static_assert(sizeof(IO) == sizeof(C), "box and FFT elements must have one size");
+  IO* sx = reinterpret_cast<IO*>(s + (size_t)Lx * ps);
+  IO* sh = sx + (size_t)nlines * nx;
   const int nin = min(nlines, rows - row0) * nx;
   const int64_t g0 = ((int64_t)r * rows + row0) * nx;
   for (int e = threadIdx.x; e < nin; e += blockDim.x) {
-    cp_async<(int)sizeof(C)>(&sx[e], &xin[g0 + e]);
-    if (MODE == XOUT_RV) cp_async<(int)sizeof(C)>(&sh[e], &rhat[g0 + e]);
+    cp_async<(int)sizeof(IO)>(&sx[e], &xin[g0 + e]);
+    if (MODE == XOUT_RV) cp_async<(int)sizeof(IO)>(&sh[e], &rhat[g0 + e]);
   }
   // all of the tile's loads in flight at once (asynchronous copies)
   for (int e = threadIdx.x; e < nlines * Lx; e += blockDim.x) {
@@ -474,8 +494,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   // only positions < nx <= Lx/2 are used below
   fft_smem<C, true>(s, nlines, ps, op.px, op.twx, 2 * nx <= Lx);
   const C* ai = op.ainv + (int64_t)r * op.ncomp1;
-  C* yr = yout + g0;
-  ChunkAcc<T, 4> acc;
+  IO* yr = yout + g0;
+  // (df64 passes only run the plain epilogue; their accumulator type is unused)
+  ChunkAcc<std::conditional_t<std::is_same<T, df64>::value, double, T>, 4> acc;
   // batches of U elements per thread: the composition bytes of a batch are
   // read before any output is stored (a byte pointer may alias the output,
   // which would otherwise serialise every element's load behind the previous
@@ -503,22 +524,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
     const int line = fast_div(e, op.div_nx), p = e - line * nx;
     const int cm = cms[u];
     C out = mk<C>(0, 0);
-    const C xv = sx[e];
+    const C xv = from_io<C>(sx[e]);
     if (MODE == XOUT_FIELD) out = s[p * ps + line];
     else if (cm) out = csub(cmul(ai[cm], xv), s[p * ps + line]);
-    yr[e] = out;
+    yr[e] = to_io<IO>(out);
     {
-      if (MODE == XOUT_RV) {
-        const C h = sh[e];
+      if constexpr (MODE == XOUT_RV) {
+        const C h = from_io<C>(sh[e]);
         acc.add(0, h.x * out.x + h.y * out.y);
         acc.add(1, h.x * out.y - h.y * out.x);
         acc.step();
-      } else if (MODE == XOUT_TS) {
+      } else if constexpr (MODE == XOUT_TS) {
         acc.add(0, out.x * xv.x + out.y * xv.y);
         acc.add(1, out.x * xv.y - out.y * xv.x);
         acc.add(2, out.x * out.x + out.y * out.y);
         acc.step();
-      } else if (MODE == XOUT_QT) {
+      } else if constexpr (MODE == XOUT_QT) {
         acc.add(0, xv.x * out.x - xv.y * out.y);
         acc.add(1, xv.x * out.y + xv.y * out.x);
         acc.step();
@@ -526,7 +547,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
     }
   }
   }
-  if (MODE != XOUT_PLAIN && MODE != XOUT_FIELD) {
+  if constexpr (MODE != XOUT_PLAIN && MODE != XOUT_FIELD) {
     acc.flush();
     if (MODE == XOUT_RV || MODE == XOUT_QT) {
       double v2[2] = {acc.tot[0], acc.tot[1]};
@@ -627,9 +648,9 @@ cudaError_t configure_matvec_kernels(const MatvecLaunch& L) {
 
 template <typename T, int XIN, int XOUT, bool CROSS = false>
 static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int R,
-                                 const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch,
+                                 const io_t<T>* x, io_t<T>* y, cplx_t<T>* scratch,
                                  const int* active, cudaStream_t st, const cudaEvent_t* ev,
-                                 XinArgs<T> xa, const cplx_t<T>* rhat, double* partials) {
+                                 XinArgs<T> xa, const io_t<T>* rhat, double* partials) {
   const int rows = 3 * op.nz * op.ny;
   // inside a stream capture the events must be external nodes to be recorded
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -698,6 +719,29 @@ cudaError_t launch_field(const OpView<T>& op, const MatvecLaunch& L, int R,
                                                          nullptr);
   return matvec_passes<T, XIN_PLAIN, XOUT_FIELD>(op, L, R, x, y, scratch, nullptr, st,
                                                  nullptr, XinArgs<T>{}, nullptr, nullptr);
+}
+
+cudaError_t launch_matvec_df(const OpView<df64>& op, const MatvecLaunch& L, int R,
+                             const double2* x, double2* y, df64c* scratch, const int* active,
+                             cudaStream_t st, const cudaEvent_t* ev) {
+  return matvec_passes<df64, XIN_PLAIN, XOUT_PLAIN>(op, L, R, x, y, scratch, active, st, ev,
+                                                    XinArgs<df64>{}, nullptr, nullptr);
+}
+
+cudaError_t configure_matvec_kernels_df() {
+  const void* k[] = {(const void*)k_fft_x_fwd<df64, XIN_PLAIN>,
+                     (const void*)k_fft_x_inv<df64, XOUT_PLAIN>,
+                     (const void*)k_fft_y<df64, false>, (const void*)k_fft_y<df64, true>,
+                     (const void*)k_fft_z_mul<df64, 16, true>, (const void*)k_fft_z_mul<df64, 8, true>,
+                     (const void*)k_fft_z_mul<df64, 4, true>, (const void*)k_fft_z_mul<df64, 2, true>,
+                     (const void*)k_fft_z_mul<df64, 16, false>, (const void*)k_fft_z_mul<df64, 8, false>,
+                     (const void*)k_fft_z_mul<df64, 4, false>, (const void*)k_fft_z_mul<df64, 2, false>};
+  for (const void* f : k) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               200 * 1024);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <typename T>

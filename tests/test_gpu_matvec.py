@@ -72,6 +72,9 @@ def test_matvec_fp64_matches_oracle(B, name, mk, m, method):
     t = B.Target(occ, comp, m, method=method)
     y = t.matvec(kd, x, khat, e, "fp64")
     assert _err(y, ref) <= TOL64, (name, method, _err(y, ref))
+    # the refinement's residual operator: FP64 vectors, double-float FFT passes
+    ydf = t.matvec(kd, x, khat, e, "df64")
+    assert _err(ydf, ref) <= TOL64, (name, method, _err(ydf, ref))
     y32 = t.matvec(kd, x, khat, e, "fp32")
     assert _err(y32, ref) <= TOL32, (name, method, _err(y32, ref))
     t.close()

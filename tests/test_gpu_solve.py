@@ -250,3 +250,24 @@ def test_qmr_circular_polarization_falls_back_and_converges(B):
     ref = O.solve_target(w.occ, w.comp, w.m, w.kd, x, y, e, "FCD", npol=2, tol=1e-12)
     assert np.allclose(q["Qext"], ref["Qext"], rtol=1e-6)
     t.close()
+
+
+def test_refined_residual_in_double_float_equals_fp64_residual(B):
+    """The refinement's residuals computed with double-float FFT passes give the
+    same converged solution as with FP64 passes (to the solve tolerance)."""
+    w = W.small_ellipsoid(9, 10, 12, m=1.5 + 0.1j, kd=0.4, method="LDR", n_orient=2, seed=3)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    a = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-10, precision="fp32_refined")
+    b = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-10, precision="fp32_refined",
+                fp64_residual=True)
+    assert np.all(a["resid"] <= 1e-10) and np.all(b["resid"] <= 1e-10)
+    assert np.allclose(a["Qext"], b["Qext"], rtol=1e-8, atol=0)
+    assert np.abs(a["P"] - b["P"]).max() <= 1e-8 * np.abs(b["P"]).max()
+    # the reported residual is the true residual (checked in FP64 by the oracle)
+    flat, pos = O.site_positions(w.occ)
+    e1, _ = O.polarization_pair(w.khat[0], w.e01[0])
+    ainv = O.site_alpha_inverse(w.comp.reshape(-1)[flat], w.m, "LDR", w.kd, w.khat[0], e1)
+    E = O.incident_field(pos, w.kd, w.khat[0], e1)
+    r = E - O.matvec_direct(a["P"][0], pos, ainv, w.kd, "LDR")
+    assert abs(np.linalg.norm(r) / np.linalg.norm(E) / a["resid"][0] - 1) < 1e-2
+    t.close()
