@@ -224,7 +224,7 @@ cudaError_t launch_green_fill(int nx, int ny, int nz, int Lx, int Ly, int Lz, do
 // Generic strided transform (used for the unpruned setup transforms along y and z).
 // Lines are columns of a row-major plane: element (p, col) at base + p*row_stride + col.
 template <typename T, bool INV>
-__global__ void k_fft_strided(cplx_t<T>* __restrict__ buf, AxisPlan P, const cplx_t<T>* tw,
+__global__ void __launch_bounds__(512) k_fft_strided(cplx_t<T>* __restrict__ buf, AxisPlan P, const cplx_t<T>* tw,
                               int64_t ncols, int64_t row_stride, int64_t plane_stride,
                               int tile) {
   using C = cplx_t<T>;

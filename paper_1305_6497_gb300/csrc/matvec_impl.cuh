@@ -13,6 +13,12 @@
 //   x pass  : inverse, Lx -> nx, then y = ainv * P - conv on occupied sites.
 // Inputs that are known to be zero (beyond the box) are never read and outputs
 // outside the box are never written (pruned transforms).
+//
+// This header holds the kernel and launcher templates; matvec_f32.cu,
+// matvec_f64.cu and matvec_df.cu instantiate them for one arithmetic each, so
+// the three compile in parallel.
+#pragma once
+
 #include <type_traits>
 
 #include "dda_ops.h"
@@ -668,7 +674,15 @@ static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int
   k_fft_y<T, false><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, active);
   note_launch();
   if (ev) record(ev[2]);
-  {
+  if constexpr (std::is_same<T, df64>::value) {
+    // double-float passes use one z variant (4 columns, Ghat from global
+    // memory): the arithmetic is ~10x the FP32 code, so fewer instantiations
+    // keep the build short
+    dim3 gz((op.Lx + 3) / 4, op.Ly, R);
+    k_fft_z_mul<T, 4, false, CROSS><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps,
+                                                                      active);
+    note_launch();
+  } else {
     dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
 #define DDA_ZL(TT, GG) \
   k_fft_z_mul<T, TT, GG, CROSS><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active)
@@ -721,28 +735,6 @@ cudaError_t launch_field(const OpView<T>& op, const MatvecLaunch& L, int R,
                                                  nullptr, XinArgs<T>{}, nullptr, nullptr);
 }
 
-cudaError_t launch_matvec_df(const OpView<df64>& op, const MatvecLaunch& L, int R,
-                             const double2* x, double2* y, df64c* scratch, const int* active,
-                             cudaStream_t st, const cudaEvent_t* ev) {
-  return matvec_passes<df64, XIN_PLAIN, XOUT_PLAIN>(op, L, R, x, y, scratch, active, st, ev,
-                                                    XinArgs<df64>{}, nullptr, nullptr);
-}
-
-cudaError_t configure_matvec_kernels_df() {
-  const void* k[] = {(const void*)k_fft_x_fwd<df64, XIN_PLAIN>,
-                     (const void*)k_fft_x_inv<df64, XOUT_PLAIN>,
-                     (const void*)k_fft_y<df64, false>, (const void*)k_fft_y<df64, true>,
-                     (const void*)k_fft_z_mul<df64, 16, true>, (const void*)k_fft_z_mul<df64, 8, true>,
-                     (const void*)k_fft_z_mul<df64, 4, true>, (const void*)k_fft_z_mul<df64, 2, true>,
-                     (const void*)k_fft_z_mul<df64, 16, false>, (const void*)k_fft_z_mul<df64, 8, false>,
-                     (const void*)k_fft_z_mul<df64, 4, false>, (const void*)k_fft_z_mul<df64, 2, false>};
-  for (const void* f : k) {
-    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               200 * 1024);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
 
 template <typename T>
 int matvec_partial_blocks(const OpView<T>& op, const MatvecLaunch& L) {
@@ -793,8 +785,6 @@ cudaError_t launch_x_fwd(const OpView<T>& op, const MatvecLaunch& L, int R,
   note_launch();
   return cudaGetLastError();
 }
-template cudaError_t launch_x_fwd<double>(const OpView<double>&, const MatvecLaunch&, int,
-                                          const double2*, double2*, cudaStream_t);
 
 // --------------------------------------------------------------------------
 // autotuning of the launch schedule (tiles, lines, row pitch, Ghat staging)
@@ -931,44 +921,5 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
   L = best;
   return cudaGetLastError();
 }
-
-template cudaError_t autotune_matvec<float>(const OpView<float>&, MatvecLaunch&, int,
-                                            const float2*, float2*, float2*, cudaStream_t);
-template cudaError_t autotune_matvec<double>(const OpView<double>&, MatvecLaunch&, int,
-                                             const double2*, double2*, double2*, cudaStream_t);
-
-template MatvecLaunch plan_matvec<float>(const OpView<float>&);
-template MatvecLaunch plan_matvec<double>(const OpView<double>&);
-template cudaError_t configure_matvec_kernels<float>(const MatvecLaunch&);
-template cudaError_t configure_matvec_kernels<double>(const MatvecLaunch&);
-#define INST_KRY(T)                                                                        \
-  template int matvec_partial_blocks<T>(const OpView<T>&, const MatvecLaunch&);            \
-  template cudaError_t launch_matvec_p<T>(const OpView<T>&, const MatvecLaunch&, int,       \
-                                          const cplx_t<T>*, cplx_t<T>*, cplx_t<T>*,         \
-                                          const cplx_t<T>*, cplx_t<T>*, const KState*,      \
-                                          double*, const int*, cudaStream_t,                \
-                                          const cudaEvent_t*);                              \
-  template cudaError_t launch_matvec_s<T>(const OpView<T>&, const MatvecLaunch&, int,       \
-                                          const cplx_t<T>*, const cplx_t<T>*, cplx_t<T>*,   \
-                                          cplx_t<T>*, cplx_t<T>*, const KState*, double*,   \
-                                          const int*, cudaStream_t, const cudaEvent_t*);    \
-  template cudaError_t launch_matvec_q<T>(const OpView<T>&, const MatvecLaunch&, int,       \
-                                          const cplx_t<T>*, cplx_t<T>*, cplx_t<T>*,         \
-                                          cplx_t<T>*, cplx_t<T>*, cplx_t<T>*,               \
-                                          const KState*, double*, const int*, cudaStream_t, \
-                                          const cudaEvent_t*);
-INST_KRY(float)
-INST_KRY(double)
-#undef INST_KRY
-
-template cudaError_t launch_matvec<float>(const OpView<float>&, const MatvecLaunch&, int,
-                                          const float2*, float2*, float2*, const int*,
-                                          cudaStream_t, const cudaEvent_t*);
-template cudaError_t launch_field<double>(const OpView<double>&, const MatvecLaunch&, int,
-                                          const double2*, double2*, double2*, cudaStream_t,
-                                          bool);
-template cudaError_t launch_matvec<double>(const OpView<double>&, const MatvecLaunch&, int,
-                                           const double2*, double2*, double2*, const int*,
-                                           cudaStream_t, const cudaEvent_t*);
 
 }  // namespace dda
