@@ -92,8 +92,13 @@ typedef enum {
  *             r^T r vanishes (|r^T r| <= 1e-10 ||r||^2 in FP64, 1e-5 in FP32;
  *             e.g. circularly polarized light, E . E = 0) it cannot go on; those
  *             right-hand sides are finished by BiCGSTAB from QMR's iterate.
+ *  BICGSTAB2: BiCGstab(2) (Sleijpen & van der Vorst 1993), the guide's PBCGS2
+ *             and its recommended method: four matvecs per cycle with a
+ *             two-dimensional minimal-residual step; a cycle counts as two
+ *             iterations; stops on the recursive residual checked after each
+ *             cycle (breakdowns finish with BiCGSTAB as for QMR).
  * Either way the reported residual is the FP64 true residual of the result. */
-typedef enum { DDA_SOLVER_BICGSTAB = 0, DDA_SOLVER_QMR = 1 } dda_solver;
+typedef enum { DDA_SOLVER_BICGSTAB = 0, DDA_SOLVER_QMR = 1, DDA_SOLVER_BICGSTAB2 = 2 } dda_solver;
 
 typedef struct dda_target dda_target; /* opaque, library-owned */
 
@@ -178,8 +183,8 @@ typedef struct {
                             y sin(theta) cos(phi) + z sin(theta) sin(phi)       */
   const double* P0;      /* optional warm start [n_inc*npol][N][3][2] or NULL   */
   int profile;           /* nonzero: time each FFT-matvec pass with CUDA events   */
-  int solver;            /* dda_solver: DDA_SOLVER_BICGSTAB (0, default) or
-                            DDA_SOLVER_QMR; unknown values: DDA_ERR_INVALID_ARG */
+  int solver;            /* dda_solver: DDA_SOLVER_BICGSTAB (0, default), _QMR or
+                            _BICGSTAB2; unknown values: DDA_ERR_INVALID_ARG     */
   int fp64_residual;     /* FP32_REFINED only: 0 (default) computes the refinement's
                             residuals E - A P with FP64 box vectors and FFT passes in
                             double-float arithmetic (pairs of FP32 values, ~48 bits,

@@ -174,10 +174,12 @@ struct Workspace {
   DevBuf x32, r32, rh32, p32, v32, s32, t32, scr32, b32;
   DevBuf partials, ks, active, active_outer, norms, sums;
   DevBuf pol, ph, ainv64, ainv32, ainvdf, wabs, fph, sitebuf;
+  DevBuf extra64, extra32;  // BiCGstab(2)'s third residual (allocated on first use)
   void release_all() {
     for (DevBuf* b : {&b64, &x64, &r64, &rh64, &p64, &v64, &s64, &t64, &scr64, &x32, &r32,
                       &rh32, &p32, &v32, &s32, &t32, &scr32, &b32, &partials, &ks, &active,
                       &active_outer, &norms, &sums, &pol, &ph, &ainv64, &ainv32, &ainvdf, &wabs, &fph,
+                      &extra64, &extra32,
                       &sitebuf})
       b->release();
   }
@@ -664,20 +666,140 @@ static void qmr(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R
   }
 }
 
+// ---------------------------------------------------------------------------
+// BiCGstab(2) driver (the guide's PBCGS2), R RHS in lockstep: r0 in V.r, the
+// shadow vector in V.rh, u0, u1, u2 in V.p, V.v, V.s, r1 in V.t, r2 in an
+// extra workspace vector.  Each cycle (two iterations, four matvecs) is one
+// fixed launch sequence; two cycles are captured per CUDA graph.
+// ---------------------------------------------------------------------------
+template <typename T>
+static void bicgstab2(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R,
+                      const Vecs<T>& V, bool x_nonzero, double tol, int max_iter,
+                      std::vector<int>& its, std::vector<int>& status, int64_t& matvecs) {
+  Workspace& w = t->ws;
+  const int64_t n = 3 * t->nbox;
+  const int nblk = reduce_blocks(n);
+  double* part = w.partials.as<double>();
+  KState* ks = w.ks.as<KState>();
+  int* act = w.active.as<int>();
+  cudaStream_t st = t->stream;
+  DevBuf& xb = sizeof(T) == 4 ? w.extra32 : w.extra64;
+  xb.ensure(sizeof(cplx_t<T>) * n * R);
+  cplx_t<T>* r2 = xb.as<cplx_t<T>>();
+  cplx_t<T>*r0 = V.r, *rt = V.rh, *u0 = V.p, *u1 = V.v, *u2 = V.s, *r1 = V.t;
+  if (x_nonzero) {
+    CK(launch_matvec<T>(op, L, R, V.x, V.s, V.scr, nullptr, st));
+    matvecs += R;
+    CK(launch_bicg_init<T>(n, R, V.b, V.s, r0, rt, u0, u1, part, st));
+  } else {
+    CK(launch_bicg_init<T>(n, R, V.b, nullptr, r0, rt, u0, u1, part, st));
+  }
+  CK(launch_state_init(R, nblk, part, ks, act, tol, max_iter, st));
+  CK(launch_bs2_scalar(6, R, nblk, part, ks, act, st));
+  std::vector<int> hact(R);
+  CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int nact = 0;
+  for (int a : hact) nact += a;
+  const int nblk_mv = matvec_partial_blocks<T>(op, L);
+  constexpr int kCycles = kCheckEvery / 2;  // two iterations per cycle
+  auto vec = [&](int which) {
+    CK(launch_bs2_vec<T>(which, n, R, V.x, r0, r1, r2, u0, u1, u2, rt, part, ks, act, st));
+  };
+  auto enqueue_block = [&](int ncyc) {
+    for (int c = 0; c < ncyc; ++c) {
+      CK(launch_bs2_scalar(0, R, nblk, part, ks, act, st));          // beta, rho0
+      vec(0);                                                        // u0 = r0 - beta u0
+      CK(launch_matvec_rv<T>(op, L, R, u0, u1, rt, V.scr, part, act, st,
+                             t->prof.iter_set(2 * c, 0)));           // u1 = A u0
+      CK(launch_scalar_alpha(R, nblk_mv, part, ks, act, st));        // alpha
+      vec(1);                                                        // r0 -= alpha u1
+      CK(launch_matvec_rv<T>(op, L, R, r0, r1, rt, V.scr, part, act, st,
+                             t->prof.iter_set(2 * c, 1)));           // r1 = A r0
+      CK(launch_bs2_scalar(2, R, nblk_mv, part, ks, act, st));      // beta, rho0
+      vec(2);                                                        // x, u0, u1
+      CK(launch_matvec_rv<T>(op, L, R, u1, u2, rt, V.scr, part, act, st,
+                             t->prof.iter_set(2 * c + 1, 0)));       // u2 = A u1
+      CK(launch_scalar_alpha(R, nblk_mv, part, ks, act, st));        // alpha
+      vec(3);                                                        // r0, r1, x
+      CK(launch_matvec<T>(op, L, R, r1, r2, V.scr, act, st,
+                          t->prof.iter_set(2 * c + 1, 1)));          // r2 = A r1
+      vec(4);                                                        // Gram partials
+      CK(launch_bs2_scalar(4, R, nblk, part, ks, act, st));          // g1, g2, omega
+      vec(5);                                                        // MR update
+      CK(launch_bs2_scalar(5, R, nblk, part, ks, act, st));          // convergence
+    }
+  };
+  std::vector<uintptr_t> sig = {(uintptr_t)2000 + sizeof(T), (uintptr_t)R, (uintptr_t)t->prof.on,
+                                (uintptr_t)r0, (uintptr_t)rt, (uintptr_t)u0, (uintptr_t)u1,
+                                (uintptr_t)u2, (uintptr_t)r1, (uintptr_t)r2, (uintptr_t)V.x,
+                                (uintptr_t)V.scr, (uintptr_t)ks, (uintptr_t)part,
+                                (uintptr_t)act, (uintptr_t)op.ghat, (uintptr_t)op.ainv,
+                                (uintptr_t)nblk_mv, (uintptr_t)nblk,
+                                (uintptr_t)t->schedule_gen};
+  IterGraph& g = t->graphs[sizeof(T) == 4 ? 0 : 1];
+  if (g.exec && g.sig != sig) g.reset();
+  if (!g.exec) {
+    const long long before = launch_count();
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue_block(kCycles);
+    } catch (...) {
+      cudaGraph_t broken = nullptr;
+      cudaStreamEndCapture(st, &broken);
+      if (broken) cudaGraphDestroy(broken);
+      throw;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamEndCapture(st, &graph));
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie);
+    g.kernels = launch_count() - before;
+    note_launches(-g.kernels);
+    g.sig = sig;
+  }
+  int iter = 0;
+  while (nact > 0 && iter < max_iter) {
+    CK(cudaGraphLaunch(g.exec, st));
+    note_launches(g.kernels);
+    CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    t->prof.harvest_iters(sizeof(T) == 4 ? 0 : 1, kCheckEvery, 2);
+    nact = 0;
+    for (int a : hact) nact += a;
+    iter += 2 * kCycles;
+  }
+  std::vector<KState> hks(R);
+  CK(cudaMemcpyAsync(hks.data(), ks, sizeof(KState) * R, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  its.resize(R);
+  status.resize(R);
+  for (int r = 0; r < R; ++r) {
+    matvecs += 2 * (int64_t)hks[r].iters;
+    its[r] = hks[r].iters;
+    status[r] = hks[r].status == KS_RUN ? KS_NOCONV : hks[r].status;
+  }
+}
+
 // Krylov solve with the requested method.  QMR's bilinear Lanczos process
 // breaks down when r^T r vanishes for r != 0 (circularly polarized incident
-// light makes E . E = 0 at every site); such right-hand sides are finished by
-// BiCGSTAB from QMR's last iterate (the others are already converged there
-// and take no further iterations).
+// light makes E . E = 0 at every site), and BiCGstab(2) when its 2x2
+// minimal-residual system is singular; such right-hand sides are finished by
+// BiCGSTAB from the last iterate (the others are already converged there and
+// take no further iterations).
 template <typename T>
 static void krylov(int solver, dda_target* t, const OpView<T>& op, const MatvecLaunch& L,
                    int R, const Vecs<T>& V, bool x_nonzero, double tol, int max_iter,
                    std::vector<int>& its, std::vector<int>& status, int64_t& matvecs) {
-  if (solver != DDA_SOLVER_QMR) {
+  if (solver == DDA_SOLVER_BICGSTAB) {
     bicgstab<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
     return;
   }
-  qmr<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
+  if (solver == DDA_SOLVER_QMR)
+    qmr<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
+  else
+    bicgstab2<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
   bool broke = false;
   int left = max_iter;
   for (int r = 0; r < R; ++r)
@@ -765,9 +887,10 @@ static int64_t workspace_bytes(const dda_target* t, int R, dda_precision prec, i
   b += ns * 16;  // FP64 scratch (final/true residual matvec)
   if (f32) b += 8 * nv * 8 + ns * 8;
   const int nblk = std::max(reduce_blocks(3 * t->nbox), 3 * t->nz * t->ny);
-  // Krylov partials [R][nblk][4]; far field, one incidence at a time: [2][ndir+1][fblk][6]
+  // Krylov partials [R][nblk][<= 8]; far field, one incidence at a time:
+  // [2][ndir+1][fblk][6]
   const int fblk = std::min(reduce_blocks(t->nbox), 304);
-  b += std::max((int64_t)4 * R * nblk, (int64_t)12 * (ndir + 1) * fblk) * 8;
+  b += std::max((int64_t)8 * R * nblk, (int64_t)12 * (ndir + 1) * fblk) * 8;
   b += (int64_t)R * (sizeof(KState) + 64) + (int64_t)R * (t->nx + t->ny + t->nz + 8) * 16;
   b += (int64_t)(ndir + 1) * (t->nx + t->ny + t->nz) * 16 + t->N * (int64_t)R * 48;
   return b;
@@ -795,7 +918,7 @@ static void ensure_workspace(dda_target* t, int R, dda_precision prec, int ndir)
   const int nblk = std::max({reduce_blocks(3 * t->nbox), (rows + t->L32.x_lines - 1) / t->L32.x_lines,
                              (rows + t->L64.x_lines - 1) / t->L64.x_lines});
   const int fblk = std::min(reduce_blocks(t->nbox), 304);
-  w.partials.ensure((size_t)std::max((int64_t)4 * R * nblk, (int64_t)12 * (ndir + 1) * fblk) * 8);
+  w.partials.ensure((size_t)std::max((int64_t)8 * R * nblk, (int64_t)12 * (ndir + 1) * fblk) * 8);
   w.ks.ensure(sizeof(KState) * R);
   w.active.ensure(sizeof(int) * R);
   w.active_outer.ensure(sizeof(int) * R);
@@ -1081,7 +1204,8 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
   if (p->precision != DDA_PREC_FP64 && p->precision != DDA_PREC_FP32 &&
       p->precision != DDA_PREC_FP32_REFINED)
     return fail(DDA_ERR_INVALID_ARG, "unknown precision");
-  if (p->solver != DDA_SOLVER_BICGSTAB && p->solver != DDA_SOLVER_QMR)
+  if (p->solver != DDA_SOLVER_BICGSTAB && p->solver != DDA_SOLVER_QMR &&
+      p->solver != DDA_SOLVER_BICGSTAB2)
     return fail(DDA_ERR_INVALID_ARG, "unknown solver");
   const int R = p->n_inc * p->npol;
   if (R > 4096) return fail(DDA_ERR_INVALID_ARG, "at most 4096 right-hand sides");

@@ -196,6 +196,28 @@ template <typename T>
 cudaError_t launch_qmr_flush(int64_t n, int R, cplx_t<T>* x, cplx_t<T>* d,
                              const cplx_t<T>* q, const KState* ks, cudaStream_t st);
 
+// BiCGstab(2) building blocks (bicgstab2.cu).  launch_bs2_vec `which`:
+//  0: u0 = r0 - beta u0            1: r0 -= alpha u1
+//  2: x += alpha u0, u0 = r0 - beta u0, u1 = r1 - beta u1
+//  3: r0 -= alpha u1, r1 -= alpha u2, x += alpha u0
+//  4: Gram partials ||r1||^2, ||r2||^2, <r1,r2>, <r1,r0>, <r2,r0> ([R][nblk][8])
+//  5: minimal-residual update with partials <rt, r0>, ||r0||^2 ([R][nblk][4])
+// launch_bs2_scalar phases: see bicgstab2.cu.
+template <typename T>
+cudaError_t launch_bs2_vec(int which, int64_t n, int R, cplx_t<T>* x, cplx_t<T>* r0,
+                           cplx_t<T>* r1, cplx_t<T>* r2, cplx_t<T>* u0, cplx_t<T>* u1,
+                           cplx_t<T>* u2, const cplx_t<T>* rt, double* partials,
+                           const KState* ks, const int* active, cudaStream_t st);
+cudaError_t launch_bs2_scalar(int phase, int R, int nblk, const double* partials, KState* ks,
+                              int* active, cudaStream_t st);
+// y = A x with the epilogue partials <rhat, y> ([R][nblk][2], nblk =
+// matvec_partial_blocks): a plain input with the XOUT_RV epilogue.
+template <typename T>
+cudaError_t launch_matvec_rv(const OpView<T>& op, const MatvecLaunch& L, int R,
+                             const cplx_t<T>* x, cplx_t<T>* y, const cplx_t<T>* rhat,
+                             cplx_t<T>* scratch, double* partials, const int* active,
+                             cudaStream_t st, const cudaEvent_t* ev = nullptr);
+
 // ---- refinement helpers -----------------------------------------------------
 // partials of ||v||^2 per RHS (FP64 vector)
 cudaError_t launch_norm2(int64_t n, int R, const double2* v, double* partials,

@@ -25,4 +25,8 @@ template cudaError_t launch_matvec<float>(const OpView<float>&, const MatvecLaun
                                           const float2*, float2*, float2*, const int*,
                                           cudaStream_t, const cudaEvent_t*);
 
+template cudaError_t launch_matvec_rv<float>(const OpView<float>&, const MatvecLaunch&, int,
+                                            const float2*, float2*, const float2*, float2*, double*,
+                                            const int*, cudaStream_t, const cudaEvent_t*);
+
 }  // namespace dda

@@ -31,4 +31,8 @@ template cudaError_t launch_field<double>(const OpView<double>&, const MatvecLau
 template cudaError_t launch_x_fwd<double>(const OpView<double>&, const MatvecLaunch&, int,
                                           const double2*, double2*, cudaStream_t);
 
+template cudaError_t launch_matvec_rv<double>(const OpView<double>&, const MatvecLaunch&, int,
+                                            const double2*, double2*, const double2*, double2*, double*,
+                                            const int*, cudaStream_t, const cudaEvent_t*);
+
 }  // namespace dda

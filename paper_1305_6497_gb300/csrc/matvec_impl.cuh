@@ -765,6 +765,15 @@ cudaError_t launch_matvec_s(const OpView<T>& op, const MatvecLaunch& L, int R,
 }
 
 template <typename T>
+cudaError_t launch_matvec_rv(const OpView<T>& op, const MatvecLaunch& L, int R,
+                             const cplx_t<T>* x, cplx_t<T>* y, const cplx_t<T>* rhat,
+                             cplx_t<T>* scratch, double* partials, const int* active,
+                             cudaStream_t st, const cudaEvent_t* ev) {
+  return matvec_passes<T, XIN_PLAIN, XOUT_RV>(op, L, R, x, y, scratch, active, st, ev,
+                                              XinArgs<T>{}, rhat, partials);
+}
+
+template <typename T>
 cudaError_t launch_matvec_q(const OpView<T>& op, const MatvecLaunch& L, int R,
                             const cplx_t<T>* r, cplx_t<T>* q, cplx_t<T>* d, cplx_t<T>* x,
                             cplx_t<T>* t_vec, cplx_t<T>* scratch, const KState* ks,

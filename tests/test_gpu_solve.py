@@ -271,3 +271,35 @@ def test_refined_residual_in_double_float_equals_fp64_residual(B):
     r = E - O.matvec_direct(a["P"][0], pos, ainv, w.kd, "LDR")
     assert abs(np.linalg.norm(r) / np.linalg.norm(E) / a["resid"][0] - 1) < 1e-2
     t.close()
+
+
+# ---- BiCGstab(2) (the guide's PBCGS2) ------------------------------------------------
+@pytest.mark.parametrize("method", ["LDR", "FCD"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+def test_bicgstab2_small_ellipsoid(B, method, precision):
+    w = W.small_ellipsoid(6, 10, 12, m=1.5 + 0.1j, kd=0.4, method=method)
+    ref = _oracle(w)
+    t = B.Target(w.occ, w.comp, w.m, method=method)
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=2, tol=1e-10, precision=precision,
+                  dirs=w.dirs, solver="bicgstab2")
+    assert out["status"] == B.DDA_OK
+    _check(out, ref)
+    assert np.all(out["resid"] <= 1e-10 * 1.01)
+    assert np.all(out["iters"] % 2 == 0)       # whole cycles of two iterations
+    t.close()
+
+
+def test_bicgstab2_batched_and_circular(B):
+    w = W.small_ellipsoid(8, 6, 7, m=1.7 + 0.1j, kd=0.5, method="FCD", n_orient=4, seed=9)
+    t = B.Target(w.occ, w.comp, w.m, method="FCD")
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-10, precision="fp32_refined",
+                  dirs=w.dirs, solver="bicgstab2")
+    for i in range(4):
+        _check(out, _oracle(w, i), r0=2 * i)
+    x, y = np.array([1.0, 0, 0]), np.array([0, 1.0, 0])
+    e = np.array([0, 1, 1j]) / np.sqrt(2)
+    q = t.solve(w.kd, x, e, yhat=y, tol=1e-10, precision="fp64", solver="bicgstab2")
+    b = t.solve(w.kd, x, e, yhat=y, tol=1e-10, precision="fp64")
+    assert q["status"] == B.DDA_OK
+    assert np.allclose(q["Qext"], b["Qext"], rtol=1e-8)
+    t.close()
