@@ -293,16 +293,33 @@ __global__ void k_update_xr(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __r
   const C omega = from_d2<C>(ks[rr].omega);
   const int64_t off = (int64_t)rr * n;
   ChunkAcc<T, 4> acc;
-  GRID_LOOP(i, n) {
-    const C si = s[off + i];
-    x[off + i] = cadd(x[off + i], cadd(cmul(alpha, p[off + i]), cmul(omega, si)));
-    const C ri = csub(si, cmul(omega, t[off + i]));
-    r[off + i] = ri;
-    const C h = rhat[off + i];
-    acc.add(0, h.x * ri.x + h.y * ri.y);
-    acc.add(1, h.x * ri.y - h.y * ri.x);
-    acc.add(2, ri.x * ri.x + ri.y * ri.y);
-    acc.step();
+  // batches of U elements per thread, every load of a batch issued before its
+  // stores, so that 5 U loads per thread are in flight at once
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+    C xv[U], pv[U], sv[U], tv[U], hv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < n) {
+        xv[u] = x[off + i]; pv[u] = p[off + i]; sv[u] = s[off + i];
+        tv[u] = t[off + i]; hv[u] = rhat[off + i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i >= n) break;
+      x[off + i] = cadd(xv[u], cadd(cmul(alpha, pv[u]), cmul(omega, sv[u])));
+      const C ri = csub(sv[u], cmul(omega, tv[u]));
+      r[off + i] = ri;
+      const C h = hv[u];
+      acc.add(0, h.x * ri.x + h.y * ri.y);
+      acc.add(1, h.x * ri.y - h.y * ri.x);
+      acc.add(2, ri.x * ri.x + ri.y * ri.y);
+      acc.step();
+    }
   }
   acc.flush();
   write_partials<4>(acc.tot, partials);
@@ -481,13 +498,27 @@ __global__ void k_qmr_update_r(int64_t n, cplx_t<T>* __restrict__ r,
   const C alpha = from_d2<C>(ks[rr].alpha);
   const int64_t off = (int64_t)rr * n;
   ChunkAcc<T, 4> acc;
-  GRID_LOOP(i, n) {
-    const C ri = csub(r[off + i], cmul(alpha, t[off + i]));
-    r[off + i] = ri;
-    acc.add(0, ri.x * ri.x + ri.y * ri.y);
-    acc.add(1, ri.x * ri.x - ri.y * ri.y);
-    acc.add(2, (T)2 * ri.x * ri.y);
-    acc.step();
+  // batches of U elements per thread, loads before stores (as k_update_xr)
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+    C rv[U], tv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < n) { rv[u] = r[off + i]; tv[u] = t[off + i]; }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i >= n) break;
+      const C ri = csub(rv[u], cmul(alpha, tv[u]));
+      r[off + i] = ri;
+      acc.add(0, ri.x * ri.x + ri.y * ri.y);
+      acc.add(1, ri.x * ri.x - ri.y * ri.y);
+      acc.add(2, (T)2 * ri.x * ri.y);
+      acc.step();
+    }
   }
   acc.flush();
   write_partials<4>(acc.tot, partials);
