@@ -1,6 +1,7 @@
 // FFT-convolution matvec and its fused Krylov variants in FP32 (the inner
 // solve of the refined precision mode).  Kernels: matvec_impl.cuh.
 #include "matvec_impl.cuh"
+#include "matvec_tune.cuh"
 
 namespace dda {
 

@@ -2,6 +2,7 @@
 // solves, the Green-tensor setup transforms, the near field).  Kernels:
 // matvec_impl.cuh.
 #include "matvec_impl.cuh"
+#include "matvec_tune.cuh"
 
 namespace dda {
 

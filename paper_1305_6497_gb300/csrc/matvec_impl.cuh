@@ -795,161 +795,4 @@ cudaError_t launch_x_fwd(const OpView<T>& op, const MatvecLaunch& L, int R,
   return cudaGetLastError();
 }
 
-// --------------------------------------------------------------------------
-// autotuning of the launch schedule (tiles, lines, row pitch, Ghat staging)
-// --------------------------------------------------------------------------
-template <typename T>
-static void fill_x(const OpView<T>& op, MatvecLaunch& L, int nl) {
-  using C = cplx_t<T>;
-  L.x_lines = nl;
-  L.x_smem = (size_t)op.Lx * (nl + 1) * sizeof(C);
-  L.xinv_smem = L.x_smem + (size_t)2 * nl * op.nx * sizeof(C);
-}
-template <typename T>
-static void fill_y(const OpView<T>& op, MatvecLaunch& L, int tile) {
-  L.y_tile = tile;
-  L.y_smem = (size_t)op.Ly * tile * sizeof(cplx_t<T>);
-}
-template <typename T>
-static void fill_z(const OpView<T>& op, MatvecLaunch& L, int tile, int pad, bool gs) {
-  using C = cplx_t<T>;
-  L.z_tile = tile;
-  L.z_ps = 3 * tile + pad;
-  L.z_gs = gs;
-  L.z_smem = (((size_t)op.Lz * L.z_ps * sizeof(C) + 15) & ~(size_t)15) +
-             (gs ? (size_t)6 * op.Hz * tile * sizeof(C) : 0);
-}
-
-// Launch one pass `reps` times between two events; returns the mean in ms.
-template <typename T>
-// The x passes are timed in their fused forms (a vector-update prologue, an
-// inner-product epilogue), which read more than the plain ones.
-static float time_pass(const OpView<T>& op, const MatvecLaunch& L, int pass, int R,
-                       const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch, cudaStream_t st,
-                       cudaEvent_t e0, cudaEvent_t e1, int reps, const KState* ks,
-                       double* part) {
-  const int rows = 3 * op.nz * op.ny;
-  dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
-  dim3 gy((op.Lx + L.y_tile - 1) / L.y_tile, 3 * op.nz, R);
-  dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
-  auto launch = [&]() {
-    switch (pass) {
-      case 0: {
-        XinArgs<T> xa{x, y, x, ks, nullptr, nullptr};  // s <- x - alpha x, into y
-        k_fft_x_fwd<T, XIN_S><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines,
-                                                                 nullptr, xa);
-        break;
-      }
-      case 1: k_fft_y<T, false><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, nullptr); break;
-      case 2:
-#define DDA_ZT(TT, GG) \
-  k_fft_z_mul<T, TT, GG><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, nullptr)
-        if (L.z_gs) {
-          switch (L.z_tile) { case 16: DDA_ZT(16, true); break; case 8: DDA_ZT(8, true); break;
-                              case 4: DDA_ZT(4, true); break; default: DDA_ZT(2, true); }
-        } else {
-          switch (L.z_tile) { case 16: DDA_ZT(16, false); break; case 8: DDA_ZT(8, false); break;
-                              case 4: DDA_ZT(4, false); break; default: DDA_ZT(2, false); }
-        }
-#undef DDA_ZT
-        break;
-      case 3: k_fft_y<T, true><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, nullptr); break;
-      default:
-        k_fft_x_inv<T, XOUT_RV><<<gx, L.x_threads, L.xinv_smem, st>>>(
-            op, scratch, x, y, L.x_lines, nullptr, x, part);
-    }
-  };
-  launch();  // warm-up
-  cudaEventRecord(e0, st);
-  for (int i = 0; i < reps; ++i) launch();
-  cudaEventRecord(e1, st);
-  if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) return 1e30f;
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  return ms / reps;
-}
-
-template <typename T>
-cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const cplx_t<T>* x,
-                            cplx_t<T>* y, cplx_t<T>* scratch, cudaStream_t st) {
-  using C = cplx_t<T>;
-  cudaEvent_t e0, e1;
-  cudaError_t e = cudaEventCreate(&e0);
-  if (e != cudaSuccess) return e;
-  e = cudaEventCreate(&e1);
-  if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
-  // a zero Krylov state (alpha = 0) and partial sums for the fused x passes,
-  // sized for the smallest line count tried (2 lines per CTA)
-  KState* ks = nullptr;
-  double* part = nullptr;
-  const size_t nks = sizeof(KState) * (size_t)R;
-  const size_t npart = sizeof(double) * 2 * (size_t)R * (3 * (size_t)op.nz * op.ny / 2 + 1);
-  e = cudaMalloc(&ks, nks);
-  if (e == cudaSuccess) e = cudaMalloc(&part, npart);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ks, 0, nks, st);
-  if (e != cudaSuccess) {
-    cudaFree(ks); cudaFree(part); cudaEventDestroy(e0); cudaEventDestroy(e1);
-    return e;
-  }
-  const int reps = 6;
-  const size_t kMax = 200 * 1024;
-  MatvecLaunch best = L;
-  // Thread counts are tuned with the tiles: a CTA's stages have different
-  // numbers of butterflies (e.g. 128-point lines as 16 x 8), and threads left
-  // without one wait at the stage's barrier.
-  // x passes (forward and inverse together)
-  {
-    float bt = time_pass<T>(op, best, 0, R, x, y, scratch, st, e0, e1, reps, ks, part) +
-               time_pass<T>(op, best, 4, R, x, y, scratch, st, e0, e1, reps, ks, part);
-    for (int nl : {2, 4, 8, 16, 32, 64})
-      for (int th : {64, 96, 128, 192, 256}) {
-        MatvecLaunch c = best;
-        fill_x<T>(op, c, nl);
-        c.x_threads = th;
-        if (c.xinv_smem > kMax || nl > 3 * op.nz * op.ny) continue;
-        const float tt = time_pass<T>(op, c, 0, R, x, y, scratch, st, e0, e1, reps, ks, part) +
-                         time_pass<T>(op, c, 4, R, x, y, scratch, st, e0, e1, reps, ks, part);
-        if (tt < bt) { bt = tt; best = c; }
-      }
-  }
-  // y passes
-  {
-    float bt = time_pass<T>(op, best, 1, R, x, y, scratch, st, e0, e1, reps, ks, part) +
-               time_pass<T>(op, best, 3, R, x, y, scratch, st, e0, e1, reps, ks, part);
-    for (int tile : {2, 4, 8, 16, 32})
-      for (int th : {64, 96, 128, 192, 256}) {
-        MatvecLaunch c = best;
-        fill_y<T>(op, c, tile);
-        c.y_threads = th;
-        if (c.y_smem > kMax) continue;
-        const float tt = time_pass<T>(op, c, 1, R, x, y, scratch, st, e0, e1, reps, ks, part) +
-                         time_pass<T>(op, c, 3, R, x, y, scratch, st, e0, e1, reps, ks, part);
-        if (tt < bt) { bt = tt; best = c; }
-      }
-  }
-  // z pass
-  {
-    float bt = time_pass<T>(op, best, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);
-    for (int tile : {2, 4, 8, 16})
-      for (int gs = 0; gs < 2; ++gs)
-        for (int pad = 0; pad < 4; ++pad)
-          for (int th : {64, 96, 128, 192, 256}) {
-            MatvecLaunch c = best;
-            fill_z<T>(op, c, tile, pad, gs != 0);
-            c.z_threads = th;
-            if (c.z_smem > kMax) continue;
-            const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);
-            if (tt < bt) { bt = tt; best = c; }
-          }
-  }
-  (void)sizeof(C);
-  cudaStreamSynchronize(st);
-  cudaFree(ks);
-  cudaFree(part);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  L = best;
-  return cudaGetLastError();
-}
-
 }  // namespace dda
