@@ -41,7 +41,9 @@ __global__ void k_bs2_a(int64_t n, const cplx_t<T>* __restrict__ r0, cplx_t<T>* 
   using C = cplx_t<T>;
   const int rr = blockIdx.y;
   if (!active[rr]) return;
-  const C beta = d2c<C>(ks[rr].beta);
+  C sc[1];
+  block_scalars<C, 1>({ks[rr].beta}, sc);
+  const C beta = sc[0];
   const int64_t off = (int64_t)rr * n;
   GRID_LOOP(i, n) u0[off + i] = csub(r0[off + i], cmul(beta, u0[off + i]));
 }
@@ -53,7 +55,9 @@ __global__ void k_bs2_b(int64_t n, cplx_t<T>* __restrict__ r0, const cplx_t<T>* 
   using C = cplx_t<T>;
   const int rr = blockIdx.y;
   if (!active[rr]) return;
-  const C alpha = d2c<C>(ks[rr].alpha);
+  C sc[1];
+  block_scalars<C, 1>({ks[rr].alpha}, sc);
+  const C alpha = sc[0];
   const int64_t off = (int64_t)rr * n;
   GRID_LOOP(i, n) r0[off + i] = csub(r0[off + i], cmul(alpha, u1[off + i]));
 }
@@ -67,7 +71,9 @@ __global__ void k_bs2_c(int64_t n, cplx_t<T>* __restrict__ x, const cplx_t<T>* _
   using C = cplx_t<T>;
   const int rr = blockIdx.y;
   if (!active[rr]) return;
-  const C alpha = d2c<C>(ks[rr].alpha), beta = d2c<C>(ks[rr].beta);
+  C sc[2];
+  block_scalars<C, 2>({ks[rr].alpha, ks[rr].beta}, sc);
+  const C alpha = sc[0], beta = sc[1];
   const int64_t off = (int64_t)rr * n;
   GRID_LOOP(i, n) {
     const int64_t g = off + i;
@@ -87,7 +93,9 @@ __global__ void k_bs2_d(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __restr
   using C = cplx_t<T>;
   const int rr = blockIdx.y;
   if (!active[rr]) return;
-  const C alpha = d2c<C>(ks[rr].alpha);
+  C sc[1];
+  block_scalars<C, 1>({ks[rr].alpha}, sc);
+  const C alpha = sc[0];
   const int64_t off = (int64_t)rr * n;
   GRID_LOOP(i, n) {
     const int64_t g = off + i;
@@ -119,8 +127,7 @@ __global__ void k_bs2_gram(int64_t n, const cplx_t<T>* __restrict__ r0,
     acc.add(7, c.x * a.y - c.y * a.x);
     acc.step();
   }
-  acc.flush();
-  write_partials<8>(acc.tot, partials);
+  acc.template write<8>(partials);
 }
 
 // minimal-residual update: u0 -= g1 u1 + g2 u2; x += g1 r0 + g2 r1;
@@ -135,7 +142,9 @@ __global__ void k_bs2_e(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __restr
   using C = cplx_t<T>;
   const int rr = blockIdx.y;
   if (!active[rr]) return;
-  const C g1 = d2c<C>(ks[rr].qa1), g2 = d2c<C>(ks[rr].qa2);
+  C sc[2];
+  block_scalars<C, 2>({ks[rr].qa1, ks[rr].qa2}, sc);
+  const C g1 = sc[0], g2 = sc[1];
   const int64_t off = (int64_t)rr * n;
   ChunkAcc<T, 4> acc;
   GRID_LOOP(i, n) {
@@ -152,8 +161,7 @@ __global__ void k_bs2_e(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __restr
     acc.add(2, rn.x * rn.x + rn.y * rn.y);
     acc.step();
   }
-  acc.flush();
-  write_partials<4>(acc.tot, partials);
+  acc.template write<4>(partials);
 }
 
 // Scalar steps, one block per RHS.  KState use: rho = rho0, rho_old = the

@@ -84,8 +84,7 @@ __global__ void k_bicg_init(int64_t n, const cplx_t<T>* __restrict__ b,
     acc.add(1, bi.x * bi.x + bi.y * bi.y);
     acc.step();
   }
-  acc.flush();
-  write_partials<2>(acc.tot, partials);
+  acc.template write<2>(partials);
 }
 
 template <typename T>
@@ -172,8 +171,7 @@ __global__ void k_dot_rhat_v(int64_t n, const cplx_t<T>* __restrict__ rhat,
     acc.add(1, a.x * b.y - a.y * b.x);
     acc.step();
   }
-  acc.flush();
-  write_partials<2>(acc.tot, partials);
+  acc.template write<2>(partials);
 }
 
 template <typename T>
@@ -247,8 +245,7 @@ __global__ void k_dot_ts(int64_t n, const cplx_t<T>* __restrict__ t,
     acc.add(2, a.x * a.x + a.y * a.y);
     acc.step();
   }
-  acc.flush();
-  write_partials<4>(acc.tot, partials);
+  acc.template write<4>(partials);
 }
 
 template <typename T>
@@ -289,8 +286,9 @@ __global__ void k_update_xr(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __r
   using C = cplx_t<T>;
   const int rr = blockIdx.y;
   if (!active[rr]) return;
-  const C alpha = from_d2<C>(ks[rr].alpha);
-  const C omega = from_d2<C>(ks[rr].omega);
+  C sc[2];
+  block_scalars<C, 2>({ks[rr].alpha, ks[rr].omega}, sc);
+  const C alpha = sc[0], omega = sc[1];
   const int64_t off = (int64_t)rr * n;
   ChunkAcc<T, 4> acc;
   // batches of U elements per thread, every load of a batch issued before its
@@ -321,8 +319,7 @@ __global__ void k_update_xr(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __r
       acc.step();
     }
   }
-  acc.flush();
-  write_partials<4>(acc.tot, partials);
+  acc.template write<4>(partials);
 }
 
 template <typename T>
@@ -405,8 +402,7 @@ __global__ void k_qmr_init(int64_t n, const cplx_t<T>* __restrict__ b,
     acc.add(3, (T)2 * ri.x * ri.y);
     acc.step();
   }
-  acc.flush();
-  write_partials<4>(acc.tot, partials);
+  acc.template write<4>(partials);
 }
 
 template <typename T>
@@ -495,7 +491,9 @@ __global__ void k_qmr_update_r(int64_t n, cplx_t<T>* __restrict__ r,
   using C = cplx_t<T>;
   const int rr = blockIdx.y;
   if (!active[rr]) return;
-  const C alpha = from_d2<C>(ks[rr].alpha);
+  C sc[1];
+  block_scalars<C, 1>({ks[rr].alpha}, sc);
+  const C alpha = sc[0];
   const int64_t off = (int64_t)rr * n;
   ChunkAcc<T, 4> acc;
   // batches of U elements per thread, loads before stores (as k_update_xr)
@@ -520,8 +518,7 @@ __global__ void k_qmr_update_r(int64_t n, cplx_t<T>* __restrict__ r,
       acc.step();
     }
   }
-  acc.flush();
-  write_partials<4>(acc.tot, partials);
+  acc.template write<4>(partials);
 }
 
 template <typename T>

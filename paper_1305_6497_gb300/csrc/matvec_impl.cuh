@@ -64,15 +64,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpVie
   const int ps = nlines + 1;
   const int64_t off = (int64_t)r * rows * nx;
   C c1 = mk<C>(0, 0), c2 = mk<C>(0, 0), c3 = mk<C>(0, 0);
-  if (MODE == XIN_P) {
-    c1 = mk<C>(xa.ks[r].beta.x, xa.ks[r].beta.y);
-    c2 = mk<C>(xa.ks[r].omega.x, xa.ks[r].omega.y);
-  } else if (MODE == XIN_S) {
-    c1 = mk<C>(xa.ks[r].alpha.x, xa.ks[r].alpha.y);
-  } else if (MODE == XIN_Q) {
-    c1 = mk<C>(xa.ks[r].beta.x, xa.ks[r].beta.y);
-    c2 = mk<C>(xa.ks[r].qa1.x, xa.ks[r].qa1.y);
-    c3 = mk<C>(xa.ks[r].qa2.x, xa.ks[r].qa2.y);
+  if constexpr (MODE == XIN_P) {
+    C sc[2];
+    block_scalars<C, 2>({xa.ks[r].beta, xa.ks[r].omega}, sc);
+    c1 = sc[0]; c2 = sc[1];
+  } else if constexpr (MODE == XIN_S) {
+    C sc[1];
+    block_scalars<C, 1>({xa.ks[r].alpha}, sc);
+    c1 = sc[0];
+  } else if constexpr (MODE == XIN_Q) {
+    C sc[3];
+    block_scalars<C, 3>({xa.ks[r].beta, xa.ks[r].qa1, xa.ks[r].qa2}, sc);
+    c1 = sc[0]; c2 = sc[1]; c3 = sc[2];
   }
   // the CTA's rows are one contiguous chunk of the box vector.  Elements go in
   // batches of U per thread with every load of a batch issued before any
@@ -554,13 +557,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   }
   }
   if constexpr (MODE != XOUT_PLAIN && MODE != XOUT_FIELD) {
-    acc.flush();
-    if (MODE == XOUT_RV || MODE == XOUT_QT) {
-      double v2[2] = {acc.tot[0], acc.tot[1]};
-      write_partials<2>(v2, partials);
-    } else {
-      write_partials<4>(acc.tot, partials);
-    }
+    if constexpr (MODE == XOUT_RV || MODE == XOUT_QT) acc.template write<2>(partials);
+    else acc.template write<4>(partials);
   }
 }
 
