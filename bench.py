@@ -319,7 +319,10 @@ def run_gpu(args, rank, world, local_rank):
 
     # ---- the other Krylov methods on the same refined FP32 solve ----
     solver_cmp = {}
-    for other in [s for s in ("bicgstab", "qmr", "bicgstab2") if s != args.solver]:
+    # normal-equation CG needs many more iterations; it is timed on the smaller
+    # workloads only
+    others = ["bicgstab", "qmr", "bicgstab2", "gpbicg"] + (["petrkp"] if N <= 1_000_000 else [])
+    for other in [s for s in others if s != args.solver]:
         kwo = dict(kw, solver=other)
         t.solve(w.kd, w.khat, w.e01, precision="fp32_refined", want_P=False, **kwo)
         ms_o, it_o, mv_o = [], [], []
@@ -440,7 +443,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sphere64", choices=sorted(WORKLOADS))
-    ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "qmr", "bicgstab2"],
+    ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "qmr", "bicgstab2", "gpbicg", "petrkp"],
                     help="Krylov method of the timed solves (the others are timed beside)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

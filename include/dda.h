@@ -97,8 +97,22 @@ typedef enum {
  *             two-dimensional minimal-residual step; a cycle counts as two
  *             iterations; stops on the recursive residual checked after each
  *             cycle (breakdowns finish with BiCGSTAB as for QMR).
- * Either way the reported residual is the FP64 true residual of the result. */
-typedef enum { DDA_SOLVER_BICGSTAB = 0, DDA_SOLVER_QMR = 1, DDA_SOLVER_BICGSTAB2 = 2 } dda_solver;
+ *  GPBICG   : GPBi-CG (Zhang 1997), the guide's GPBICG: two matvecs per
+ *             iteration; each iteration minimises the residual over a
+ *             two-parameter (zeta, eta) update (eta = 0 gives BiCGSTAB); stops
+ *             on the recursive residual (breakdowns finish with BiCGSTAB).
+ *  PETRKP   : conjugate gradients on the normal equations A^H A P = A^H E
+ *             (Petravic & Kuo-Petravic 1979), the guide's PETRKP: two matvecs
+ *             per iteration (A p and A^H r = conj(A conj(r)), since A = A^T);
+ *             slow but monotone in ||E - A P||, on which it stops.
+ * Every method's reported residual is the FP64 true residual of the result. */
+typedef enum {
+  DDA_SOLVER_BICGSTAB = 0,
+  DDA_SOLVER_QMR = 1,
+  DDA_SOLVER_BICGSTAB2 = 2,
+  DDA_SOLVER_GPBICG = 3,
+  DDA_SOLVER_PETRKP = 4
+} dda_solver;
 
 typedef struct dda_target dda_target; /* opaque, library-owned */
 
@@ -183,8 +197,9 @@ typedef struct {
                             y sin(theta) cos(phi) + z sin(theta) sin(phi)       */
   const double* P0;      /* optional warm start [n_inc*npol][N][3][2] or NULL   */
   int profile;           /* nonzero: time each FFT-matvec pass with CUDA events   */
-  int solver;            /* dda_solver: DDA_SOLVER_BICGSTAB (0, default), _QMR or
-                            _BICGSTAB2; unknown values: DDA_ERR_INVALID_ARG     */
+  int solver;            /* dda_solver: DDA_SOLVER_BICGSTAB (0, default), _QMR,
+                            _BICGSTAB2, _GPBICG or _PETRKP; unknown values:
+                            DDA_ERR_INVALID_ARG                                 */
   int fp64_residual;     /* FP32_REFINED only: 0 (default) computes the refinement's
                             residuals E - A P with FP64 box vectors and FFT passes in
                             double-float arithmetic (pairs of FP32 values, ~48 bits,

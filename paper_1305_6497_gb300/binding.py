@@ -19,7 +19,7 @@ DDA_OK, DDA_ERR_INVALID_ARG, DDA_ERR_OOM, DDA_ERR_CUDA, DDA_ERR_NOCONV, \
     DDA_ERR_BREAKDOWN, DDA_ERR_TIMEOUT = range(7)
 POL = {"CM": 0, "LDR": 1, "FCD": 2}
 PREC = {"fp64": 0, "fp32": 1, "fp32_refined": 2, "df64": 3}
-SOLVER = {"bicgstab": 0, "qmr": 1, "bicgstab2": 2}
+SOLVER = {"bicgstab": 0, "qmr": 1, "bicgstab2": 2, "gpbicg": 3, "petrkp": 4}
 
 _dp = ct.POINTER(ct.c_double)
 _ip = ct.POINTER(ct.c_int)
@@ -246,8 +246,10 @@ def _params(kd, khat, e01, yhat, npol, tol, max_iter, precision, inner_tol, dirs
     return prm, keep, n_inc
 
 
-def dda_solve_hbm_bytes(h, kd, khat, e01, npol=2, precision="fp64", dirs=None) -> int:
-    prm, keep, _ = _params(kd, khat, e01, None, npol, 1e-8, 1, precision, 0.0, dirs, None)
+def dda_solve_hbm_bytes(h, kd, khat, e01, npol=2, precision="fp64", dirs=None,
+                       solver="bicgstab") -> int:
+    prm, keep, _ = _params(kd, khat, e01, None, npol, 1e-8, 1, precision, 0.0, dirs, None,
+                           solver=solver)
     return int(lib.dda_solve_hbm_bytes(h, ct.byref(prm)))
 
 
@@ -256,8 +258,11 @@ def dda_solve(h, kd, khat, e01, yhat=None, npol=2, tol=1e-8, max_iter=2000,
               want_famp=True, raise_on_noconv=False, profile=False,
               solver="bicgstab", fp64_residual=False) -> dict:
     """Solve for every incidence x polarization.  Returns a dict of numpy arrays.
-    solver: "bicgstab" (two matvecs per iteration) or "qmr" (complex-symmetric
-    QMR, one matvec per iteration)."""
+    solver: "bicgstab" (two matvecs per iteration), "qmr" (complex-symmetric
+    QMR, one matvec per iteration), "bicgstab2" (BiCGstab(2), four matvecs per
+    two-iteration cycle), "gpbicg" (GPBi-CG, two matvecs per iteration) or
+    "petrkp" (conjugate gradients on the normal equations, two matvecs per
+    iteration)."""
     prm, keep, n_inc = _params(kd, khat, e01, yhat, npol, tol, max_iter, precision,
                                inner_tol, dirs, P0, profile, solver, fp64_residual)
     N = dda_target_num_dipoles(h)

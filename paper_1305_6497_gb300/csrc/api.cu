@@ -782,6 +782,198 @@ static void bicgstab2(dda_target* t, const OpView<T>& op, const MatvecLaunch& L,
   }
 }
 
+// Runs one block of iterations as a CUDA graph (captured on first use, rebuilt
+// when `sig` changes) until every RHS is frozen on the device.  `per_block`
+// iterations of `nmv` matvecs each are enqueued by `enqueue`.
+template <typename T, class ENQ>
+static void run_graph_loop(dda_target* t, const std::vector<uintptr_t>& sig, int per_block,
+                           int nmv, int max_iter, int nact, std::vector<int>& hact,
+                           const ENQ& enqueue) {
+  cudaStream_t st = t->stream;
+  int* act = t->ws.active.as<int>();
+  const int R = (int)hact.size();
+  IterGraph& g = t->graphs[sizeof(T) == 4 ? 0 : 1];
+  if (g.exec && g.sig != sig) g.reset();
+  if (!g.exec) {
+    const long long before = launch_count();
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue();
+    } catch (...) {
+      cudaGraph_t broken = nullptr;
+      cudaStreamEndCapture(st, &broken);
+      if (broken) cudaGraphDestroy(broken);
+      throw;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamEndCapture(st, &graph));
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie);
+    g.kernels = launch_count() - before;
+    note_launches(-g.kernels);
+    g.sig = sig;
+  }
+  int iter = 0;
+  while (nact > 0 && iter < max_iter) {
+    CK(cudaGraphLaunch(g.exec, st));
+    note_launches(g.kernels);
+    CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    t->prof.harvest_iters(sizeof(T) == 4 ? 0 : 1, per_block, nmv);
+    nact = 0;
+    for (int a : hact) nact += a;
+    iter += per_block;
+  }
+}
+
+static void finish_states(dda_target* t, int R, int nmv, std::vector<int>& its,
+                          std::vector<int>& status, int64_t& matvecs) {
+  std::vector<KState> hks(R);
+  CK(cudaMemcpyAsync(hks.data(), t->ws.ks.as<KState>(), sizeof(KState) * R,
+                     cudaMemcpyDeviceToHost, t->stream));
+  CK(cudaStreamSynchronize(t->stream));
+  its.resize(R);
+  status.resize(R);
+  for (int r = 0; r < R; ++r) {
+    matvecs += nmv * (int64_t)hks[r].iters;
+    its[r] = hks[r].iters;
+    status[r] = hks[r].status == KS_RUN ? KS_NOCONV : hks[r].status;
+  }
+}
+
+static int active_count(dda_target* t, std::vector<int>& hact) {
+  CK(cudaMemcpyAsync(hact.data(), t->ws.active.as<int>(), sizeof(int) * hact.size(),
+                     cudaMemcpyDeviceToHost, t->stream));
+  CK(cudaStreamSynchronize(t->stream));
+  int nact = 0;
+  for (int a : hact) nact += a;
+  return nact;
+}
+
+// ---------------------------------------------------------------------------
+// GPBi-CG driver (the guide's GPBICG), R RHS in lockstep: r, the shadow vector,
+// p, q = A p, t and At = A t in V.r, V.rh, V.p, V.v, V.t, V.s; y, u, z, w in
+// four extra workspace vectors.  Iterations (two matvecs each) are captured
+// kCheckEvery per CUDA graph.
+// ---------------------------------------------------------------------------
+template <typename T>
+static void gpbicg(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R,
+                   const Vecs<T>& V, bool x_nonzero, double tol, int max_iter,
+                   std::vector<int>& its, std::vector<int>& status, int64_t& matvecs) {
+  using C = cplx_t<T>;
+  Workspace& w = t->ws;
+  const int64_t n = 3 * t->nbox;
+  const int nblk = reduce_blocks(n);
+  double* part = w.partials.as<double>();
+  KState* ks = w.ks.as<KState>();
+  int* act = w.active.as<int>();
+  cudaStream_t st = t->stream;
+  DevBuf& xb = sizeof(T) == 4 ? w.extra32 : w.extra64;
+  xb.ensure(4 * sizeof(C) * n * R);
+  C* ex = xb.as<C>();
+  const GpVecs<T> g{V.x, V.r, V.p, V.v, V.t, V.s, ex, ex + n * R, ex + 2 * n * R,
+                    ex + 3 * n * R, V.rh};
+  if (x_nonzero) {
+    CK(launch_matvec<T>(op, L, R, V.x, V.s, V.scr, nullptr, st));
+    matvecs += R;
+    CK(launch_bicg_init<T>(n, R, V.b, V.s, V.r, V.rh, V.p, V.v, part, st));
+  } else {
+    CK(launch_bicg_init<T>(n, R, V.b, nullptr, V.r, V.rh, V.p, V.v, part, st));
+  }
+  CK(launch_state_init(R, nblk, part, ks, act, tol, max_iter, st));
+  // t, At, u and z start at zero (p and q are zeroed by the set-up, beta = 0)
+  const size_t vb = sizeof(C) * n * R;
+  CK(cudaMemsetAsync(g.t, 0, vb, st));
+  CK(cudaMemsetAsync(g.at, 0, vb, st));
+  CK(cudaMemsetAsync(g.u, 0, vb, st));
+  CK(cudaMemsetAsync(g.z, 0, vb, st));
+  std::vector<int> hact(R);
+  const int nact = active_count(t, hact);
+  const int nblk_mv = matvec_partial_blocks<T>(op, L);
+  auto enqueue = [&]() {
+    for (int q = 0; q < kCheckEvery; ++q) {
+      CK(launch_gp_vec<T>(0, n, R, g, part, ks, act, st));                 // p, w
+      CK(launch_matvec_rv<T>(op, L, R, g.p, g.q, g.rt, V.scr, part, act, st,
+                             t->prof.iter_set(q, 0)));                      // q = A p
+      CK(launch_scalar_alpha(R, nblk_mv, part, ks, act, st));               // alpha
+      CK(launch_gp_vec<T>(1, n, R, g, part, ks, act, st));                 // t, y, u
+      CK(launch_matvec<T>(op, L, R, g.t, g.at, V.scr, act, st,
+                          t->prof.iter_set(q, 1)));                         // At = A t
+      CK(launch_gp_vec<T>(2, n, R, g, part, ks, act, st));                 // 2x2 sums
+      CK(launch_gp_zeta(R, nblk, part, ks, act, st));                      // zeta, eta
+      CK(launch_gp_vec<T>(3, n, R, g, part, ks, act, st));                 // u, z, x, r
+      CK(launch_scalar_rho(R, nblk, part, ks, act, st));                   // beta, convergence
+    }
+  };
+  const std::vector<uintptr_t> sig = {
+      (uintptr_t)3000 + sizeof(T), (uintptr_t)R, (uintptr_t)t->prof.on, (uintptr_t)V.x,
+      (uintptr_t)V.r, (uintptr_t)V.rh, (uintptr_t)V.p, (uintptr_t)V.v, (uintptr_t)V.t,
+      (uintptr_t)V.s, (uintptr_t)ex, (uintptr_t)V.scr, (uintptr_t)ks, (uintptr_t)part,
+      (uintptr_t)act, (uintptr_t)op.ghat, (uintptr_t)op.ainv, (uintptr_t)nblk_mv,
+      (uintptr_t)nblk, (uintptr_t)t->schedule_gen};
+  run_graph_loop<T>(t, sig, kCheckEvery, 2, max_iter, nact, hact, enqueue);
+  finish_states(t, R, 2, its, status, matvecs);
+}
+
+// ---------------------------------------------------------------------------
+// Conjugate gradients on the normal equations (the guide's PETRKP), R RHS in
+// lockstep: r, c = conj(r), p, w = A p and m = A c in V.r, V.rh, V.p, V.v, V.s.
+// ---------------------------------------------------------------------------
+template <typename T>
+static void cgnr(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R,
+                 const Vecs<T>& V, bool x_nonzero, double tol, int max_iter,
+                 std::vector<int>& its, std::vector<int>& status, int64_t& matvecs) {
+  Workspace& w = t->ws;
+  const int64_t n = 3 * t->nbox;
+  const int nblk = reduce_blocks(n);
+  double* part = w.partials.as<double>();
+  KState* ks = w.ks.as<KState>();
+  int* act = w.active.as<int>();
+  cudaStream_t st = t->stream;
+  cplx_t<T>*r = V.r, *c = V.rh, *p = V.p, *wv = V.v, *m = V.s;
+  if (x_nonzero) {
+    CK(launch_matvec<T>(op, L, R, V.x, V.s, V.scr, nullptr, st));
+    matvecs += R;
+    CK(launch_bicg_init<T>(n, R, V.b, V.s, r, c, p, wv, part, st));
+  } else {
+    CK(launch_bicg_init<T>(n, R, V.b, nullptr, r, c, p, wv, part, st));
+  }
+  CK(launch_state_init(R, nblk, part, ks, act, tol, max_iter, st));
+  auto vec = [&](int which) {
+    CK(launch_cg_vec<T>(which, n, R, V.x, r, p, wv, c, m, part, ks, act, st));
+  };
+  // p = A^H r = conj(A conj(r)), gamma = ||p||^2
+  vec(0);
+  CK(launch_matvec<T>(op, L, R, c, m, V.scr, act, st));
+  vec(3);
+  CK(launch_cg_scalar(0, R, nblk, part, ks, act, st));
+  vec(4);
+  std::vector<int> hact(R);
+  const int nact = active_count(t, hact);
+  matvecs += nact;
+  auto enqueue = [&]() {
+    for (int q = 0; q < kCheckEvery; ++q) {
+      CK(launch_matvec<T>(op, L, R, p, wv, V.scr, act, st, t->prof.iter_set(q, 0)));  // w = A p
+      vec(1);                                                          // ||w||^2
+      CK(launch_cg_scalar(1, R, nblk, part, ks, act, st));             // alpha
+      vec(2);                                                          // x, r, c = conj(r)
+      CK(launch_cg_scalar(2, R, nblk, part, ks, act, st));             // convergence
+      CK(launch_matvec<T>(op, L, R, c, m, V.scr, act, st, t->prof.iter_set(q, 1)));  // m = A c
+      vec(3);                                                          // ||m||^2
+      CK(launch_cg_scalar(3, R, nblk, part, ks, act, st));             // beta, gamma
+      vec(5);                                                          // p = conj(m) + beta p
+    }
+  };
+  const std::vector<uintptr_t> sig = {
+      (uintptr_t)4000 + sizeof(T), (uintptr_t)R, (uintptr_t)t->prof.on, (uintptr_t)V.x,
+      (uintptr_t)r, (uintptr_t)c, (uintptr_t)p, (uintptr_t)wv, (uintptr_t)m,
+      (uintptr_t)V.scr, (uintptr_t)ks, (uintptr_t)part, (uintptr_t)act, (uintptr_t)op.ghat,
+      (uintptr_t)op.ainv, (uintptr_t)nblk, (uintptr_t)t->schedule_gen};
+  run_graph_loop<T>(t, sig, kCheckEvery, 2, max_iter, nact, hact, enqueue);
+  finish_states(t, R, 2, its, status, matvecs);
+}
+
 // Krylov solve with the requested method.  QMR's bilinear Lanczos process
 // breaks down when r^T r vanishes for r != 0 (circularly polarized incident
 // light makes E . E = 0 at every site), and BiCGstab(2) when its 2x2
@@ -798,6 +990,10 @@ static void krylov(int solver, dda_target* t, const OpView<T>& op, const MatvecL
   }
   if (solver == DDA_SOLVER_QMR)
     qmr<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
+  else if (solver == DDA_SOLVER_GPBICG)
+    gpbicg<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
+  else if (solver == DDA_SOLVER_PETRKP)
+    cgnr<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
   else
     bicgstab2<T>(t, op, L, R, V, x_nonzero, tol, max_iter, its, status, matvecs);
   bool broke = false;
@@ -1105,6 +1301,9 @@ int64_t dda_solve_hbm_bytes(const dda_target* t, const dda_solve_params* p) {
   if (!t || !p || p->n_inc < 1 || (p->npol != 1 && p->npol != 2) || p->n_dirs < 0) return -1;
   const int R = p->n_inc * p->npol;
   int64_t b = workspace_bytes(t, R, p->precision, p->n_dirs);
+  // the method's extra Krylov vectors (BiCGstab(2): r2; GPBi-CG: y, u, z, w)
+  const int nextra = p->solver == DDA_SOLVER_BICGSTAB2 ? 1 : p->solver == DDA_SOLVER_GPBICG ? 4 : 0;
+  b += (int64_t)nextra * 3 * t->nbox * R * (p->precision == DDA_PREC_FP64 ? 16 : 8);
   const int filtered = t->method == DDA_POL_FCD ? 1 : 0;
   if (!(t->have_green && t->green_kd == p->kd && t->green_filtered == filtered)) {
     const int64_t M = (int64_t)t->Lx * t->Ly * t->Lz;
@@ -1204,8 +1403,7 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
   if (p->precision != DDA_PREC_FP64 && p->precision != DDA_PREC_FP32 &&
       p->precision != DDA_PREC_FP32_REFINED)
     return fail(DDA_ERR_INVALID_ARG, "unknown precision");
-  if (p->solver != DDA_SOLVER_BICGSTAB && p->solver != DDA_SOLVER_QMR &&
-      p->solver != DDA_SOLVER_BICGSTAB2)
+  if (p->solver < DDA_SOLVER_BICGSTAB || p->solver > DDA_SOLVER_PETRKP)
     return fail(DDA_ERR_INVALID_ARG, "unknown solver");
   const int R = p->n_inc * p->npol;
   if (R > 4096) return fail(DDA_ERR_INVALID_ARG, "at most 4096 right-hand sides");

@@ -210,6 +210,36 @@ cudaError_t launch_bs2_vec(int which, int64_t n, int R, cplx_t<T>* x, cplx_t<T>*
                            const KState* ks, const int* active, cudaStream_t st);
 cudaError_t launch_bs2_scalar(int phase, int R, int nblk, const double* partials, KState* ks,
                               int* active, cudaStream_t st);
+
+// GPBi-CG building blocks (gpbicg.cu), vectors of R RHS ([R][n] each).
+// launch_gp_vec `which`:
+//  0: p = r + beta (p - u), w = At + beta q
+//  1: t' = r - alpha q, y = t - t' - alpha w, u = t - r + beta u, t = t'
+//  2: partials <At,t>, <At,At>, <y,y>, <At,y>, <y,t> ([R][nblk][8])
+//  3: u, z, x, r updates with partials <rt, r>, ||r||^2 ([R][nblk][4], the
+//     layout launch_scalar_rho reads)
+// launch_gp_zeta: zeta -> KState.omega, eta -> KState.qa1.
+template <typename T> struct GpVecs {
+  cplx_t<T>*x, *r, *p, *q, *t, *at, *y, *u, *z, *w;
+  const cplx_t<T>* rt;
+};
+template <typename T>
+cudaError_t launch_gp_vec(int which, int64_t n, int R, const GpVecs<T>& v, double* partials,
+                          const KState* ks, const int* active, cudaStream_t st);
+cudaError_t launch_gp_zeta(int R, int nblk, const double* partials, KState* ks, int* active,
+                           cudaStream_t st);
+// Conjugate gradients on the normal equations (gpbicg.cu).  launch_cg_vec
+// `which`: 0: c = conj(r) (active may be NULL);  1: partials ||w||^2;
+//  2: x += alpha p, r -= alpha w, c = conj(r), partials ||r||^2;
+//  3: partials ||m||^2;  4: p = conj(m);  5: p = conj(m) + beta p
+// (partials [R][nblk][1]).  launch_cg_scalar phases: see gpbicg.cu.
+template <typename T>
+cudaError_t launch_cg_vec(int which, int64_t n, int R, cplx_t<T>* x, cplx_t<T>* r,
+                          cplx_t<T>* p, const cplx_t<T>* w, cplx_t<T>* c, const cplx_t<T>* m,
+                          double* partials, const KState* ks, const int* active,
+                          cudaStream_t st);
+cudaError_t launch_cg_scalar(int phase, int R, int nblk, const double* partials, KState* ks,
+                             int* active, cudaStream_t st);
 // y = A x with the epilogue partials <rhat, y> ([R][nblk][2], nblk =
 // matvec_partial_blocks): a plain input with the XOUT_RV epilogue.
 template <typename T>

@@ -55,7 +55,7 @@ def test_sphere64_matvec_sampled_rows(B):
     _sampled_rows_check(B, W.c2_sphere64(), 48, 1)
 
 
-@pytest.mark.parametrize("solver", ["bicgstab", "qmr", "bicgstab2"])
+@pytest.mark.parametrize("solver", ["bicgstab", "qmr", "bicgstab2", "gpbicg"])
 @pytest.mark.parametrize("precision", ["fp32_refined", "fp64"])
 def test_sphere64_solve_matches_oracle(B, precision, solver):
     w = W.c2_sphere64()

@@ -303,3 +303,95 @@ def test_bicgstab2_batched_and_circular(B):
     assert q["status"] == B.DDA_OK
     assert np.allclose(q["Qext"], b["Qext"], rtol=1e-8)
     t.close()
+
+
+# ---- GPBi-CG (the guide's GPBICG) and normal-equation CG (PETRKP) ------------------
+@pytest.mark.parametrize("solver", ["gpbicg", "petrkp"])
+@pytest.mark.parametrize("method", ["LDR", "FCD"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+def test_gpbicg_petrkp_small_ellipsoid(B, solver, method, precision):
+    w = W.small_ellipsoid(6, 10, 12, m=1.5 + 0.1j, kd=0.4, method=method)
+    ref = _oracle(w)
+    t = B.Target(w.occ, w.comp, w.m, method=method)
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=2, tol=1e-10, precision=precision,
+                  dirs=w.dirs, solver=solver, max_iter=5000)
+    assert out["status"] == B.DDA_OK
+    _check(out, ref)
+    assert np.all(out["resid"] <= 1e-10 * 1.01)
+    fa, fr = out["famp"][0], ref["famp"]
+    assert np.abs(fa - fr).max() < 1e-6 * np.abs(fr).max()
+    t.close()
+
+
+def _linear_system(w):
+    """E and v -> A v (the oracle's direct sum) for the first incidence and
+    polarization, as flat site-major vectors."""
+    flat, pos = O.site_positions(w.occ)
+    e1, _ = O.polarization_pair(w.khat[0], w.e01[0])
+    ainv = O.site_alpha_inverse(w.comp.reshape(-1)[flat], w.m, w.method, w.kd, w.khat[0], e1)
+    E = O.incident_field(pos, w.kd, w.khat[0], e1)
+    mv = lambda v: O.matvec_direct(v.reshape(-1, 3), pos, ainv, w.kd, w.method).reshape(-1)
+    return E, mv
+
+
+def test_gpbicg_first_iteration_is_bicgstab(B):
+    """GPBi-CG's first iteration has eta = 0 by definition, so its iterate is
+    BiCGSTAB's first iterate (the oracle's, from the same zero start and shadow
+    vector); after three iterations eta != 0 and the two differ."""
+    w = W.small_ellipsoid(6, 7, 8, m=1.5 + 0.1j, kd=0.4, method="LDR")
+    E, mv = _linear_system(w)
+    x1, _, _ = O.bicgstab(mv, E.reshape(-1), tol=0.0, maxiter=1)
+    x3, _, _ = O.bicgstab(mv, E.reshape(-1), tol=0.0, maxiter=3)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    g1 = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=1, tol=1e-14, max_iter=1,
+                 precision="fp64", solver="gpbicg")
+    assert g1["status"] == B.DDA_ERR_NOCONV and g1["iters"][0] == 1
+    assert np.abs(g1["P"][0].reshape(-1) - x1).max() <= 1e-10 * np.abs(x1).max()
+    g3 = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=1, tol=1e-14, max_iter=3,
+                 precision="fp64", solver="gpbicg")
+    assert np.abs(g3["P"][0].reshape(-1) - x3).max() > 1e-8 * np.abs(x3).max()
+    t.close()
+
+
+def test_petrkp_first_iterate_and_monotone_residual(B):
+    """Normal-equation CG: the first iterate is alpha A^H E with
+    alpha = ||A^H E||^2 / ||A A^H E||^2 (A^H v = conj(A conj v)), and the true
+    residual never grows from one iteration to the next (CG on A^H A minimises
+    ||E - A P|| over a growing Krylov space)."""
+    w = W.small_ellipsoid(6, 7, 8, m=1.5 + 0.1j, kd=0.4, method="LDR")
+    E, mv = _linear_system(w)
+    b = E.reshape(-1)
+    z = np.conj(mv(np.conj(b)))
+    az = mv(z)
+    x1 = (np.vdot(z, z).real / np.vdot(az, az).real) * z
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    res = []
+    for k in (1, 2, 3, 5, 8, 13):
+        o = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=1, tol=1e-14, max_iter=k,
+                    precision="fp64", solver="petrkp")
+        assert o["iters"][0] == k
+        if k == 1:
+            assert np.abs(o["P"][0].reshape(-1) - x1).max() <= 1e-10 * np.abs(x1).max()
+        res.append(o["resid"][0])
+    assert all(b2 <= b1 * (1 + 1e-12) for b1, b2 in zip(res, res[1:])), res
+    t.close()
+
+
+def test_gpbicg_batched_circular_and_fallback(B):
+    """Four orientations x two polarizations in one batch; circular
+    polarization (E . E = 0 breaks QMR, not GPBi-CG) agrees with BiCGSTAB."""
+    w = W.small_ellipsoid(8, 6, 7, m=1.7 + 0.1j, kd=0.5, method="FCD", n_orient=4, seed=9)
+    t = B.Target(w.occ, w.comp, w.m, method="FCD")
+    out = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, tol=1e-10, precision="fp32_refined",
+                  dirs=w.dirs, solver="gpbicg")
+    for i in range(4):
+        _check(out, _oracle(w, i), r0=2 * i)
+    x, y = np.array([1.0, 0, 0]), np.array([0, 1.0, 0])
+    e = np.array([0, 1, 1j]) / np.sqrt(2)
+    for solver in ("gpbicg", "petrkp"):
+        q = t.solve(w.kd, x, e, yhat=y, tol=1e-10, precision="fp64", solver=solver,
+                    max_iter=5000)
+        b = t.solve(w.kd, x, e, yhat=y, tol=1e-10, precision="fp64")
+        assert q["status"] == B.DDA_OK
+        assert np.allclose(q["Qext"], b["Qext"], rtol=1e-8)
+    t.close()
