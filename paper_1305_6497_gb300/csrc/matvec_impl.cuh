@@ -444,6 +444,220 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
 }
 
 // --------------------------------------------------------------------------
+// z pass for the two-stage lengths Lz = R0 R1 (radix plans 16 x 8 and 16 x 4:
+// Lz = 128 and 64), with every size known at compile time.  It runs the same
+// stages, twiddles, multiply and operations in the same order as k_fft_z_mul
+// (the product is bit-identical); the shared-memory pitch, strides, loop
+// bounds and the frequency at each digit-reversed position (kz = blk + R0 i
+// at position blk R1 + i) become constants, which takes the index arithmetic
+// out of the issue-bound loop and leaves a smaller kernel (one plan, no radix
+// dispatch) for the instruction cache.
+// --------------------------------------------------------------------------
+template <int TILE> constexpr int zc_pitch() { return 3 * TILE + (TILE * 8 < 128 ? 1 : 0); }
+
+template <int TILE, bool GS, int R0, int R1>
+__global__ void __launch_bounds__(256, 3)
+k_fft_z_mul_c(OpView<float> op, float2* __restrict__ buf, const int* __restrict__ active) {
+  using C = float2;
+  constexpr int L = R0 * R1, S = R1, NL = 3 * TILE, PS = zc_pitch<TILE>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const int r = blockIdx.z;
+  if (active && !active[r]) return;
+  const int Lx = op.Lx, Ly = op.Ly, nz = op.nz;
+  const int pyy = blockIdx.y;
+  const int ky = op.ky_at[pyy];
+  const bool fy = ky > (Ly >> 1);
+  const int hy = fy ? Ly - ky : ky;
+  const int col0 = blockIdx.x * TILE;
+  const int ncol = min(TILE, Lx - col0);
+  const int64_t plane_sz = (int64_t)Ly * Lx;
+  const int64_t comp_sz = (int64_t)nz * plane_sz;
+  C* base = buf + (int64_t)r * 3 * comp_sz + (int64_t)pyy * Lx + col0;
+  C* gs = reinterpret_cast<C*>(smem_raw + (((size_t)L * PS * sizeof(C) + 15) & ~(size_t)15));
+  if (GS) ghat_tile_async<float, TILE>(op, gs, col0, ncol, hy);
+  const C* __restrict__ tw = op.twz;
+  const bool half = 2 * nz <= L;
+  const int64_t sstride = (int64_t)S * plane_sz;  // global distance of one butterfly input
+  // first forward stage (radix R0, span S), read straight from global memory
+  for (int b = threadIdx.x; b < NL * S; b += blockDim.x) {
+    const int line = b % NL, j = b / NL;
+    const int c = line / TILE, t = line - c * TILE;
+    const C* src = base + c * comp_sz + (int64_t)j * plane_sz + t;
+    const bool ok = t < ncol;
+    C v[R0];
+    if (half) {
+#pragma unroll
+      for (int i = 0; i < R0 / 2; ++i)
+        v[i] = (ok && j + i * S < nz) ? src[i * sstride] : make_float2(0.f, 0.f);
+      dft_half<R0, false, true, false>(v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < R0; ++i)
+        v[i] = (ok && j + i * S < nz) ? src[i * sstride] : make_float2(0.f, 0.f);
+      dft<R0, false>(v);
+    }
+    if (j > 0) {
+#pragma unroll
+      for (int m = 1; m < R0; ++m) v[m] = cmul(v[m], ldc(&tw[j * (R0 - 1) + (m - 1)]));
+    }
+#pragma unroll
+    for (int m = 0; m < R0; ++m) s[(j + m * S) * PS + line] = v[m];
+  }
+  if (GS) cp_async_wait_all();
+  __syncthreads();
+  // last forward stage + multiply + first inverse stage (radix R1, span 1):
+  // a thread owns R1 consecutive positions of one column, all three components
+  {
+    const int kxh = Lx >> 1;
+    for (int b = threadIdx.x; b < TILE * R0; b += blockDim.x) {
+      const int t = b % TILE, blk = b / TILE;
+      C* q = s + blk * R1 * PS + t;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        C v[R1];
+#pragma unroll
+        for (int i = 0; i < R1; ++i) v[i] = q[i * PS + c * TILE];
+        dft<R1, false>(v);
+#pragma unroll
+        for (int i = 0; i < R1; ++i) q[i * PS + c * TILE] = v[i];
+      }
+      if (t < ncol) {
+        const int kx = op.kx_at[col0 + t];
+        const bool fx = kx > kxh;
+#pragma unroll
+        for (int i = 0; i < R1; ++i) {
+          const int kz = blk + R0 * i;
+          const bool fz = kz > L / 2;
+          const int hz = fz ? L - kz : kz;
+          C g[6];
+          if (GS) {
+            G6<float>::load_smem(gs + 6 * (hz * TILE + t), g);
+          } else {
+            const int hx = fx ? Lx - kx : kx;
+            G6<float>::load(op.ghat + 6 * (((int64_t)hz * op.Hy + hy) * op.Hx + hx), g);
+          }
+          spectral_mul<float, false>(g, fx, fy, fz, q + i * PS, TILE);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        C v[R1];
+#pragma unroll
+        for (int i = 0; i < R1; ++i) v[i] = q[i * PS + c * TILE];
+        dft<R1, true>(v);
+#pragma unroll
+        for (int i = 0; i < R1; ++i) q[i * PS + c * TILE] = v[i];
+      }
+    }
+  }
+  __syncthreads();
+  // last inverse stage (radix R0), written straight to global memory
+  for (int b = threadIdx.x; b < NL * S; b += blockDim.x) {
+    const int line = b % NL, j = b / NL;
+    const int c = line / TILE, t = line - c * TILE;
+    C* dst = base + c * comp_sz + (int64_t)j * plane_sz + t;
+    const bool ok = t < ncol;
+    C v[R0];
+#pragma unroll
+    for (int m = 0; m < R0; ++m) v[m] = s[(j + m * S) * PS + line];
+    if (j > 0) {
+#pragma unroll
+      for (int m = 1; m < R0; ++m) v[m] = cmulc(ldc(&tw[j * (R0 - 1) + (m - 1)]), v[m]);
+    }
+    if (half) {
+      dft_half<R0, true, false, true>(v);
+#pragma unroll
+      for (int i = 0; i < R0 / 2; ++i)
+        if (ok && j + i * S < nz) dst[i * sstride] = v[i];
+    } else {
+      dft<R0, true>(v);
+#pragma unroll
+      for (int i = 0; i < R0; ++i)
+        if (ok && j + i * S < nz) dst[i * sstride] = v[i];
+    }
+  }
+}
+
+// The compile-time z kernel applies (FP32, no cross product, a 16 x 8 or
+// 16 x 4 plan).
+template <typename T, bool CROSS>
+static bool zc_applies(const OpView<T>& op) {
+  return std::is_same<T, float>::value && !CROSS && op.pz.nstage == 2 && op.pz.radix[0] == 16 &&
+         (op.pz.radix[1] == 8 || op.pz.radix[1] == 4);
+}
+
+template <int TILE, bool GS>
+static size_t zc_smem(const OpView<float>& op) {
+  const size_t d = ((size_t)op.Lz * zc_pitch<TILE>() * sizeof(float2) + 15) & ~(size_t)15;
+  return d + (GS ? (size_t)6 * op.Hz * TILE * sizeof(float2) : 0);
+}
+
+// One z pass (forward z, multiply, inverse z) with the schedule's tile.
+template <typename T, bool CROSS>
+static void launch_z_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
+                          cplx_t<T>* scratch, const int* active, cudaStream_t st) {
+  if constexpr (std::is_same<T, df64>::value) {
+    // double-float passes use one z variant (4 columns, Ghat from global
+    // memory): the arithmetic is ~10x the FP32 code, so fewer instantiations
+    // keep the build short
+    dim3 gz((op.Lx + 3) / 4, op.Ly, R);
+    k_fft_z_mul<T, 4, false, CROSS><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps,
+                                                                      active);
+  } else {
+    dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
+    if constexpr (std::is_same<T, float>::value && !CROSS) {
+      if (zc_applies<T, CROSS>(op)) {
+#define DDA_ZC(TT, GG)                                                                        \
+  {                                                                                           \
+    if (op.pz.radix[1] == 8)                                                                  \
+      k_fft_z_mul_c<TT, GG, 16, 8><<<gz, L.z_threads, zc_smem<TT, GG>(op), st>>>(op, scratch, \
+                                                                                  active);    \
+    else                                                                                      \
+      k_fft_z_mul_c<TT, GG, 16, 4><<<gz, L.z_threads, zc_smem<TT, GG>(op), st>>>(op, scratch, \
+                                                                                  active);    \
+  }
+        if (L.z_gs) {
+          switch (L.z_tile) {
+            case 16: DDA_ZC(16, true); break;
+            case 8: DDA_ZC(8, true); break;
+            case 4: DDA_ZC(4, true); break;
+            default: DDA_ZC(2, true); break;
+          }
+        } else {
+          switch (L.z_tile) {
+            case 16: DDA_ZC(16, false); break;
+            case 8: DDA_ZC(8, false); break;
+            case 4: DDA_ZC(4, false); break;
+            default: DDA_ZC(2, false); break;
+          }
+        }
+#undef DDA_ZC
+        return;
+      }
+    }
+#define DDA_ZL(TT, GG) \
+  k_fft_z_mul<T, TT, GG, CROSS><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active)
+    if (L.z_gs) {
+      switch (L.z_tile) {
+        case 16: DDA_ZL(16, true); break;
+        case 8: DDA_ZL(8, true); break;
+        case 4: DDA_ZL(4, true); break;
+        default: DDA_ZL(2, true); break;
+      }
+    } else {
+      switch (L.z_tile) {
+        case 16: DDA_ZL(16, false); break;
+        case 8: DDA_ZL(8, false); break;
+        case 4: DDA_ZL(4, false); break;
+        default: DDA_ZL(2, false); break;
+      }
+    }
+#undef DDA_ZL
+  }
+}
+
+// --------------------------------------------------------------------------
 // x pass, inverse + diagonal term: y = ainv * x - conv on occupied sites
 // grid: (row tiles, R)
 // --------------------------------------------------------------------------
@@ -633,6 +847,21 @@ cudaError_t configure_matvec_kernels(const MatvecLaunch& L) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
   }
+  if constexpr (std::is_same<T, float>::value) {
+    const void* zf[] = {
+        (const void*)k_fft_z_mul_c<16, true, 16, 8>, (const void*)k_fft_z_mul_c<8, true, 16, 8>,
+        (const void*)k_fft_z_mul_c<4, true, 16, 8>, (const void*)k_fft_z_mul_c<2, true, 16, 8>,
+        (const void*)k_fft_z_mul_c<16, false, 16, 8>, (const void*)k_fft_z_mul_c<8, false, 16, 8>,
+        (const void*)k_fft_z_mul_c<4, false, 16, 8>, (const void*)k_fft_z_mul_c<2, false, 16, 8>,
+        (const void*)k_fft_z_mul_c<16, true, 16, 4>, (const void*)k_fft_z_mul_c<8, true, 16, 4>,
+        (const void*)k_fft_z_mul_c<4, true, 16, 4>, (const void*)k_fft_z_mul_c<2, true, 16, 4>,
+        (const void*)k_fft_z_mul_c<16, false, 16, 4>, (const void*)k_fft_z_mul_c<8, false, 16, 4>,
+        (const void*)k_fft_z_mul_c<4, false, 16, 4>, (const void*)k_fft_z_mul_c<2, false, 16, 4>};
+    for (const void* k : zf) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return e;
+    }
+  }
   if constexpr (sizeof(T) == 8) {  // magnetic near field (FP64 only)
     const void* zc[] = {(const void*)k_fft_z_mul<T, 16, true, true>,
                         (const void*)k_fft_z_mul<T, 8, true, true>,
@@ -672,36 +901,8 @@ static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int
   k_fft_y<T, false><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, active);
   note_launch();
   if (ev) record(ev[2]);
-  if constexpr (std::is_same<T, df64>::value) {
-    // double-float passes use one z variant (4 columns, Ghat from global
-    // memory): the arithmetic is ~10x the FP32 code, so fewer instantiations
-    // keep the build short
-    dim3 gz((op.Lx + 3) / 4, op.Ly, R);
-    k_fft_z_mul<T, 4, false, CROSS><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps,
-                                                                      active);
-    note_launch();
-  } else {
-    dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
-#define DDA_ZL(TT, GG) \
-  k_fft_z_mul<T, TT, GG, CROSS><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active)
-    if (L.z_gs) {
-      switch (L.z_tile) {
-        case 16: DDA_ZL(16, true); break;
-        case 8: DDA_ZL(8, true); break;
-        case 4: DDA_ZL(4, true); break;
-        default: DDA_ZL(2, true); break;
-      }
-    } else {
-      switch (L.z_tile) {
-        case 16: DDA_ZL(16, false); break;
-        case 8: DDA_ZL(8, false); break;
-        case 4: DDA_ZL(4, false); break;
-        default: DDA_ZL(2, false); break;
-      }
-    }
-#undef DDA_ZL
-    note_launch();
-  }
+  launch_z_pass<T, CROSS>(op, L, R, scratch, active, st);
+  note_launch();
   if (ev) record(ev[3]);
   k_fft_y<T, true><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, active);
   note_launch();

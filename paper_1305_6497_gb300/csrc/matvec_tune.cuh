@@ -52,18 +52,7 @@ static float time_pass(const OpView<T>& op, const MatvecLaunch& L, int pass, int
         break;
       }
       case 1: k_fft_y<T, false><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, nullptr); break;
-      case 2:
-#define DDA_ZT(TT, GG) \
-  k_fft_z_mul<T, TT, GG><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, nullptr)
-        if (L.z_gs) {
-          switch (L.z_tile) { case 16: DDA_ZT(16, true); break; case 8: DDA_ZT(8, true); break;
-                              case 4: DDA_ZT(4, true); break; default: DDA_ZT(2, true); }
-        } else {
-          switch (L.z_tile) { case 16: DDA_ZT(16, false); break; case 8: DDA_ZT(8, false); break;
-                              case 4: DDA_ZT(4, false); break; default: DDA_ZT(2, false); }
-        }
-#undef DDA_ZT
-        break;
+      case 2: launch_z_pass<T, false>(op, L, R, scratch, nullptr, st); break;
       case 3: k_fft_y<T, true><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, nullptr); break;
       default:
         k_fft_x_inv<T, XOUT_RV><<<gx, L.x_threads, L.xinv_smem, st>>>(

@@ -31,17 +31,20 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
 
 @pytest.mark.parametrize("threads", [32, 64, 128, 256])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_every_thread_count_gives_the_same_product(threads, precision):
+@pytest.mark.parametrize("nz", [22, 32, 64])
+def test_every_thread_count_gives_the_same_product(threads, precision, nz):
     """Explicit schedules with every thread count the tuner may pick (and odd
-    line/tile counts) must reproduce the default schedule's product."""
+    line/tile counts) must reproduce the default schedule's product; nz = 32
+    and 64 give the z lengths 64 and 128 of the compile-time FP32 z kernel."""
     from paper_1305_6497_gb300 import binding as B
-    occ, comp = tg.ellipsoid(13, 18, 22)
+    occ, comp = tg.ellipsoid(13, 18, nz)
     flat, pos = O.site_positions(occ)
     x = O.box_to_sites(W.random_polarization(occ, 5)[0], flat)
     t = B.Target(occ, comp, [1.5 + 0.1j], method="LDR")
     kh, e = [1.0, 0, 0], [0, 1.0, 0]
     y0 = t.matvec(0.4, x, kh, e, precision)
-    for xl, yt, zt, gs in ((3, 5, 2, 0), (16, 8, 8, 1), (64, 32, 16, 0)):
+    for xl, yt, zt, gs in ((3, 5, 2, 0), (16, 8, 8, 1), (64, 32, 16, 0), (5, 16, 4, 1),
+                           (8, 16, 16, 1)):
         t.set_schedule(dict(x_lines=xl, y_tile=yt, z_tile=zt, z_pitch=3 * zt + 1,
                             z_stage_ghat=gs, x_threads=threads, y_threads=threads,
                             z_threads=threads), precision)

@@ -57,6 +57,10 @@ CASES = [
     ("slab_24x20x9", lambda: tg.ellipsoid(24, 20, 9, 30, 30, 12), [1.33 + 0.05j]),
     ("sphere16", lambda: tg.sphere(16), [1.33 + 0.01j]),
     ("cyl_13x13x31", lambda: tg.cylinder(31, 13, 3), [1.6 + 0.3j]),
+    # z lengths 64 and 128 (compile-time z kernel), ragged x tiles, nz < Lz/2
+    ("ell_20x24x32", lambda: tg.ellipsoid(20, 24, 32), [1.5 + 0.1j]),
+    ("ell_13x9x64", lambda: tg.ellipsoid(13, 9, 64), [1.33 + 0.05j]),
+    ("ell_11x10x63", lambda: tg.ellipsoid(11, 10, 63), [1.7 + 0.2j]),
 ]
 
 
