@@ -207,6 +207,105 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_y(OpView<T>
   }
 }
 
+// y pass for the two-stage lengths Ly = R0 R1 (radix plans 16 x 8 and 16 x 4)
+// with the tile width, strides and loop bounds known at compile time: the
+// same stages and operations as k_fft_y (bit-identical output).
+template <int TILE, bool INV, int R0, int R1>
+__global__ void __launch_bounds__(256, 3)
+k_fft_y_c(OpView<float> op, float2* __restrict__ buf, const int* __restrict__ active) {
+  using C = float2;
+  constexpr int L = R0 * R1, S = R1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* s = reinterpret_cast<C*>(smem_raw);
+  const int r = blockIdx.z;
+  if (active && !active[r]) return;
+  const int Lx = op.Lx, ny = op.ny;
+  const int col0 = blockIdx.x * TILE;
+  const int ncol = min(TILE, Lx - col0);
+  C* base = buf + ((int64_t)r * 3 * op.nz + blockIdx.y) * (int64_t)L * Lx + col0;
+  const C* __restrict__ tw = op.twy;
+  const bool half = 2 * ny <= L;
+  const int64_t sstride = (int64_t)S * Lx;
+  if (!INV) {
+    // first stage (radix R0, span S) from global memory: ny input rows
+    for (int b = threadIdx.x; b < TILE * S; b += blockDim.x) {
+      const int t = b % TILE, j = b / TILE;
+      const C* src = base + (int64_t)j * Lx + t;
+      const bool ok = t < ncol;
+      C v[R0];
+      if (half) {
+#pragma unroll
+        for (int i = 0; i < R0 / 2; ++i)
+          v[i] = (ok && j + i * S < ny) ? src[i * sstride] : make_float2(0.f, 0.f);
+        dft_half<R0, false, true, false>(v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < R0; ++i)
+          v[i] = (ok && j + i * S < ny) ? src[i * sstride] : make_float2(0.f, 0.f);
+        dft<R0, false>(v);
+      }
+      if (j > 0) {
+#pragma unroll
+        for (int m = 1; m < R0; ++m) v[m] = cmul(v[m], ldc(&tw[j * (R0 - 1) + (m - 1)]));
+      }
+#pragma unroll
+      for (int m = 0; m < R0; ++m) s[(j + m * S) * TILE + t] = v[m];
+    }
+    __syncthreads();
+    // last stage (radix R1, span 1) to global memory: all L rows
+    for (int b = threadIdx.x; b < TILE * R0; b += blockDim.x) {
+      const int t = b % TILE, blk = b / TILE;
+      C v[R1];
+#pragma unroll
+      for (int i = 0; i < R1; ++i) v[i] = s[(blk * R1 + i) * TILE + t];
+      dft<R1, false>(v);
+      if (t < ncol) {
+        C* dst = base + (int64_t)blk * R1 * Lx + t;
+#pragma unroll
+        for (int m = 0; m < R1; ++m) dst[(int64_t)m * Lx] = v[m];
+      }
+    }
+  } else {
+    // first inverse stage (radix R1, span 1) from global memory: all L rows
+    for (int b = threadIdx.x; b < TILE * R0; b += blockDim.x) {
+      const int t = b % TILE, blk = b / TILE;
+      const C* src = base + (int64_t)blk * R1 * Lx + t;
+      const bool ok = t < ncol;
+      C v[R1];
+#pragma unroll
+      for (int m = 0; m < R1; ++m) v[m] = ok ? src[(int64_t)m * Lx] : make_float2(0.f, 0.f);
+      dft<R1, true>(v);
+#pragma unroll
+      for (int i = 0; i < R1; ++i) s[(blk * R1 + i) * TILE + t] = v[i];
+    }
+    __syncthreads();
+    // last inverse stage (radix R0) to global memory: ny output rows
+    for (int b = threadIdx.x; b < TILE * S; b += blockDim.x) {
+      const int t = b % TILE, j = b / TILE;
+      C* dst = base + (int64_t)j * Lx + t;
+      const bool ok = t < ncol;
+      C v[R0];
+#pragma unroll
+      for (int m = 0; m < R0; ++m) v[m] = s[(j + m * S) * TILE + t];
+      if (j > 0) {
+#pragma unroll
+        for (int m = 1; m < R0; ++m) v[m] = cmulc(ldc(&tw[j * (R0 - 1) + (m - 1)]), v[m]);
+      }
+      if (half) {
+        dft_half<R0, true, false, true>(v);
+#pragma unroll
+        for (int i = 0; i < R0 / 2; ++i)
+          if (ok && j + i * S < ny) dst[i * sstride] = v[i];
+      } else {
+        dft<R0, true>(v);
+#pragma unroll
+        for (int i = 0; i < R0; ++i)
+          if (ok && j + i * S < ny) dst[i * sstride] = v[i];
+      }
+    }
+  }
+}
+
 // --------------------------------------------------------------------------
 // z pass: forward FFT along z, multiply by Ghat (3x3 complex symmetric),
 // inverse FFT along z; the three components of a column tile in one CTA.
@@ -579,6 +678,36 @@ k_fft_z_mul_c(OpView<float> op, float2* __restrict__ buf, const int* __restrict_
   }
 }
 
+// One y pass (forward: ny -> Ly rows, inverse: Ly -> ny rows) with the
+// schedule's tile; FP32 with a 16 x 8 or 16 x 4 plan and a tile of 8, 16 or
+// 32 columns runs the compile-time kernel.
+template <typename T, bool INV>
+static void launch_y_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
+                          cplx_t<T>* scratch, const int* active, cudaStream_t st) {
+  dim3 gy((op.Lx + L.y_tile - 1) / L.y_tile, 3 * op.nz, R);
+  if constexpr (std::is_same<T, float>::value) {
+    const AxisPlan& P = op.py;
+    if (P.nstage == 2 && P.radix[0] == 16 && (P.radix[1] == 8 || P.radix[1] == 4) &&
+        (L.y_tile == 8 || L.y_tile == 16 || L.y_tile == 32)) {
+#define DDA_YC(TT)                                                                    \
+  {                                                                                   \
+    if (P.radix[1] == 8)                                                              \
+      k_fft_y_c<TT, INV, 16, 8><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, active); \
+    else                                                                              \
+      k_fft_y_c<TT, INV, 16, 4><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, active); \
+  }
+      switch (L.y_tile) {
+        case 8: DDA_YC(8); break;
+        case 16: DDA_YC(16); break;
+        default: DDA_YC(32); break;
+      }
+#undef DDA_YC
+      return;
+    }
+  }
+  k_fft_y<T, INV><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, active);
+}
+
 // The compile-time z kernel applies (FP32, no cross product, a 16 x 8 or
 // 16 x 4 plan).
 template <typename T, bool CROSS>
@@ -862,6 +991,19 @@ cudaError_t configure_matvec_kernels(const MatvecLaunch& L) {
       if (e != cudaSuccess) return e;
     }
   }
+  if constexpr (std::is_same<T, float>::value) {
+    const void* yf[] = {
+        (const void*)k_fft_y_c<8, false, 16, 8>, (const void*)k_fft_y_c<16, false, 16, 8>,
+        (const void*)k_fft_y_c<32, false, 16, 8>, (const void*)k_fft_y_c<8, true, 16, 8>,
+        (const void*)k_fft_y_c<16, true, 16, 8>, (const void*)k_fft_y_c<32, true, 16, 8>,
+        (const void*)k_fft_y_c<8, false, 16, 4>, (const void*)k_fft_y_c<16, false, 16, 4>,
+        (const void*)k_fft_y_c<32, false, 16, 4>, (const void*)k_fft_y_c<8, true, 16, 4>,
+        (const void*)k_fft_y_c<16, true, 16, 4>, (const void*)k_fft_y_c<32, true, 16, 4>};
+    for (const void* k : yf) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return e;
+    }
+  }
   if constexpr (sizeof(T) == 8) {  // magnetic near field (FP64 only)
     const void* zc[] = {(const void*)k_fft_z_mul<T, 16, true, true>,
                         (const void*)k_fft_z_mul<T, 8, true, true>,
@@ -897,14 +1039,13 @@ static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int
   k_fft_x_fwd<T, XIN><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines, active, xa);
   note_launch();
   if (ev) record(ev[1]);
-  dim3 gy((op.Lx + L.y_tile - 1) / L.y_tile, 3 * op.nz, R);
-  k_fft_y<T, false><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, active);
+  launch_y_pass<T, false>(op, L, R, scratch, active, st);
   note_launch();
   if (ev) record(ev[2]);
   launch_z_pass<T, CROSS>(op, L, R, scratch, active, st);
   note_launch();
   if (ev) record(ev[3]);
-  k_fft_y<T, true><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, active);
+  launch_y_pass<T, true>(op, L, R, scratch, active, st);
   note_launch();
   if (ev) record(ev[4]);
   k_fft_x_inv<T, XOUT><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y, L.x_lines,

@@ -41,8 +41,6 @@ static float time_pass(const OpView<T>& op, const MatvecLaunch& L, int pass, int
                        double* part) {
   const int rows = 3 * op.nz * op.ny;
   dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
-  dim3 gy((op.Lx + L.y_tile - 1) / L.y_tile, 3 * op.nz, R);
-  dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
   auto launch = [&]() {
     switch (pass) {
       case 0: {
@@ -51,9 +49,9 @@ static float time_pass(const OpView<T>& op, const MatvecLaunch& L, int pass, int
                                                                  nullptr, xa);
         break;
       }
-      case 1: k_fft_y<T, false><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, nullptr); break;
+      case 1: launch_y_pass<T, false>(op, L, R, scratch, nullptr, st); break;
       case 2: launch_z_pass<T, false>(op, L, R, scratch, nullptr, st); break;
-      case 3: k_fft_y<T, true><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, nullptr); break;
+      case 3: launch_y_pass<T, true>(op, L, R, scratch, nullptr, st); break;
       default:
         k_fft_x_inv<T, XOUT_RV><<<gx, L.x_threads, L.xinv_smem, st>>>(
             op, scratch, x, y, L.x_lines, nullptr, x, part);
@@ -136,6 +134,8 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
           for (int th : {64, 96, 128, 192, 256}) {
             MatvecLaunch c = best;
             fill_z<T>(op, c, tile, pad, gs != 0);
+            // the compile-time z kernel sets its own pitch: one pad value is enough
+            if (zc_applies<T, false>(op) && pad != 0) continue;
             c.z_threads = th;
             if (c.z_smem > kMax) continue;
             const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);
