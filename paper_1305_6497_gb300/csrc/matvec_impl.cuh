@@ -49,16 +49,21 @@ template <typename T> struct XinArgs {
   cplx_t<T>* x;
 };
 
-template <typename T, int MODE>
+// PLAN: 0 -- any radix plan (read at run time); 1 / 2 -- the 16 x 8 / 16 x 4
+// plan (Lx = 128 / 64) with Lx and the stages known at compile time (FP32).
+template <int PLAN> constexpr int plan_len() { return PLAN == 1 ? 128 : PLAN == 2 ? 64 : 0; }
+
+template <typename T, int MODE, int PLAN = 0>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpView<T> op, const io_t<T>* __restrict__ in,
-                            cplx_t<T>* __restrict__ buf, int nlines,
+                            cplx_t<T>* __restrict__ buf, int nlines, unsigned long long div_nl,
                             const int* __restrict__ active, XinArgs<T> xa) {
   using C = cplx_t<T>;
+  constexpr int LP = plan_len<PLAN>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int r = blockIdx.y;
   if (active && !active[r]) return;
-  const int nx = op.nx, Lx = op.Lx;
+  const int nx = op.nx, Lx = LP ? LP : op.Lx;
   const int rows = 3 * op.nz * op.ny;
   const int row0 = blockIdx.x * nlines;
   const int ps = nlines + 1;
@@ -136,16 +141,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpVie
   const bool half = 2 * nx <= Lx && op.px.radix[0] % 2 == 0;
   const int zend = half ? Lx / 2 : Lx;
   for (int e = threadIdx.x; e < nlines * (zend - nx); e += blockDim.x) {
-    const int line = e % nlines, p = nx + e / nlines;
+    const int q = fast_div(e, div_nl), line = e - q * nlines, p = nx + q;
     s[p * ps + line] = mk<C>(0, 0);
   }
   __syncthreads();
-  fft_smem<C, false>(s, nlines, ps, op.px, op.twx, half);
+  if constexpr (PLAN == 0) fft_smem<C, false>(s, nlines, ps, op.px, op.twx, half);
+  else fft_smem_c<C, false, 16, PLAN == 1 ? 8 : 4>(s, nlines, div_nl, ps, op.twx, half);
   const int64_t plane_sz = (int64_t)op.Ly * Lx;
   C* dst = buf + (int64_t)r * 3 * op.nz * plane_sz;
 #pragma unroll 4
   for (int e = threadIdx.x; e < nlines * Lx; e += blockDim.x) {
-    const int line = fast_div(e, op.div_Lx), p = e - line * Lx;
+    const int line = LP ? e / LP : fast_div(e, op.div_Lx), p = e - line * Lx;
     const int row = row0 + line;
     if (row < rows) {
       const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
@@ -800,17 +806,18 @@ static void launch_z_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
 //                not (the field the dipoles radiate; near-field output)
 enum { XOUT_PLAIN = 0, XOUT_RV = 1, XOUT_TS = 2, XOUT_QT = 3, XOUT_FIELD = 4 };
 
-template <typename T, int MODE>
+template <typename T, int MODE, int PLAN = 0>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpView<T> op, const cplx_t<T>* __restrict__ buf,
                             const io_t<T>* __restrict__ xin, io_t<T>* __restrict__ yout,
-                            int nlines, const int* __restrict__ active,
+                            int nlines, unsigned long long div_nl, const int* __restrict__ active,
                             const io_t<T>* __restrict__ rhat, double* __restrict__ partials) {
   using C = cplx_t<T>;
+  constexpr int LP = plan_len<PLAN>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int r = blockIdx.y;
   if (active && !active[r]) return;
-  const int nx = op.nx, Lx = op.Lx;
+  const int nx = op.nx, Lx = LP ? LP : op.Lx;
   const int rows = 3 * op.nz * op.ny;
   const int row0 = blockIdx.x * nlines;
   const int ps = nlines + 1;
@@ -831,7 +838,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   }
   // all of the tile's loads in flight at once (asynchronous copies)
   for (int e = threadIdx.x; e < nlines * Lx; e += blockDim.x) {
-    const int line = fast_div(e, op.div_Lx), p = e - line * Lx;
+    const int line = LP ? e / LP : fast_div(e, op.div_Lx), p = e - line * Lx;
     const int row = row0 + line;
     if (row < rows) {
       const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
@@ -844,7 +851,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   cp_async_wait_all();
   __syncthreads();
   // only positions < nx <= Lx/2 are used below
-  fft_smem<C, true>(s, nlines, ps, op.px, op.twx, 2 * nx <= Lx);
+  if constexpr (PLAN == 0) fft_smem<C, true>(s, nlines, ps, op.px, op.twx, 2 * nx <= Lx);
+  else fft_smem_c<C, true, 16, PLAN == 1 ? 8 : 4>(s, nlines, div_nl, ps, op.twx, 2 * nx <= Lx);
   const C* ai = op.ainv + (int64_t)r * op.ncomp1;
   IO* yr = yout + g0;
   // (df64 passes only run the plain epilogue; their accumulator type is unused)
@@ -903,6 +911,74 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
     if constexpr (MODE == XOUT_RV || MODE == XOUT_QT) acc.template write<2>(partials);
     else acc.template write<4>(partials);
   }
+}
+
+// Radix plan of the x passes as a compile-time variant (see k_fft_x_fwd).
+template <typename T>
+static int x_plan(const OpView<T>& op) {
+  if constexpr (std::is_same<T, float>::value) {
+    const AxisPlan& P = op.px;
+    if (P.nstage == 2 && P.radix[0] == 16 && P.radix[1] == 8 && op.Lx == 128) return 1;
+    if (P.nstage == 2 && P.radix[0] == 16 && P.radix[1] == 4 && op.Lx == 64) return 2;
+  }
+  return 0;
+}
+
+static inline unsigned long long div_magic(int d) {
+  return ((1ull << 36) + (unsigned long long)d - 1) / (unsigned long long)d;
+}
+
+// One forward x pass (prologue mode XIN) with the schedule's line count.
+template <typename T, int XIN>
+static void launch_x_fwd_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
+                              const io_t<T>* x, cplx_t<T>* scratch, const int* active,
+                              XinArgs<T> xa, cudaStream_t st) {
+  const int rows = 3 * op.nz * op.ny;
+  dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
+  const unsigned long long dv = div_magic(L.x_lines);
+  if constexpr (std::is_same<T, float>::value) {
+    const int pl = x_plan(op);
+    if (pl == 1) {
+      k_fft_x_fwd<T, XIN, 1><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines, dv,
+                                                                active, xa);
+      return;
+    }
+    if (pl == 2) {
+      k_fft_x_fwd<T, XIN, 2><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines, dv,
+                                                                active, xa);
+      return;
+    }
+  }
+  k_fft_x_fwd<T, XIN, 0><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines, dv,
+                                                            active, xa);
+}
+
+// One inverse x pass (epilogue mode XOUT) with the schedule's line count.
+template <typename T, int XOUT>
+static void launch_x_inv_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
+                              const cplx_t<T>* scratch, const io_t<T>* x, io_t<T>* y,
+                              const int* active, const io_t<T>* rhat, double* partials,
+                              cudaStream_t st) {
+  const int rows = 3 * op.nz * op.ny;
+  dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
+  const unsigned long long dv = div_magic(L.x_lines);
+  if constexpr (std::is_same<T, float>::value && XOUT != XOUT_FIELD) {
+    const int pl = x_plan(op);
+    if (pl == 1) {
+      k_fft_x_inv<T, XOUT, 1><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y,
+                                                                    L.x_lines, dv, active,
+                                                                    rhat, partials);
+      return;
+    }
+    if (pl == 2) {
+      k_fft_x_inv<T, XOUT, 2><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y,
+                                                                    L.x_lines, dv, active,
+                                                                    rhat, partials);
+      return;
+    }
+  }
+  k_fft_x_inv<T, XOUT, 0><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y, L.x_lines,
+                                                                dv, active, rhat, partials);
 }
 
 // --------------------------------------------------------------------------
@@ -977,6 +1053,19 @@ cudaError_t configure_matvec_kernels(const MatvecLaunch& L) {
     if (e != cudaSuccess) return e;
   }
   if constexpr (std::is_same<T, float>::value) {
+    const void* xf[] = {
+        (const void*)k_fft_x_fwd<T, XIN_PLAIN, 1>, (const void*)k_fft_x_fwd<T, XIN_P, 1>,
+        (const void*)k_fft_x_fwd<T, XIN_S, 1>, (const void*)k_fft_x_fwd<T, XIN_Q, 1>,
+        (const void*)k_fft_x_inv<T, XOUT_PLAIN, 1>, (const void*)k_fft_x_inv<T, XOUT_RV, 1>,
+        (const void*)k_fft_x_inv<T, XOUT_TS, 1>, (const void*)k_fft_x_inv<T, XOUT_QT, 1>,
+        (const void*)k_fft_x_fwd<T, XIN_PLAIN, 2>, (const void*)k_fft_x_fwd<T, XIN_P, 2>,
+        (const void*)k_fft_x_fwd<T, XIN_S, 2>, (const void*)k_fft_x_fwd<T, XIN_Q, 2>,
+        (const void*)k_fft_x_inv<T, XOUT_PLAIN, 2>, (const void*)k_fft_x_inv<T, XOUT_RV, 2>,
+        (const void*)k_fft_x_inv<T, XOUT_TS, 2>, (const void*)k_fft_x_inv<T, XOUT_QT, 2>};
+    for (const void* k : xf) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return e;
+    }
     const void* zf[] = {
         (const void*)k_fft_z_mul_c<16, true, 16, 8>, (const void*)k_fft_z_mul_c<8, true, 16, 8>,
         (const void*)k_fft_z_mul_c<4, true, 16, 8>, (const void*)k_fft_z_mul_c<2, true, 16, 8>,
@@ -1026,7 +1115,6 @@ static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int
                                  const io_t<T>* x, io_t<T>* y, cplx_t<T>* scratch,
                                  const int* active, cudaStream_t st, const cudaEvent_t* ev,
                                  XinArgs<T> xa, const io_t<T>* rhat, double* partials) {
-  const int rows = 3 * op.nz * op.ny;
   // inside a stream capture the events must be external nodes to be recorded
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (ev) cudaStreamIsCapturing(st, &cap);
@@ -1035,8 +1123,7 @@ static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int
     else cudaEventRecord(e, st);
   };
   if (ev) record(ev[0]);
-  dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
-  k_fft_x_fwd<T, XIN><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines, active, xa);
+  launch_x_fwd_pass<T, XIN>(op, L, R, x, scratch, active, xa, st);
   note_launch();
   if (ev) record(ev[1]);
   launch_y_pass<T, false>(op, L, R, scratch, active, st);
@@ -1048,8 +1135,7 @@ static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int
   launch_y_pass<T, true>(op, L, R, scratch, active, st);
   note_launch();
   if (ev) record(ev[4]);
-  k_fft_x_inv<T, XOUT><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y, L.x_lines,
-                                                             active, rhat, partials);
+  launch_x_inv_pass<T, XOUT>(op, L, R, scratch, x, y, active, rhat, partials, st);
   note_launch();
   if (ev) record(ev[5]);
   return cudaGetLastError();
@@ -1127,10 +1213,7 @@ cudaError_t launch_matvec_q(const OpView<T>& op, const MatvecLaunch& L, int R,
 template <typename T>
 cudaError_t launch_x_fwd(const OpView<T>& op, const MatvecLaunch& L, int R,
                          const cplx_t<T>* x, cplx_t<T>* out, cudaStream_t st) {
-  const int rows = 3 * op.nz * op.ny;
-  dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
-  k_fft_x_fwd<T, XIN_PLAIN><<<gx, L.x_threads, L.x_smem, st>>>(op, x, out, L.x_lines, nullptr,
-                                                               XinArgs<T>{});
+  launch_x_fwd_pass<T, XIN_PLAIN>(op, L, R, x, out, nullptr, XinArgs<T>{}, st);
   note_launch();
   return cudaGetLastError();
 }

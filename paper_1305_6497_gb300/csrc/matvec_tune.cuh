@@ -39,22 +39,18 @@ static float time_pass(const OpView<T>& op, const MatvecLaunch& L, int pass, int
                        const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch, cudaStream_t st,
                        cudaEvent_t e0, cudaEvent_t e1, int reps, const KState* ks,
                        double* part) {
-  const int rows = 3 * op.nz * op.ny;
-  dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
   auto launch = [&]() {
     switch (pass) {
       case 0: {
         XinArgs<T> xa{x, y, x, ks, nullptr, nullptr};  // s <- x - alpha x, into y
-        k_fft_x_fwd<T, XIN_S><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines,
-                                                                 nullptr, xa);
+        launch_x_fwd_pass<T, XIN_S>(op, L, R, x, scratch, nullptr, xa, st);
         break;
       }
       case 1: launch_y_pass<T, false>(op, L, R, scratch, nullptr, st); break;
       case 2: launch_z_pass<T, false>(op, L, R, scratch, nullptr, st); break;
       case 3: launch_y_pass<T, true>(op, L, R, scratch, nullptr, st); break;
       default:
-        k_fft_x_inv<T, XOUT_RV><<<gx, L.x_threads, L.xinv_smem, st>>>(
-            op, scratch, x, y, L.x_lines, nullptr, x, part);
+        launch_x_inv_pass<T, XOUT_RV>(op, L, R, scratch, x, y, nullptr, x, part, st);
     }
   };
   launch();  // warm-up

@@ -61,6 +61,10 @@ CASES = [
     ("ell_20x24x32", lambda: tg.ellipsoid(20, 24, 32), [1.5 + 0.1j]),
     ("ell_13x9x64", lambda: tg.ellipsoid(13, 9, 64), [1.33 + 0.05j]),
     ("ell_11x10x63", lambda: tg.ellipsoid(11, 10, 63), [1.7 + 0.2j]),
+    # x lengths 64 and 128 (compile-time x kernels), ragged row tiles, nx < Lx/2
+    ("ell_32x7x5", lambda: tg.ellipsoid(32, 7, 5), [1.5 + 0.1j]),
+    ("ell_64x6x5", lambda: tg.ellipsoid(64, 6, 5), [1.33 + 0.05j]),
+    ("ell_63x5x6", lambda: tg.ellipsoid(63, 5, 6), [1.7 + 0.2j]),
 ]
 
 
