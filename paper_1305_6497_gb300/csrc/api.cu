@@ -174,12 +174,13 @@ struct Workspace {
   DevBuf x32, r32, rh32, p32, v32, s32, t32, scr32, b32;
   DevBuf partials, ks, active, active_outer, norms, sums;
   DevBuf pol, ph, ainv64, ainv32, ainvdf, wabs, fph, sitebuf;
-  DevBuf extra64, extra32;  // BiCGstab(2)'s third residual (allocated on first use)
+  DevBuf extra64, extra32;  // extra Krylov vectors of BiCGstab(2), GPBi-CG (on first use)
+  DevBuf fold;              // per-RHS block counters of the passes that end a scalar step
   void release_all() {
     for (DevBuf* b : {&b64, &x64, &r64, &rh64, &p64, &v64, &s64, &t64, &scr64, &x32, &r32,
                       &rh32, &p32, &v32, &s32, &t32, &scr32, &b32, &partials, &ks, &active,
                       &active_outer, &norms, &sums, &pol, &ph, &ainv64, &ainv32, &ainvdf, &wabs, &fph,
-                      &extra64, &extra32,
+                      &extra64, &extra32, &fold,
                       &sitebuf})
       b->release();
   }
@@ -478,6 +479,12 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
     CK(launch_bicg_init<T>(n, R, V.b, nullptr, V.r, V.rh, V.p, V.v, part, st));
   }
   CK(launch_state_init(R, nblk, part, ks, act, tol, max_iter, st));
+  // the scalar steps alpha, omega, rho run in the last block of the pass that
+  // produces their sums (block counters start at zero and are re-armed there)
+  w.fold.ensure(sizeof(unsigned) * R);
+  unsigned* cnt = w.fold.as<unsigned>();
+  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * R, st));
+  FoldArgs fa{ks, act, cnt, FOLD_ALPHA}, fo{ks, act, cnt, FOLD_OMEGA}, fr{ks, act, cnt, FOLD_RHO};
   std::vector<int> hact(R);
   CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -491,15 +498,12 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
     for (int q = 0; q < nq; ++q) {
       // p <- r + beta (p - omega v); v = A p; <rhat, v>
       CK(launch_matvec_p<T>(op, L, R, V.r, V.p, V.v, V.rh, V.scr, ks, part, act, st,
-                            t->prof.iter_set(q, 0)));
-      CK(launch_scalar_alpha(R, nblk_mv, part, ks, act, st));
+                            t->prof.iter_set(q, 0), fa));
       // s <- r - alpha v; t = A s; <t, s>, <t, t>
       CK(launch_matvec_s<T>(op, L, R, V.r, V.v, V.s, V.t, V.scr, ks, part, act, st,
-                            t->prof.iter_set(q, 1)));
-      CK(launch_scalar_omega(R, nblk_mv, part, ks, act, st));
+                            t->prof.iter_set(q, 1), fo));
       // x += alpha p + omega s; r = s - omega t; <rhat, r>, <r, r>
-      CK(launch_update_xr<T>(n, R, V.x, V.r, V.p, V.s, V.t, V.rh, part, ks, act, st));
-      CK(launch_scalar_rho(R, nblk, part, ks, act, st));
+      CK(launch_update_xr<T>(n, R, V.x, V.r, V.p, V.s, V.t, V.rh, part, ks, act, st, fr));
     }
   };
   // A full block is captured once into a CUDA graph and replayed; the graph is
@@ -510,7 +514,7 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
                                 (uintptr_t)V.x, (uintptr_t)V.scr, (uintptr_t)ks,
                                 (uintptr_t)part, (uintptr_t)act, (uintptr_t)op.ghat,
                                 (uintptr_t)op.ainv, (uintptr_t)nblk_mv, (uintptr_t)nblk,
-                                (uintptr_t)t->schedule_gen};
+                                (uintptr_t)cnt, (uintptr_t)t->schedule_gen};
   IterGraph& g = t->graphs[sizeof(T) == 4 ? 0 : 1];
   if (g.exec && g.sig != sig) g.reset();
   if (!g.exec) {
@@ -598,15 +602,19 @@ static void qmr(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R
   for (int a : hact) nact += a;
   int iter = 0;
   const int nblk_mv = matvec_partial_blocks<T>(op, L);
+  // sigma/alpha and the rotation step run in the last block of the pass that
+  // produces their sums
+  w.fold.ensure(sizeof(unsigned) * R);
+  unsigned* cnt = w.fold.as<unsigned>();
+  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * R, st));
+  const FoldArgs fs{ks, act, cnt, FOLD_QSIGMA}, fq{ks, act, cnt, FOLD_QMR};
   auto enqueue_block = [&](int nq) {
     for (int k = 0; k < nq; ++k) {
-      // pending d/x update, q <- r + beta q; t = A q; q^T t
+      // pending d/x update, q <- r + beta q; t = A q; q^T t; alpha
       CK(launch_matvec_q<T>(op, L, R, V.r, q, d, V.x, V.t, V.scr, ks, part, act, st,
-                            t->prof.iter_set(k, 0)));
-      CK(launch_qmr_sigma(R, nblk_mv, part, ks, act, st));
+                            t->prof.iter_set(k, 0), fs));
       // r -= alpha t; ||r||^2, r^T r; rotation and the next pending update
-      CK(launch_qmr_update_r<T>(n, R, V.r, V.t, part, ks, act, st));
-      CK(launch_qmr_scalar(R, nblk, part, ks, act, st));
+      CK(launch_qmr_update_r<T>(n, R, V.r, V.t, part, ks, act, st, fq));
     }
   };
   std::vector<uintptr_t> sig = {(uintptr_t)1000 + sizeof(T), (uintptr_t)R, (uintptr_t)t->prof.on,
@@ -614,7 +622,7 @@ static void qmr(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R
                                 (uintptr_t)V.x, (uintptr_t)V.scr, (uintptr_t)ks,
                                 (uintptr_t)part, (uintptr_t)act, (uintptr_t)op.ghat,
                                 (uintptr_t)op.ainv, (uintptr_t)nblk_mv, (uintptr_t)nblk,
-                                (uintptr_t)t->schedule_gen};
+                                (uintptr_t)cnt, (uintptr_t)t->schedule_gen};
   IterGraph& g = t->graphs[sizeof(T) == 4 ? 0 : 1];
   if (g.exec && g.sig != sig) g.reset();
   if (!g.exec) {

@@ -90,6 +90,18 @@ struct KState {
 
 enum { KS_RUN = 0, KS_CONV = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3 };
 
+// A vector pass that finishes one of the Krylov scalar steps in its last
+// block (instead of a separate one-block kernel): `counter` holds one word per
+// RHS, zero between passes, counting the blocks that have written partials.
+enum { FOLD_NONE = 0, FOLD_ALPHA = 1, FOLD_OMEGA = 2, FOLD_RHO = 3, FOLD_QSIGMA = 4,
+       FOLD_QMR = 5 };
+struct FoldArgs {
+  KState* ks = nullptr;
+  int* active = nullptr;
+  unsigned* counter = nullptr;
+  int step = FOLD_NONE;
+};
+
 // Matvecs fused with BiCGSTAB steps (same five passes as launch_matvec):
 //  launch_matvec_p: p <- r + beta (p - omega v); v = A p; partials of <rhat, v>
 //                   ([R][nblk][2])
@@ -102,13 +114,13 @@ cudaError_t launch_matvec_p(const OpView<T>& op, const MatvecLaunch& L, int R,
                             const cplx_t<T>* r, cplx_t<T>* p, cplx_t<T>* v,
                             const cplx_t<T>* rhat, cplx_t<T>* scratch, const KState* ks,
                             double* partials, const int* active, cudaStream_t st,
-                            const cudaEvent_t* ev = nullptr);
+                            const cudaEvent_t* ev = nullptr, FoldArgs fold = FoldArgs());
 template <typename T>
 cudaError_t launch_matvec_s(const OpView<T>& op, const MatvecLaunch& L, int R,
                             const cplx_t<T>* r, const cplx_t<T>* v, cplx_t<T>* s_vec,
                             cplx_t<T>* t_vec, cplx_t<T>* scratch, const KState* ks,
                             double* partials, const int* active, cudaStream_t st,
-                            const cudaEvent_t* ev = nullptr);
+                            const cudaEvent_t* ev = nullptr, FoldArgs fold = FoldArgs());
 
 // QMR for complex-symmetric A (one matvec per iteration):
 //  launch_matvec_q: the pending d/x update, q <- r + beta q; t = A q; partials
@@ -118,7 +130,7 @@ cudaError_t launch_matvec_q(const OpView<T>& op, const MatvecLaunch& L, int R,
                             const cplx_t<T>* r, cplx_t<T>* q, cplx_t<T>* d, cplx_t<T>* x,
                             cplx_t<T>* t_vec, cplx_t<T>* scratch, const KState* ks,
                             double* partials, const int* active, cudaStream_t st,
-                            const cudaEvent_t* ev = nullptr);
+                            const cudaEvent_t* ev = nullptr, FoldArgs fold = FoldArgs());
 
 struct RhsTables {            // per-RHS incident-wave data (device)
   const double2* pol;         // [R][3] polarization vector
@@ -163,7 +175,7 @@ template <typename T>
 cudaError_t launch_update_xr(int64_t n, int R, cplx_t<T>* x, cplx_t<T>* r,
                              const cplx_t<T>* p, const cplx_t<T>* s, const cplx_t<T>* t,
                              const cplx_t<T>* rhat, double* partials, const KState* ks,
-                             const int* active, cudaStream_t st);
+                             const int* active, cudaStream_t st, FoldArgs fold = FoldArgs());
 cudaError_t launch_scalar_rho(int R, int nblk, const double* partials, KState* ks,
                               int* active, cudaStream_t st);
 
@@ -189,7 +201,7 @@ cudaError_t launch_qmr_sigma(int R, int nblk, const double* partials, KState* ks
 template <typename T>
 cudaError_t launch_qmr_update_r(int64_t n, int R, cplx_t<T>* r, const cplx_t<T>* t,
                                 double* partials, const KState* ks, const int* active,
-                                cudaStream_t st);
+                                cudaStream_t st, FoldArgs fold = FoldArgs());
 cudaError_t launch_qmr_scalar(int R, int nblk, const double* partials, KState* ks,
                               int* active, cudaStream_t st);
 template <typename T>

@@ -9,6 +9,7 @@
 // partial per value, and a single block per RHS adds the partials in a fixed
 // tree order inside the scalar kernels, so repeated runs are bit-identical.
 #include "dda_ops.h"
+#include "krylov_scalar.cuh"
 #include "reduce.cuh"
 
 namespace dda {
@@ -188,16 +189,7 @@ __global__ void k_scalar_alpha(int nblk, const double* partials, KState* ks, int
   if (!active[r]) return;
   double tot[2];
   sum_partials<2>(partials, nblk, r, tot);
-  if (threadIdx.x == 0) {
-    const double2 rv = make_double2(tot[0], tot[1]);
-    KState& k = ks[r];
-    if (!(rv.x != 0.0 || rv.y != 0.0) || !finite2(rv)) {
-      k.status = KS_BREAKDOWN;
-      active[r] = 0;
-      return;
-    }
-    k.alpha = cdiv(k.rho, rv);
-  }
+  if (threadIdx.x == 0) step_alpha(tot, ks[r], active + r);
 }
 
 cudaError_t launch_scalar_alpha(int R, int nblk, const double* partials, KState* ks,
@@ -262,12 +254,7 @@ __global__ void k_scalar_omega(int nblk, const double* partials, KState* ks, int
   if (!active[r]) return;
   double tot[4];
   sum_partials<4>(partials, nblk, r, tot);
-  if (threadIdx.x == 0) {
-    KState& k = ks[r];
-    const double tt = tot[2];
-    if (tt > 0.0 && isfinite(tt)) k.omega = make_double2(tot[0] / tt, tot[1] / tt);
-    else k.omega = make_double2(0.0, 0.0);
-  }
+  if (threadIdx.x == 0) step_omega(tot, ks[r]);
 }
 
 cudaError_t launch_scalar_omega(int R, int nblk, const double* partials, KState* ks,
@@ -282,7 +269,7 @@ __global__ void k_update_xr(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __r
                             const cplx_t<T>* __restrict__ p, const cplx_t<T>* __restrict__ s,
                             const cplx_t<T>* __restrict__ t, const cplx_t<T>* __restrict__ rhat,
                             double* partials, const KState* __restrict__ ks,
-                            const int* __restrict__ active) {
+                            const int* __restrict__ active, FoldArgs fold) {
   using C = cplx_t<T>;
   const int rr = blockIdx.y;
   if (!active[rr]) return;
@@ -320,15 +307,16 @@ __global__ void k_update_xr(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __r
     }
   }
   acc.template write<4>(partials);
+  if (fold.counter) fold_scalar_step<4>(partials, fold);
 }
 
 template <typename T>
 cudaError_t launch_update_xr(int64_t n, int R, cplx_t<T>* x, cplx_t<T>* r,
                              const cplx_t<T>* p, const cplx_t<T>* s, const cplx_t<T>* t,
                              const cplx_t<T>* rhat, double* partials, const KState* ks,
-                             const int* active, cudaStream_t st) {
+                             const int* active, cudaStream_t st, FoldArgs fold) {
   dim3 g(reduce_blocks(n), R);
-  k_update_xr<T><<<g, kThreads, 0, st>>>(n, x, r, p, s, t, rhat, partials, ks, active);
+  k_update_xr<T><<<g, kThreads, 0, st>>>(n, x, r, p, s, t, rhat, partials, ks, active, fold);
   note_launch();
   return cudaGetLastError();
 }
@@ -338,26 +326,7 @@ __global__ void k_scalar_rho(int nblk, const double* partials, KState* ks, int* 
   if (!active[r]) return;
   double tot[4];
   sum_partials<4>(partials, nblk, r, tot);
-  if (threadIdx.x == 0) {
-    KState& k = ks[r];
-    const double2 rho_new = make_double2(tot[0], tot[1]);
-    k.rnorm2 = tot[2];
-    k.iters += 1;
-    if (k.rnorm2 <= k.tol2 * k.bnorm2) {
-      k.status = KS_CONV; active[r] = 0; return;
-    }
-    if (!isfinite(k.rnorm2) || !finite2(rho_new) ||
-        (rho_new.x == 0.0 && rho_new.y == 0.0) ||
-        (k.omega.x == 0.0 && k.omega.y == 0.0)) {
-      k.status = KS_BREAKDOWN; active[r] = 0; return;
-    }
-    if (k.iters >= k.max_iter) {
-      k.status = KS_NOCONV; active[r] = 0; return;
-    }
-    k.beta = cmul(cdiv(rho_new, k.rho), cdiv(k.alpha, k.omega));
-    k.rho_old = k.rho;
-    k.rho = rho_new;
-  }
+  if (threadIdx.x == 0) step_rho(tot, ks[r], active + r);
 }
 
 cudaError_t launch_scalar_rho(int R, int nblk, const double* partials, KState* ks,
@@ -462,19 +431,7 @@ __global__ void k_qmr_sigma(int nblk, const double* partials, KState* ks, int* a
   if (!active[r]) return;
   double tot[2];
   sum_partials<2>(partials, nblk, r, tot);
-  if (threadIdx.x == 0) {
-    const double2 sigma = make_double2(tot[0], tot[1]);
-    KState& k = ks[r];
-    if (!(sigma.x != 0.0 || sigma.y != 0.0) || !finite2(sigma)) {
-      // this iteration's first pass already applied the pending update
-      k.qa1 = make_double2(0.0, 0.0);
-      k.qa2 = make_double2(0.0, 0.0);
-      k.status = KS_BREAKDOWN;
-      active[r] = 0;
-      return;
-    }
-    k.alpha = cdiv(k.rho, sigma);
-  }
+  if (threadIdx.x == 0) step_qmr_sigma(tot, ks[r], active + r);
 }
 
 cudaError_t launch_qmr_sigma(int R, int nblk, const double* partials, KState* ks,
@@ -487,7 +444,8 @@ cudaError_t launch_qmr_sigma(int R, int nblk, const double* partials, KState* ks
 template <typename T>
 __global__ void k_qmr_update_r(int64_t n, cplx_t<T>* __restrict__ r,
                                const cplx_t<T>* __restrict__ t, double* partials,
-                               const KState* __restrict__ ks, const int* __restrict__ active) {
+                               const KState* __restrict__ ks, const int* __restrict__ active,
+                               FoldArgs fold) {
   using C = cplx_t<T>;
   const int rr = blockIdx.y;
   if (!active[rr]) return;
@@ -519,14 +477,15 @@ __global__ void k_qmr_update_r(int64_t n, cplx_t<T>* __restrict__ r,
     }
   }
   acc.template write<4>(partials);
+  if (fold.counter) fold_scalar_step<4>(partials, fold);
 }
 
 template <typename T>
 cudaError_t launch_qmr_update_r(int64_t n, int R, cplx_t<T>* r, const cplx_t<T>* t,
                                 double* partials, const KState* ks, const int* active,
-                                cudaStream_t st) {
+                                cudaStream_t st, FoldArgs fold) {
   dim3 g(reduce_blocks(n), R);
-  k_qmr_update_r<T><<<g, kThreads, 0, st>>>(n, r, t, partials, ks, active);
+  k_qmr_update_r<T><<<g, kThreads, 0, st>>>(n, r, t, partials, ks, active, fold);
   note_launch();
   return cudaGetLastError();
 }
@@ -536,37 +495,7 @@ __global__ void k_qmr_scalar(int nblk, const double* partials, KState* ks, int* 
   if (!active[r]) return;
   double tot[4];
   sum_partials<4>(partials, nblk, r, tot);
-  if (threadIdx.x == 0) {
-    KState& k = ks[r];
-    const double rn2 = tot[0];
-    const double2 rho_new = make_double2(tot[1], tot[2]);
-    const double th = sqrt(rn2) / k.tau;
-    const double c2 = 1.0 / (1.0 + th * th);
-    const double tau = k.tau * th * sqrt(c2);
-    k.qa1 = make_double2(c2 * k.theta * k.theta, 0.0);
-    k.qa2 = make_double2(c2 * k.alpha.x, c2 * k.alpha.y);
-    k.theta = th;
-    k.tau = tau;
-    k.rnorm2 = rn2;
-    k.iters += 1;
-    if (!isfinite(rn2) || !isfinite(tau)) {
-      k.qa1 = make_double2(0.0, 0.0);
-      k.qa2 = make_double2(0.0, 0.0);
-      k.status = KS_BREAKDOWN; active[r] = 0; return;
-    }
-    if (tau * tau * (k.iters + 1) <= k.tol2 * k.bnorm2) {
-      k.status = KS_CONV; active[r] = 0; return;
-    }
-    if (!finite2(rho_new) || hypot(rho_new.x, rho_new.y) <= k.rho_floor * rn2) {
-      k.status = KS_BREAKDOWN; active[r] = 0; return;
-    }
-    if (k.iters >= k.max_iter) {
-      k.status = KS_NOCONV; active[r] = 0; return;
-    }
-    k.beta = cdiv(rho_new, k.rho);
-    k.rho_old = k.rho;
-    k.rho = rho_new;
-  }
+  if (threadIdx.x == 0) step_qmr(tot, ks[r], active + r);
 }
 
 cudaError_t launch_qmr_scalar(int R, int nblk, const double* partials, KState* ks,
@@ -794,13 +723,14 @@ cudaError_t launch_box_to_sites(int64_t N, int64_t nbox, int R, const int64_t* s
   template cudaError_t launch_update_xr<T>(int64_t, int, cplx_t<T>*, cplx_t<T>*,             \
                                            const cplx_t<T>*, const cplx_t<T>*,               \
                                            const cplx_t<T>*, const cplx_t<T>*, double*,      \
-                                           const KState*, const int*, cudaStream_t);   \
+                                           const KState*, const int*, cudaStream_t,    \
+                                           FoldArgs);                                  \
   template cudaError_t launch_qmr_init<T>(int64_t, int, const cplx_t<T>*, const cplx_t<T>*,  \
                                           cplx_t<T>*, cplx_t<T>*, cplx_t<T>*, double*,       \
                                           cudaStream_t);                                     \
   template cudaError_t launch_qmr_update_r<T>(int64_t, int, cplx_t<T>*, const cplx_t<T>*,    \
                                               double*, const KState*, const int*,            \
-                                              cudaStream_t);                                 \
+                                              cudaStream_t, FoldArgs);                                 \
   template cudaError_t launch_qmr_flush<T>(int64_t, int, cplx_t<T>*, cplx_t<T>*,             \
                                            const cplx_t<T>*, const KState*, cudaStream_t);
 INST(float)

@@ -13,15 +13,15 @@ template int matvec_partial_blocks<float>(const OpView<float>&, const MatvecLaun
 template cudaError_t launch_matvec_p<float>(const OpView<float>&, const MatvecLaunch&, int,
                                             const float2*, float2*, float2*, const float2*,
                                             float2*, const KState*, double*, const int*,
-                                            cudaStream_t, const cudaEvent_t*);
+                                            cudaStream_t, const cudaEvent_t*, FoldArgs);
 template cudaError_t launch_matvec_s<float>(const OpView<float>&, const MatvecLaunch&, int,
                                             const float2*, const float2*, float2*, float2*,
                                             float2*, const KState*, double*, const int*,
-                                            cudaStream_t, const cudaEvent_t*);
+                                            cudaStream_t, const cudaEvent_t*, FoldArgs);
 template cudaError_t launch_matvec_q<float>(const OpView<float>&, const MatvecLaunch&, int,
                                             const float2*, float2*, float2*, float2*, float2*,
                                             float2*, const KState*, double*, const int*,
-                                            cudaStream_t, const cudaEvent_t*);
+                                            cudaStream_t, const cudaEvent_t*, FoldArgs);
 template cudaError_t launch_matvec<float>(const OpView<float>&, const MatvecLaunch&, int,
                                           const float2*, float2*, float2*, const int*,
                                           cudaStream_t, const cudaEvent_t*);

@@ -14,15 +14,15 @@ template int matvec_partial_blocks<double>(const OpView<double>&, const MatvecLa
 template cudaError_t launch_matvec_p<double>(const OpView<double>&, const MatvecLaunch&, int,
                                              const double2*, double2*, double2*,
                                              const double2*, double2*, const KState*, double*,
-                                             const int*, cudaStream_t, const cudaEvent_t*);
+                                             const int*, cudaStream_t, const cudaEvent_t*, FoldArgs);
 template cudaError_t launch_matvec_s<double>(const OpView<double>&, const MatvecLaunch&, int,
                                              const double2*, const double2*, double2*,
                                              double2*, double2*, const KState*, double*,
-                                             const int*, cudaStream_t, const cudaEvent_t*);
+                                             const int*, cudaStream_t, const cudaEvent_t*, FoldArgs);
 template cudaError_t launch_matvec_q<double>(const OpView<double>&, const MatvecLaunch&, int,
                                              const double2*, double2*, double2*, double2*,
                                              double2*, double2*, const KState*, double*,
-                                             const int*, cudaStream_t, const cudaEvent_t*);
+                                             const int*, cudaStream_t, const cudaEvent_t*, FoldArgs);
 template cudaError_t launch_matvec<double>(const OpView<double>&, const MatvecLaunch&, int,
                                            const double2*, double2*, double2*, const int*,
                                            cudaStream_t, const cudaEvent_t*);

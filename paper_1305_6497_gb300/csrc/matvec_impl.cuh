@@ -23,6 +23,7 @@
 
 #include "dda_ops.h"
 #include "fft_core.cuh"
+#include "krylov_scalar.cuh"
 #include "reduce.cuh"
 
 namespace dda {
@@ -810,7 +811,8 @@ template <typename T, int MODE, int PLAN = 0>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpView<T> op, const cplx_t<T>* __restrict__ buf,
                             const io_t<T>* __restrict__ xin, io_t<T>* __restrict__ yout,
                             int nlines, unsigned long long div_nl, const int* __restrict__ active,
-                            const io_t<T>* __restrict__ rhat, double* __restrict__ partials) {
+                            const io_t<T>* __restrict__ rhat, double* __restrict__ partials,
+                            FoldArgs fold) {
   using C = cplx_t<T>;
   constexpr int LP = plan_len<PLAN>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -908,8 +910,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   }
   }
   if constexpr (MODE != XOUT_PLAIN && MODE != XOUT_FIELD) {
-    if constexpr (MODE == XOUT_RV || MODE == XOUT_QT) acc.template write<2>(partials);
-    else acc.template write<4>(partials);
+    if constexpr (MODE == XOUT_RV || MODE == XOUT_QT) {
+      acc.template write<2>(partials);
+      if (fold.counter) fold_scalar_step<2>(partials, fold);
+    } else {
+      acc.template write<4>(partials);
+      if (fold.counter) fold_scalar_step<4>(partials, fold);
+    }
   }
 }
 
@@ -958,7 +965,7 @@ template <typename T, int XOUT>
 static void launch_x_inv_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
                               const cplx_t<T>* scratch, const io_t<T>* x, io_t<T>* y,
                               const int* active, const io_t<T>* rhat, double* partials,
-                              cudaStream_t st) {
+                              cudaStream_t st, FoldArgs fold = FoldArgs()) {
   const int rows = 3 * op.nz * op.ny;
   dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
   const unsigned long long dv = div_magic(L.x_lines);
@@ -967,18 +974,18 @@ static void launch_x_inv_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
     if (pl == 1) {
       k_fft_x_inv<T, XOUT, 1><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y,
                                                                     L.x_lines, dv, active,
-                                                                    rhat, partials);
+                                                                    rhat, partials, fold);
       return;
     }
     if (pl == 2) {
       k_fft_x_inv<T, XOUT, 2><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y,
                                                                     L.x_lines, dv, active,
-                                                                    rhat, partials);
+                                                                    rhat, partials, fold);
       return;
     }
   }
   k_fft_x_inv<T, XOUT, 0><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y, L.x_lines,
-                                                                dv, active, rhat, partials);
+                                                                dv, active, rhat, partials, fold);
 }
 
 // --------------------------------------------------------------------------
@@ -1114,7 +1121,8 @@ template <typename T, int XIN, int XOUT, bool CROSS = false>
 static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int R,
                                  const io_t<T>* x, io_t<T>* y, cplx_t<T>* scratch,
                                  const int* active, cudaStream_t st, const cudaEvent_t* ev,
-                                 XinArgs<T> xa, const io_t<T>* rhat, double* partials) {
+                                 XinArgs<T> xa, const io_t<T>* rhat, double* partials,
+                                 FoldArgs fold = FoldArgs()) {
   // inside a stream capture the events must be external nodes to be recorded
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (ev) cudaStreamIsCapturing(st, &cap);
@@ -1135,7 +1143,7 @@ static cudaError_t matvec_passes(const OpView<T>& op, const MatvecLaunch& L, int
   launch_y_pass<T, true>(op, L, R, scratch, active, st);
   note_launch();
   if (ev) record(ev[4]);
-  launch_x_inv_pass<T, XOUT>(op, L, R, scratch, x, y, active, rhat, partials, st);
+  launch_x_inv_pass<T, XOUT>(op, L, R, scratch, x, y, active, rhat, partials, st, fold);
   note_launch();
   if (ev) record(ev[5]);
   return cudaGetLastError();
@@ -1173,10 +1181,10 @@ cudaError_t launch_matvec_p(const OpView<T>& op, const MatvecLaunch& L, int R,
                             const cplx_t<T>* r, cplx_t<T>* p, cplx_t<T>* v,
                             const cplx_t<T>* rhat, cplx_t<T>* scratch, const KState* ks,
                             double* partials, const int* active, cudaStream_t st,
-                            const cudaEvent_t* ev) {
+                            const cudaEvent_t* ev, FoldArgs fold) {
   XinArgs<T> xa{r, p, v, ks};
   return matvec_passes<T, XIN_P, XOUT_RV>(op, L, R, p, v, scratch, active, st, ev, xa, rhat,
-                                          partials);
+                                          partials, fold);
 }
 
 template <typename T>
@@ -1184,10 +1192,10 @@ cudaError_t launch_matvec_s(const OpView<T>& op, const MatvecLaunch& L, int R,
                             const cplx_t<T>* r, const cplx_t<T>* v, cplx_t<T>* s_vec,
                             cplx_t<T>* t_vec, cplx_t<T>* scratch, const KState* ks,
                             double* partials, const int* active, cudaStream_t st,
-                            const cudaEvent_t* ev) {
+                            const cudaEvent_t* ev, FoldArgs fold) {
   XinArgs<T> xa{r, s_vec, v, ks};
   return matvec_passes<T, XIN_S, XOUT_TS>(op, L, R, s_vec, t_vec, scratch, active, st, ev, xa,
-                                          nullptr, partials);
+                                          nullptr, partials, fold);
 }
 
 template <typename T>
@@ -1204,10 +1212,10 @@ cudaError_t launch_matvec_q(const OpView<T>& op, const MatvecLaunch& L, int R,
                             const cplx_t<T>* r, cplx_t<T>* q, cplx_t<T>* d, cplx_t<T>* x,
                             cplx_t<T>* t_vec, cplx_t<T>* scratch, const KState* ks,
                             double* partials, const int* active, cudaStream_t st,
-                            const cudaEvent_t* ev) {
+                            const cudaEvent_t* ev, FoldArgs fold) {
   XinArgs<T> xa{r, q, nullptr, ks, d, x};
   return matvec_passes<T, XIN_Q, XOUT_QT>(op, L, R, q, t_vec, scratch, active, st, ev, xa,
-                                          nullptr, partials);
+                                          nullptr, partials, fold);
 }
 
 template <typename T>
