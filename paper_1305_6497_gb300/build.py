@@ -19,7 +19,8 @@ LIB = os.path.join(HERE, "libdda.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["api.cu", "matvec_f32.cu", "matvec_f64.cu", "matvec_df.cu", "krylov.cu",
-           "bicgstab2.cu", "gpbicg.cu", "green.cu", "observables.cu", "scattering.cu"]
+           "bicgstab2.cu", "gpbicg.cu", "green.cu", "observables.cu", "scattering.cu",
+           "matvec_fixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

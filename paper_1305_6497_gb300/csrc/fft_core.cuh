@@ -287,72 +287,6 @@ __device__ void fft_smem(C* s, int nlines, int pstride, const AxisPlan& P,
   }
 }
 
-// The same transform for the two-stage plan R0 x R1 (L = R0 R1) with the
-// radices, spans and twiddle layout known at compile time: stage 0 (radix R0,
-// block L, span R1, twiddles w_L^{jm}) and stage 1 (radix R1, span 1, no
-// twiddles), the operations of fft_smem in the same order.  div_nl is the
-// fast_div magic of nlines.
-template <typename C, bool INV, int R0, int R1>
-__device__ void fft_smem_c(C* s, int nlines, unsigned long long div_nl, int ps,
-                           const C* __restrict__ tw, bool half) {
-  auto stage0 = [&]() {
-    for (int b = threadIdx.x; b < nlines * R1; b += blockDim.x) {
-      const int j = fast_div(b, div_nl), line = b - j * nlines;
-      C* base = s + j * ps + line;
-      C v[R0];
-      if (!INV) {
-        if (half) {
-#pragma unroll
-          for (int i = 0; i < R0 / 2; ++i) v[i] = base[i * R1 * ps];
-          dft_half<R0, false, true, false>(v);
-        } else {
-#pragma unroll
-          for (int i = 0; i < R0; ++i) v[i] = base[i * R1 * ps];
-          dft<R0, false>(v);
-        }
-        if (j > 0) {
-#pragma unroll
-          for (int m = 1; m < R0; ++m) v[m] = cmul(v[m], ldc(&tw[j * (R0 - 1) + (m - 1)]));
-        }
-#pragma unroll
-        for (int i = 0; i < R0; ++i) base[i * R1 * ps] = v[i];
-      } else {
-#pragma unroll
-        for (int i = 0; i < R0; ++i) v[i] = base[i * R1 * ps];
-        if (j > 0) {
-#pragma unroll
-          for (int m = 1; m < R0; ++m) v[m] = cmulc(ldc(&tw[j * (R0 - 1) + (m - 1)]), v[m]);
-        }
-        if (half) {
-          dft_half<R0, true, false, true>(v);
-#pragma unroll
-          for (int i = 0; i < R0 / 2; ++i) base[i * R1 * ps] = v[i];
-        } else {
-          dft<R0, true>(v);
-#pragma unroll
-          for (int i = 0; i < R0; ++i) base[i * R1 * ps] = v[i];
-        }
-      }
-    }
-    __syncthreads();
-  };
-  auto stage1 = [&]() {
-    for (int b = threadIdx.x; b < nlines * R0; b += blockDim.x) {
-      const int blk = fast_div(b, div_nl), line = b - blk * nlines;
-      C* base = s + blk * R1 * ps + line;
-      C v[R1];
-#pragma unroll
-      for (int i = 0; i < R1; ++i) v[i] = base[i * ps];
-      dft<R1, INV>(v);
-#pragma unroll
-      for (int i = 0; i < R1; ++i) base[i * ps] = v[i];
-    }
-    __syncthreads();
-  };
-  if (!INV) { stage0(); stage1(); }
-  else { stage1(); stage0(); }
-}
-
 // ---- stages fused with global memory ---------------------------------------------
 // The first forward stage (block = L) reads its R inputs straight from global
 // memory through ld(line, p) (which returns 0 for positions beyond the input);

@@ -23,6 +23,7 @@
 
 #include "dda_ops.h"
 #include "fft_core.cuh"
+#include "fft_plan.cuh"
 #include "krylov_scalar.cuh"
 #include "reduce.cuh"
 
@@ -50,16 +51,19 @@ template <typename T> struct XinArgs {
   cplx_t<T>* x;
 };
 
-// PLAN: 0 -- any radix plan (read at run time); 1 / 2 -- the 16 x 8 / 16 x 4
-// plan (Lx = 128 / 64) with Lx and the stages known at compile time (FP32).
-template <int PLAN> constexpr int plan_len() { return PLAN == 1 ? 128 : PLAN == 2 ? 64 : 0; }
+// P: void -- the radix plan is read at run time; a FixedPlan -- Lx and the
+// stages are compile-time constants (FP32, see fft_plan.cuh).
+template <class P> constexpr int plan_len() {
+  if constexpr (std::is_void<P>::value) return 0;
+  else return P::L;
+}
 
-template <typename T, int MODE, int PLAN = 0>
+template <typename T, int MODE, class P = void>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpView<T> op, const io_t<T>* __restrict__ in,
                             cplx_t<T>* __restrict__ buf, int nlines, unsigned long long div_nl,
                             const int* __restrict__ active, XinArgs<T> xa) {
   using C = cplx_t<T>;
-  constexpr int LP = plan_len<PLAN>();
+  constexpr int LP = plan_len<P>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int r = blockIdx.y;
@@ -146,8 +150,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpVie
     s[p * ps + line] = mk<C>(0, 0);
   }
   __syncthreads();
-  if constexpr (PLAN == 0) fft_smem<C, false>(s, nlines, ps, op.px, op.twx, half);
-  else fft_smem_c<C, false, 16, PLAN == 1 ? 8 : 4>(s, nlines, div_nl, ps, op.twx, half);
+  if constexpr (std::is_void<P>::value) fft_smem<C, false>(s, nlines, ps, op.px, op.twx, half);
+  else fft_smem_p<C, false, P>(s, nlines, div_nl, ps, op.twx, half);
   const int64_t plane_sz = (int64_t)op.Ly * Lx;
   C* dst = buf + (int64_t)r * 3 * op.nz * plane_sz;
 #pragma unroll 4
@@ -214,14 +218,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_y(OpView<T>
   }
 }
 
-// y pass for the two-stage lengths Ly = R0 R1 (radix plans 16 x 8 and 16 x 4)
-// with the tile width, strides and loop bounds known at compile time: the
-// same stages and operations as k_fft_y (bit-identical output).
-template <int TILE, bool INV, int R0, int R1>
+// y pass with a radix plan P fixed at compile time (FP32, a tile of TILE
+// columns): the same stages and operations as k_fft_y (bit-identical output).
+template <int TILE, bool INV, class P>
 __global__ void __launch_bounds__(256, 3)
-k_fft_y_c(OpView<float> op, float2* __restrict__ buf, const int* __restrict__ active) {
+k_fft_y_p(OpView<float> op, float2* __restrict__ buf, const int* __restrict__ active) {
   using C = float2;
-  constexpr int L = R0 * R1, S = R1;
+  constexpr int L = P::L, NS = P::NS, R0 = P::radix(0), S0 = P::span(0);
+  constexpr int RL = P::radix(NS - 1);
+  constexpr unsigned long long DV = div_magic_c(TILE);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int r = blockIdx.z;
@@ -232,23 +237,23 @@ k_fft_y_c(OpView<float> op, float2* __restrict__ buf, const int* __restrict__ ac
   C* base = buf + ((int64_t)r * 3 * op.nz + blockIdx.y) * (int64_t)L * Lx + col0;
   const C* __restrict__ tw = op.twy;
   const bool half = 2 * ny <= L;
-  const int64_t sstride = (int64_t)S * Lx;
+  const int64_t sstride = (int64_t)S0 * Lx;
   if (!INV) {
-    // first stage (radix R0, span S) from global memory: ny input rows
-    for (int b = threadIdx.x; b < TILE * S; b += blockDim.x) {
+    // first stage (radix R0, span S0) from global memory: ny input rows
+    for (int b = threadIdx.x; b < TILE * S0; b += blockDim.x) {
       const int t = b % TILE, j = b / TILE;
       const C* src = base + (int64_t)j * Lx + t;
       const bool ok = t < ncol;
       C v[R0];
-      if (half) {
+      if (R0 % 2 == 0 && half) {
 #pragma unroll
         for (int i = 0; i < R0 / 2; ++i)
-          v[i] = (ok && j + i * S < ny) ? src[i * sstride] : make_float2(0.f, 0.f);
-        dft_half<R0, false, true, false>(v);
+          v[i] = (ok && j + i * S0 < ny) ? src[i * sstride] : make_float2(0.f, 0.f);
+        if constexpr (R0 % 2 == 0) dft_half<R0, false, true, false>(v);
       } else {
 #pragma unroll
         for (int i = 0; i < R0; ++i)
-          v[i] = (ok && j + i * S < ny) ? src[i * sstride] : make_float2(0.f, 0.f);
+          v[i] = (ok && j + i * S0 < ny) ? src[i * sstride] : make_float2(0.f, 0.f);
         dft<R0, false>(v);
       }
       if (j > 0) {
@@ -256,58 +261,60 @@ k_fft_y_c(OpView<float> op, float2* __restrict__ buf, const int* __restrict__ ac
         for (int m = 1; m < R0; ++m) v[m] = cmul(v[m], ldc(&tw[j * (R0 - 1) + (m - 1)]));
       }
 #pragma unroll
-      for (int m = 0; m < R0; ++m) s[(j + m * S) * TILE + t] = v[m];
+      for (int m = 0; m < R0; ++m) s[(j + m * S0) * TILE + t] = v[m];
     }
     __syncthreads();
-    // last stage (radix R1, span 1) to global memory: all L rows
-    for (int b = threadIdx.x; b < TILE * R0; b += blockDim.x) {
+    stages_p<C, false, P, 1, NS - 2>(s, TILE, DV, TILE, tw);
+    // last stage (radix RL, span 1) to global memory: all L rows
+    for (int b = threadIdx.x; b < TILE * (L / RL); b += blockDim.x) {
       const int t = b % TILE, blk = b / TILE;
-      C v[R1];
+      C v[RL];
 #pragma unroll
-      for (int i = 0; i < R1; ++i) v[i] = s[(blk * R1 + i) * TILE + t];
-      dft<R1, false>(v);
+      for (int i = 0; i < RL; ++i) v[i] = s[(blk * RL + i) * TILE + t];
+      dft<RL, false>(v);
       if (t < ncol) {
-        C* dst = base + (int64_t)blk * R1 * Lx + t;
+        C* dst = base + (int64_t)blk * RL * Lx + t;
 #pragma unroll
-        for (int m = 0; m < R1; ++m) dst[(int64_t)m * Lx] = v[m];
+        for (int m = 0; m < RL; ++m) dst[(int64_t)m * Lx] = v[m];
       }
     }
   } else {
-    // first inverse stage (radix R1, span 1) from global memory: all L rows
-    for (int b = threadIdx.x; b < TILE * R0; b += blockDim.x) {
+    // first inverse stage (radix RL, span 1) from global memory: all L rows
+    for (int b = threadIdx.x; b < TILE * (L / RL); b += blockDim.x) {
       const int t = b % TILE, blk = b / TILE;
-      const C* src = base + (int64_t)blk * R1 * Lx + t;
+      const C* src = base + (int64_t)blk * RL * Lx + t;
       const bool ok = t < ncol;
-      C v[R1];
+      C v[RL];
 #pragma unroll
-      for (int m = 0; m < R1; ++m) v[m] = ok ? src[(int64_t)m * Lx] : make_float2(0.f, 0.f);
-      dft<R1, true>(v);
+      for (int m = 0; m < RL; ++m) v[m] = ok ? src[(int64_t)m * Lx] : make_float2(0.f, 0.f);
+      dft<RL, true>(v);
 #pragma unroll
-      for (int i = 0; i < R1; ++i) s[(blk * R1 + i) * TILE + t] = v[i];
+      for (int i = 0; i < RL; ++i) s[(blk * RL + i) * TILE + t] = v[i];
     }
     __syncthreads();
+    stages_p<C, true, P, 1, NS - 2>(s, TILE, DV, TILE, tw);
     // last inverse stage (radix R0) to global memory: ny output rows
-    for (int b = threadIdx.x; b < TILE * S; b += blockDim.x) {
+    for (int b = threadIdx.x; b < TILE * S0; b += blockDim.x) {
       const int t = b % TILE, j = b / TILE;
       C* dst = base + (int64_t)j * Lx + t;
       const bool ok = t < ncol;
       C v[R0];
 #pragma unroll
-      for (int m = 0; m < R0; ++m) v[m] = s[(j + m * S) * TILE + t];
+      for (int m = 0; m < R0; ++m) v[m] = s[(j + m * S0) * TILE + t];
       if (j > 0) {
 #pragma unroll
         for (int m = 1; m < R0; ++m) v[m] = cmulc(ldc(&tw[j * (R0 - 1) + (m - 1)]), v[m]);
       }
-      if (half) {
-        dft_half<R0, true, false, true>(v);
+      if (R0 % 2 == 0 && half) {
+        if constexpr (R0 % 2 == 0) dft_half<R0, true, false, true>(v);
 #pragma unroll
         for (int i = 0; i < R0 / 2; ++i)
-          if (ok && j + i * S < ny) dst[i * sstride] = v[i];
+          if (ok && j + i * S0 < ny) dst[i * sstride] = v[i];
       } else {
         dft<R0, true>(v);
 #pragma unroll
         for (int i = 0; i < R0; ++i)
-          if (ok && j + i * S < ny) dst[i * sstride] = v[i];
+          if (ok && j + i * S0 < ny) dst[i * sstride] = v[i];
       }
     }
   }
@@ -550,22 +557,23 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
 }
 
 // --------------------------------------------------------------------------
-// z pass for the two-stage lengths Lz = R0 R1 (radix plans 16 x 8 and 16 x 4:
-// Lz = 128 and 64), with every size known at compile time.  It runs the same
+// z pass with a radix plan P fixed at compile time (FP32).  It runs the same
 // stages, twiddles, multiply and operations in the same order as k_fft_z_mul
 // (the product is bit-identical); the shared-memory pitch, strides, loop
-// bounds and the frequency at each digit-reversed position (kz = blk + R0 i
-// at position blk R1 + i) become constants, which takes the index arithmetic
-// out of the issue-bound loop and leaves a smaller kernel (one plan, no radix
-// dispatch) for the instruction cache.
+// bounds and the frequency at each digit-reversed position (P::k_at) become
+// constants, which takes the index arithmetic out of the issue-bound loop and
+// leaves a smaller kernel (one plan, no radix dispatch) for the instruction
+// cache.
 // --------------------------------------------------------------------------
 template <int TILE> constexpr int zc_pitch() { return 3 * TILE + (TILE * 8 < 128 ? 1 : 0); }
 
-template <int TILE, bool GS, int R0, int R1>
+template <int TILE, bool GS, class P>
 __global__ void __launch_bounds__(256, 3)
-k_fft_z_mul_c(OpView<float> op, float2* __restrict__ buf, const int* __restrict__ active) {
+k_fft_z_mul_p(OpView<float> op, float2* __restrict__ buf, const int* __restrict__ active) {
   using C = float2;
-  constexpr int L = R0 * R1, S = R1, NL = 3 * TILE, PS = zc_pitch<TILE>();
+  constexpr int L = P::L, NS = P::NS, R0 = P::radix(0), S0 = P::span(0);
+  constexpr int RL = P::radix(NS - 1), NL = 3 * TILE, PS = zc_pitch<TILE>();
+  constexpr unsigned long long DV = div_magic_c(NL);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int r = blockIdx.z;
@@ -584,23 +592,23 @@ k_fft_z_mul_c(OpView<float> op, float2* __restrict__ buf, const int* __restrict_
   if (GS) ghat_tile_async<float, TILE>(op, gs, col0, ncol, hy);
   const C* __restrict__ tw = op.twz;
   const bool half = 2 * nz <= L;
-  const int64_t sstride = (int64_t)S * plane_sz;  // global distance of one butterfly input
-  // first forward stage (radix R0, span S), read straight from global memory
-  for (int b = threadIdx.x; b < NL * S; b += blockDim.x) {
+  const int64_t sstride = (int64_t)S0 * plane_sz;  // global distance of one butterfly input
+  // first forward stage (radix R0, span S0), read straight from global memory
+  for (int b = threadIdx.x; b < NL * S0; b += blockDim.x) {
     const int line = b % NL, j = b / NL;
     const int c = line / TILE, t = line - c * TILE;
     const C* src = base + c * comp_sz + (int64_t)j * plane_sz + t;
     const bool ok = t < ncol;
     C v[R0];
-    if (half) {
+    if (R0 % 2 == 0 && half) {
 #pragma unroll
       for (int i = 0; i < R0 / 2; ++i)
-        v[i] = (ok && j + i * S < nz) ? src[i * sstride] : make_float2(0.f, 0.f);
-      dft_half<R0, false, true, false>(v);
+        v[i] = (ok && j + i * S0 < nz) ? src[i * sstride] : make_float2(0.f, 0.f);
+      if constexpr (R0 % 2 == 0) dft_half<R0, false, true, false>(v);
     } else {
 #pragma unroll
       for (int i = 0; i < R0; ++i)
-        v[i] = (ok && j + i * S < nz) ? src[i * sstride] : make_float2(0.f, 0.f);
+        v[i] = (ok && j + i * S0 < nz) ? src[i * sstride] : make_float2(0.f, 0.f);
       dft<R0, false>(v);
     }
     if (j > 0) {
@@ -608,32 +616,36 @@ k_fft_z_mul_c(OpView<float> op, float2* __restrict__ buf, const int* __restrict_
       for (int m = 1; m < R0; ++m) v[m] = cmul(v[m], ldc(&tw[j * (R0 - 1) + (m - 1)]));
     }
 #pragma unroll
-    for (int m = 0; m < R0; ++m) s[(j + m * S) * PS + line] = v[m];
+    for (int m = 0; m < R0; ++m) s[(j + m * S0) * PS + line] = v[m];
+  }
+  if constexpr (NS > 2) {
+    __syncthreads();
+    stages_p<C, false, P, 1, NS - 2>(s, NL, DV, PS, tw);
   }
   if (GS) cp_async_wait_all();
   __syncthreads();
-  // last forward stage + multiply + first inverse stage (radix R1, span 1):
-  // a thread owns R1 consecutive positions of one column, all three components
+  // last forward stage + multiply + first inverse stage (radix RL, span 1):
+  // a thread owns RL consecutive positions of one column, all three components
   {
     const int kxh = Lx >> 1;
-    for (int b = threadIdx.x; b < TILE * R0; b += blockDim.x) {
+    for (int b = threadIdx.x; b < TILE * (L / RL); b += blockDim.x) {
       const int t = b % TILE, blk = b / TILE;
-      C* q = s + blk * R1 * PS + t;
+      C* q = s + blk * RL * PS + t;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        C v[R1];
+        C v[RL];
 #pragma unroll
-        for (int i = 0; i < R1; ++i) v[i] = q[i * PS + c * TILE];
-        dft<R1, false>(v);
+        for (int i = 0; i < RL; ++i) v[i] = q[i * PS + c * TILE];
+        dft<RL, false>(v);
 #pragma unroll
-        for (int i = 0; i < R1; ++i) q[i * PS + c * TILE] = v[i];
+        for (int i = 0; i < RL; ++i) q[i * PS + c * TILE] = v[i];
       }
       if (t < ncol) {
         const int kx = op.kx_at[col0 + t];
         const bool fx = kx > kxh;
 #pragma unroll
-        for (int i = 0; i < R1; ++i) {
-          const int kz = blk + R0 * i;
+        for (int i = 0; i < RL; ++i) {
+          const int kz = P::k_at(blk * RL + i);
           const bool fz = kz > L / 2;
           const int hz = fz ? L - kz : kz;
           C g[6];
@@ -648,85 +660,77 @@ k_fft_z_mul_c(OpView<float> op, float2* __restrict__ buf, const int* __restrict_
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        C v[R1];
+        C v[RL];
 #pragma unroll
-        for (int i = 0; i < R1; ++i) v[i] = q[i * PS + c * TILE];
-        dft<R1, true>(v);
+        for (int i = 0; i < RL; ++i) v[i] = q[i * PS + c * TILE];
+        dft<RL, true>(v);
 #pragma unroll
-        for (int i = 0; i < R1; ++i) q[i * PS + c * TILE] = v[i];
+        for (int i = 0; i < RL; ++i) q[i * PS + c * TILE] = v[i];
       }
     }
   }
   __syncthreads();
+  if constexpr (NS > 2) stages_p<C, true, P, 1, NS - 2>(s, NL, DV, PS, tw);
   // last inverse stage (radix R0), written straight to global memory
-  for (int b = threadIdx.x; b < NL * S; b += blockDim.x) {
+  for (int b = threadIdx.x; b < NL * S0; b += blockDim.x) {
     const int line = b % NL, j = b / NL;
     const int c = line / TILE, t = line - c * TILE;
     C* dst = base + c * comp_sz + (int64_t)j * plane_sz + t;
     const bool ok = t < ncol;
     C v[R0];
 #pragma unroll
-    for (int m = 0; m < R0; ++m) v[m] = s[(j + m * S) * PS + line];
+    for (int m = 0; m < R0; ++m) v[m] = s[(j + m * S0) * PS + line];
     if (j > 0) {
 #pragma unroll
       for (int m = 1; m < R0; ++m) v[m] = cmulc(ldc(&tw[j * (R0 - 1) + (m - 1)]), v[m]);
     }
-    if (half) {
-      dft_half<R0, true, false, true>(v);
+    if (R0 % 2 == 0 && half) {
+      if constexpr (R0 % 2 == 0) dft_half<R0, true, false, true>(v);
 #pragma unroll
       for (int i = 0; i < R0 / 2; ++i)
-        if (ok && j + i * S < nz) dst[i * sstride] = v[i];
+        if (ok && j + i * S0 < nz) dst[i * sstride] = v[i];
     } else {
       dft<R0, true>(v);
 #pragma unroll
       for (int i = 0; i < R0; ++i)
-        if (ok && j + i * S < nz) dst[i * sstride] = v[i];
+        if (ok && j + i * S0 < nz) dst[i * sstride] = v[i];
     }
   }
-}
-
-// One y pass (forward: ny -> Ly rows, inverse: Ly -> ny rows) with the
-// schedule's tile; FP32 with a 16 x 8 or 16 x 4 plan and a tile of 8, 16 or
-// 32 columns runs the compile-time kernel.
-template <typename T, bool INV>
-static void launch_y_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
-                          cplx_t<T>* scratch, const int* active, cudaStream_t st) {
-  dim3 gy((op.Lx + L.y_tile - 1) / L.y_tile, 3 * op.nz, R);
-  if constexpr (std::is_same<T, float>::value) {
-    const AxisPlan& P = op.py;
-    if (P.nstage == 2 && P.radix[0] == 16 && (P.radix[1] == 8 || P.radix[1] == 4) &&
-        (L.y_tile == 8 || L.y_tile == 16 || L.y_tile == 32)) {
-#define DDA_YC(TT)                                                                    \
-  {                                                                                   \
-    if (P.radix[1] == 8)                                                              \
-      k_fft_y_c<TT, INV, 16, 8><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, active); \
-    else                                                                              \
-      k_fft_y_c<TT, INV, 16, 4><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, active); \
-  }
-      switch (L.y_tile) {
-        case 8: DDA_YC(8); break;
-        case 16: DDA_YC(16); break;
-        default: DDA_YC(32); break;
-      }
-#undef DDA_YC
-      return;
-    }
-  }
-  k_fft_y<T, INV><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, active);
-}
-
-// The compile-time z kernel applies (FP32, no cross product, a 16 x 8 or
-// 16 x 4 plan).
-template <typename T, bool CROSS>
-static bool zc_applies(const OpView<T>& op) {
-  return std::is_same<T, float>::value && !CROSS && op.pz.nstage == 2 && op.pz.radix[0] == 16 &&
-         (op.pz.radix[1] == 8 || op.pz.radix[1] == 4);
 }
 
 template <int TILE, bool GS>
-static size_t zc_smem(const OpView<float>& op) {
+static size_t zp_smem(const OpView<float>& op) {
   const size_t d = ((size_t)op.Lz * zc_pitch<TILE>() * sizeof(float2) + 15) & ~(size_t)15;
   return d + (GS ? (size_t)6 * op.Hz * TILE * sizeof(float2) : 0);
+}
+
+// FP32 passes with a compiled radix plan (matvec_fixed.cu).  Each returns
+// false, launching nothing, when no compiled variant matches the axis plan
+// and the schedule's tile.
+bool launch_y_fixed(bool inv, const OpView<float>& op, const MatvecLaunch& L, int R,
+                    float2* scratch, const int* active, cudaStream_t st);
+bool launch_z_fixed(const OpView<float>& op, const MatvecLaunch& L, int R, float2* scratch,
+                    const int* active, cudaStream_t st);
+bool z_fixed_plan(const AxisPlan& P);
+template <int XIN>
+bool launch_x_fwd_fixed(const OpView<float>& op, const MatvecLaunch& L, int R, const float2* x,
+                        float2* scratch, const int* active, XinArgs<float> xa, cudaStream_t st);
+template <int XOUT>
+bool launch_x_inv_fixed(const OpView<float>& op, const MatvecLaunch& L, int R,
+                        const float2* scratch, const float2* x, float2* y, const int* active,
+                        const float2* rhat, double* partials, cudaStream_t st, FoldArgs fold);
+cudaError_t configure_fixed_kernels();
+
+// One y pass (forward: ny -> Ly rows, inverse: Ly -> ny rows) with the
+// schedule's tile (a compiled radix plan where one matches).
+template <typename T, bool INV>
+static void launch_y_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
+                          cplx_t<T>* scratch, const int* active, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (launch_y_fixed(INV, op, L, R, scratch, active, st)) return;
+  }
+  dim3 gy((op.Lx + L.y_tile - 1) / L.y_tile, 3 * op.nz, R);
+  k_fft_y<T, INV><<<gy, L.y_threads, L.y_smem, st>>>(op, scratch, L.y_tile, active);
 }
 
 // One z pass (forward z, multiply, inverse z) with the schedule's tile.
@@ -743,34 +747,7 @@ static void launch_z_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
   } else {
     dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly, R);
     if constexpr (std::is_same<T, float>::value && !CROSS) {
-      if (zc_applies<T, CROSS>(op)) {
-#define DDA_ZC(TT, GG)                                                                        \
-  {                                                                                           \
-    if (op.pz.radix[1] == 8)                                                                  \
-      k_fft_z_mul_c<TT, GG, 16, 8><<<gz, L.z_threads, zc_smem<TT, GG>(op), st>>>(op, scratch, \
-                                                                                  active);    \
-    else                                                                                      \
-      k_fft_z_mul_c<TT, GG, 16, 4><<<gz, L.z_threads, zc_smem<TT, GG>(op), st>>>(op, scratch, \
-                                                                                  active);    \
-  }
-        if (L.z_gs) {
-          switch (L.z_tile) {
-            case 16: DDA_ZC(16, true); break;
-            case 8: DDA_ZC(8, true); break;
-            case 4: DDA_ZC(4, true); break;
-            default: DDA_ZC(2, true); break;
-          }
-        } else {
-          switch (L.z_tile) {
-            case 16: DDA_ZC(16, false); break;
-            case 8: DDA_ZC(8, false); break;
-            case 4: DDA_ZC(4, false); break;
-            default: DDA_ZC(2, false); break;
-          }
-        }
-#undef DDA_ZC
-        return;
-      }
+      if (launch_z_fixed(op, L, R, scratch, active, st)) return;
     }
 #define DDA_ZL(TT, GG) \
   k_fft_z_mul<T, TT, GG, CROSS><<<gz, L.z_threads, L.z_smem, st>>>(op, scratch, L.z_ps, active)
@@ -807,14 +784,14 @@ static void launch_z_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
 //                not (the field the dipoles radiate; near-field output)
 enum { XOUT_PLAIN = 0, XOUT_RV = 1, XOUT_TS = 2, XOUT_QT = 3, XOUT_FIELD = 4 };
 
-template <typename T, int MODE, int PLAN = 0>
+template <typename T, int MODE, class P = void>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpView<T> op, const cplx_t<T>* __restrict__ buf,
                             const io_t<T>* __restrict__ xin, io_t<T>* __restrict__ yout,
                             int nlines, unsigned long long div_nl, const int* __restrict__ active,
                             const io_t<T>* __restrict__ rhat, double* __restrict__ partials,
                             FoldArgs fold) {
   using C = cplx_t<T>;
-  constexpr int LP = plan_len<PLAN>();
+  constexpr int LP = plan_len<P>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int r = blockIdx.y;
@@ -853,8 +830,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   cp_async_wait_all();
   __syncthreads();
   // only positions < nx <= Lx/2 are used below
-  if constexpr (PLAN == 0) fft_smem<C, true>(s, nlines, ps, op.px, op.twx, 2 * nx <= Lx);
-  else fft_smem_c<C, true, 16, PLAN == 1 ? 8 : 4>(s, nlines, div_nl, ps, op.twx, 2 * nx <= Lx);
+  if constexpr (std::is_void<P>::value) fft_smem<C, true>(s, nlines, ps, op.px, op.twx, 2 * nx <= Lx);
+  else fft_smem_p<C, true, P>(s, nlines, div_nl, ps, op.twx, 2 * nx <= Lx);
   const C* ai = op.ainv + (int64_t)r * op.ncomp1;
   IO* yr = yout + g0;
   // (df64 passes only run the plain epilogue; their accumulator type is unused)
@@ -920,44 +897,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   }
 }
 
-// Radix plan of the x passes as a compile-time variant (see k_fft_x_fwd).
-template <typename T>
-static int x_plan(const OpView<T>& op) {
-  if constexpr (std::is_same<T, float>::value) {
-    const AxisPlan& P = op.px;
-    if (P.nstage == 2 && P.radix[0] == 16 && P.radix[1] == 8 && op.Lx == 128) return 1;
-    if (P.nstage == 2 && P.radix[0] == 16 && P.radix[1] == 4 && op.Lx == 64) return 2;
-  }
-  return 0;
-}
-
 static inline unsigned long long div_magic(int d) {
   return ((1ull << 36) + (unsigned long long)d - 1) / (unsigned long long)d;
 }
 
-// One forward x pass (prologue mode XIN) with the schedule's line count.
+// One forward x pass (prologue mode XIN) with the schedule's line count (a
+// compiled radix plan where one matches).
 template <typename T, int XIN>
 static void launch_x_fwd_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
                               const io_t<T>* x, cplx_t<T>* scratch, const int* active,
                               XinArgs<T> xa, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (launch_x_fwd_fixed<XIN>(op, L, R, x, scratch, active, xa, st)) return;
+  }
   const int rows = 3 * op.nz * op.ny;
   dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
-  const unsigned long long dv = div_magic(L.x_lines);
-  if constexpr (std::is_same<T, float>::value) {
-    const int pl = x_plan(op);
-    if (pl == 1) {
-      k_fft_x_fwd<T, XIN, 1><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines, dv,
-                                                                active, xa);
-      return;
-    }
-    if (pl == 2) {
-      k_fft_x_fwd<T, XIN, 2><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines, dv,
-                                                                active, xa);
-      return;
-    }
-  }
-  k_fft_x_fwd<T, XIN, 0><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines, dv,
-                                                            active, xa);
+  k_fft_x_fwd<T, XIN><<<gx, L.x_threads, L.x_smem, st>>>(op, x, scratch, L.x_lines,
+                                                         div_magic(L.x_lines), active, xa);
 }
 
 // One inverse x pass (epilogue mode XOUT) with the schedule's line count.
@@ -966,26 +922,15 @@ static void launch_x_inv_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
                               const cplx_t<T>* scratch, const io_t<T>* x, io_t<T>* y,
                               const int* active, const io_t<T>* rhat, double* partials,
                               cudaStream_t st, FoldArgs fold = FoldArgs()) {
+  if constexpr (std::is_same<T, float>::value && XOUT != XOUT_FIELD) {
+    if (launch_x_inv_fixed<XOUT>(op, L, R, scratch, x, y, active, rhat, partials, st, fold))
+      return;
+  }
   const int rows = 3 * op.nz * op.ny;
   dim3 gx((rows + L.x_lines - 1) / L.x_lines, R);
-  const unsigned long long dv = div_magic(L.x_lines);
-  if constexpr (std::is_same<T, float>::value && XOUT != XOUT_FIELD) {
-    const int pl = x_plan(op);
-    if (pl == 1) {
-      k_fft_x_inv<T, XOUT, 1><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y,
-                                                                    L.x_lines, dv, active,
-                                                                    rhat, partials, fold);
-      return;
-    }
-    if (pl == 2) {
-      k_fft_x_inv<T, XOUT, 2><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y,
-                                                                    L.x_lines, dv, active,
-                                                                    rhat, partials, fold);
-      return;
-    }
-  }
-  k_fft_x_inv<T, XOUT, 0><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y, L.x_lines,
-                                                                dv, active, rhat, partials, fold);
+  k_fft_x_inv<T, XOUT><<<gx, L.x_threads, L.xinv_smem, st>>>(op, scratch, x, y, L.x_lines,
+                                                             div_magic(L.x_lines), active, rhat,
+                                                             partials, fold);
 }
 
 // --------------------------------------------------------------------------
@@ -1060,45 +1005,8 @@ cudaError_t configure_matvec_kernels(const MatvecLaunch& L) {
     if (e != cudaSuccess) return e;
   }
   if constexpr (std::is_same<T, float>::value) {
-    const void* xf[] = {
-        (const void*)k_fft_x_fwd<T, XIN_PLAIN, 1>, (const void*)k_fft_x_fwd<T, XIN_P, 1>,
-        (const void*)k_fft_x_fwd<T, XIN_S, 1>, (const void*)k_fft_x_fwd<T, XIN_Q, 1>,
-        (const void*)k_fft_x_inv<T, XOUT_PLAIN, 1>, (const void*)k_fft_x_inv<T, XOUT_RV, 1>,
-        (const void*)k_fft_x_inv<T, XOUT_TS, 1>, (const void*)k_fft_x_inv<T, XOUT_QT, 1>,
-        (const void*)k_fft_x_fwd<T, XIN_PLAIN, 2>, (const void*)k_fft_x_fwd<T, XIN_P, 2>,
-        (const void*)k_fft_x_fwd<T, XIN_S, 2>, (const void*)k_fft_x_fwd<T, XIN_Q, 2>,
-        (const void*)k_fft_x_inv<T, XOUT_PLAIN, 2>, (const void*)k_fft_x_inv<T, XOUT_RV, 2>,
-        (const void*)k_fft_x_inv<T, XOUT_TS, 2>, (const void*)k_fft_x_inv<T, XOUT_QT, 2>};
-    for (const void* k : xf) {
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (e != cudaSuccess) return e;
-    }
-    const void* zf[] = {
-        (const void*)k_fft_z_mul_c<16, true, 16, 8>, (const void*)k_fft_z_mul_c<8, true, 16, 8>,
-        (const void*)k_fft_z_mul_c<4, true, 16, 8>, (const void*)k_fft_z_mul_c<2, true, 16, 8>,
-        (const void*)k_fft_z_mul_c<16, false, 16, 8>, (const void*)k_fft_z_mul_c<8, false, 16, 8>,
-        (const void*)k_fft_z_mul_c<4, false, 16, 8>, (const void*)k_fft_z_mul_c<2, false, 16, 8>,
-        (const void*)k_fft_z_mul_c<16, true, 16, 4>, (const void*)k_fft_z_mul_c<8, true, 16, 4>,
-        (const void*)k_fft_z_mul_c<4, true, 16, 4>, (const void*)k_fft_z_mul_c<2, true, 16, 4>,
-        (const void*)k_fft_z_mul_c<16, false, 16, 4>, (const void*)k_fft_z_mul_c<8, false, 16, 4>,
-        (const void*)k_fft_z_mul_c<4, false, 16, 4>, (const void*)k_fft_z_mul_c<2, false, 16, 4>};
-    for (const void* k : zf) {
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (e != cudaSuccess) return e;
-    }
-  }
-  if constexpr (std::is_same<T, float>::value) {
-    const void* yf[] = {
-        (const void*)k_fft_y_c<8, false, 16, 8>, (const void*)k_fft_y_c<16, false, 16, 8>,
-        (const void*)k_fft_y_c<32, false, 16, 8>, (const void*)k_fft_y_c<8, true, 16, 8>,
-        (const void*)k_fft_y_c<16, true, 16, 8>, (const void*)k_fft_y_c<32, true, 16, 8>,
-        (const void*)k_fft_y_c<8, false, 16, 4>, (const void*)k_fft_y_c<16, false, 16, 4>,
-        (const void*)k_fft_y_c<32, false, 16, 4>, (const void*)k_fft_y_c<8, true, 16, 4>,
-        (const void*)k_fft_y_c<16, true, 16, 4>, (const void*)k_fft_y_c<32, true, 16, 4>};
-    for (const void* k : yf) {
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (e != cudaSuccess) return e;
-    }
+    e = configure_fixed_kernels();
+    if (e != cudaSuccess) return e;
   }
   if constexpr (sizeof(T) == 8) {  // magnetic near field (FP64 only)
     const void* zc[] = {(const void*)k_fft_z_mul<T, 16, true, true>,

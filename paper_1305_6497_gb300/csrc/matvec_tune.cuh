@@ -130,8 +130,8 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
           for (int th : {64, 96, 128, 192, 256}) {
             MatvecLaunch c = best;
             fill_z<T>(op, c, tile, pad, gs != 0);
-            // the compile-time z kernel sets its own pitch: one pad value is enough
-            if (zc_applies<T, false>(op) && pad != 0) continue;
+            // a compiled-plan z kernel sets its own pitch: one pad value is enough
+            if (std::is_same<T, float>::value && z_fixed_plan(op.pz) && pad != 0) continue;
             c.z_threads = th;
             if (c.z_smem > kMax) continue;
             const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);

@@ -31,7 +31,8 @@ def test_autotune_keeps_results(tmp_path, monkeypatch):
 
 @pytest.mark.parametrize("threads", [32, 64, 128, 256])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("shape", [(13, 18, 22), (13, 32, 32), (32, 18, 64), (64, 7, 9)])
+@pytest.mark.parametrize("shape", [(13, 18, 22), (13, 32, 32), (32, 18, 64), (64, 7, 9),
+                                   (48, 96, 9), (9, 7, 144), (5, 6, 256)])
 def test_every_thread_count_gives_the_same_product(threads, precision, shape):
     """Explicit schedules with every thread count the tuner may pick (and odd
     line/tile counts) must reproduce the default schedule's product; box sides

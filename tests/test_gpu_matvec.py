@@ -65,6 +65,14 @@ CASES = [
     ("ell_32x7x5", lambda: tg.ellipsoid(32, 7, 5), [1.5 + 0.1j]),
     ("ell_64x6x5", lambda: tg.ellipsoid(64, 6, 5), [1.33 + 0.05j]),
     ("ell_63x5x6", lambda: tg.ellipsoid(63, 5, 6), [1.7 + 0.2j]),
+    # three- and four-stage compiled plans: 512 = 16x8x4 on each axis, and the
+    # ellipsoid grid's 96 = 8x4x3 (x), 192 = 16x4x3 (y), 288 = 8x4x3x3 (z)
+    ("ell_256x5x4", lambda: tg.ellipsoid(256, 5, 4), [1.33 + 0.01j]),
+    ("ell_4x256x5", lambda: tg.ellipsoid(4, 256, 5), [1.33 + 0.01j]),
+    ("ell_5x4x256", lambda: tg.ellipsoid(5, 4, 256), [1.33 + 0.01j]),
+    ("ell_48x7x5", lambda: tg.ellipsoid(48, 7, 5), [1.7 + 0.1j]),
+    ("ell_5x96x6", lambda: tg.ellipsoid(5, 96, 6), [1.7 + 0.1j]),
+    ("ell_6x5x144", lambda: tg.ellipsoid(6, 5, 144), [1.7 + 0.1j]),
 ]
 
 
