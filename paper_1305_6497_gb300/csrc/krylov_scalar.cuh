@@ -13,9 +13,11 @@
 namespace dda {
 
 __device__ __forceinline__ bool ks_finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+// a / b with one FP64 reciprocal (divisions are long dependency chains on
+// this part's FP64 pipe, and these steps sit on the solve's critical path)
 __device__ __forceinline__ double2 ks_cdiv(double2 a, double2 b) {
-  const double d = b.x * b.x + b.y * b.y;
-  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+  const double inv = 1.0 / (b.x * b.x + b.y * b.y);
+  return make_double2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
 }
 __device__ __forceinline__ double2 ks_cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -35,8 +37,13 @@ __device__ inline void step_alpha(const double* tot, KState& k, int* active_r) {
 // tot[0..1] = <t, s>, tot[2] = <t, t>
 __device__ inline void step_omega(const double* tot, KState& k) {
   const double tt = tot[2];
-  if (tt > 0.0 && isfinite(tt)) k.omega = make_double2(tot[0] / tt, tot[1] / tt);
-  else k.omega = make_double2(0.0, 0.0);
+  if (tt > 0.0 && isfinite(tt)) {
+    const double inv = 1.0 / tt;
+    k.omega = make_double2(tot[0] * inv, tot[1] * inv);
+  }
+  else {
+    k.omega = make_double2(0.0, 0.0);
+  }
 }
 
 // tot[0..1] = <rhat, r>, tot[2] = ||r||^2
@@ -54,7 +61,8 @@ __device__ inline void step_rho(const double* tot, KState& k, int* active_r) {
   if (k.iters >= k.max_iter) {
     k.status = KS_NOCONV; *active_r = 0; return;
   }
-  k.beta = ks_cmul(ks_cdiv(rho_new, k.rho), ks_cdiv(k.alpha, k.omega));
+  // beta = (rho' / rho)(alpha / omega) as one quotient
+  k.beta = ks_cdiv(ks_cmul(rho_new, k.alpha), ks_cmul(k.rho, k.omega));
   k.rho_old = k.rho;
   k.rho = rho_new;
 }
@@ -114,9 +122,11 @@ __device__ inline void step_qmr(const double* tot, KState& k, int* active_r) {
 template <int NV>
 __device__ void fold_scalar_step(const double* partials, const FoldArgs& f) {
   __shared__ int last;
-  __threadfence();  // the partials thread 0 wrote, before its ticket
-  __syncthreads();
   if (threadIdx.x == 0) {
+    // thread 0 wrote the block's partials: make them visible before its ticket
+    // (the other threads wrote nothing the last block reads, and a fence in
+    // every thread would hold each block until all of its stores drained)
+    __threadfence();
     const unsigned ticket = atomicAdd(&f.counter[blockIdx.y], 1u);
     last = ticket == gridDim.x - 1;
   }
