@@ -153,23 +153,7 @@ cudaError_t launch_bicg_init(int64_t n, int R, const cplx_t<T>* b, const cplx_t<
                              double* partials, cudaStream_t st);
 cudaError_t launch_state_init(int R, int nblk, const double* partials, KState* ks,
                               int* active, double tol, int max_iter, cudaStream_t st);
-template <typename T>
-cudaError_t launch_update_p(int64_t n, int R, const cplx_t<T>* r, cplx_t<T>* p,
-                            const cplx_t<T>* v, const KState* ks, const int* active,
-                            cudaStream_t st);
-template <typename T>
-cudaError_t launch_dot_rhat_v(int64_t n, int R, const cplx_t<T>* rhat, const cplx_t<T>* v,
-                              double* partials, const int* active, cudaStream_t st);
 cudaError_t launch_scalar_alpha(int R, int nblk, const double* partials, KState* ks,
-                                int* active, cudaStream_t st);
-template <typename T>
-cudaError_t launch_update_s(int64_t n, int R, const cplx_t<T>* r, const cplx_t<T>* v,
-                            cplx_t<T>* s, const KState* ks, const int* active,
-                            cudaStream_t st);
-template <typename T>
-cudaError_t launch_dot_ts(int64_t n, int R, const cplx_t<T>* t, const cplx_t<T>* s,
-                          double* partials, const int* active, cudaStream_t st);
-cudaError_t launch_scalar_omega(int R, int nblk, const double* partials, KState* ks,
                                 int* active, cudaStream_t st);
 template <typename T>
 cudaError_t launch_update_xr(int64_t n, int R, cplx_t<T>* x, cplx_t<T>* r,
@@ -184,10 +168,11 @@ cudaError_t launch_scalar_rho(int R, int nblk, const double* partials, KState* k
 //               ||b||^2, r^T r ([R][nblk][4])
 //  qmr_state:   tau = ||r||, theta = 0, rho = r^T r, beta = 0, no pending update;
 //               |r^T r| <= rho_floor ||r||^2 (now or later) is a breakdown
-//  qmr_sigma:   alpha = rho / (q^T t) from the matvec partials
-//  qmr_update_r: r -= alpha t; partials of ||r||^2, r^T r ([R][nblk][4])
-//  qmr_scalar:  rotation, pending update coefficients, convergence on the
-//               quasi-residual bound tau sqrt(k+1) <= tol ||b||, beta
+//  (alpha = rho / (q^T t) runs in the last block of the matvec, FOLD_QSIGMA)
+//  qmr_update_r: r -= alpha t; partials of ||r||^2, r^T r ([R][nblk][4]); its
+//               last block runs the rotation, pending update coefficients,
+//               convergence on the quasi-residual bound tau sqrt(k+1) <= tol
+//               ||b|| and beta (FOLD_QMR)
 //  qmr_flush:   apply the last pending update (all RHS)
 template <typename T>
 cudaError_t launch_qmr_init(int64_t n, int R, const cplx_t<T>* b, const cplx_t<T>* ax,
@@ -196,14 +181,10 @@ cudaError_t launch_qmr_init(int64_t n, int R, const cplx_t<T>* b, const cplx_t<T
 cudaError_t launch_qmr_state(int R, int nblk, const double* partials, KState* ks,
                              int* active, double tol, int max_iter, double rho_floor,
                              cudaStream_t st);
-cudaError_t launch_qmr_sigma(int R, int nblk, const double* partials, KState* ks,
-                             int* active, cudaStream_t st);
 template <typename T>
 cudaError_t launch_qmr_update_r(int64_t n, int R, cplx_t<T>* r, const cplx_t<T>* t,
                                 double* partials, const KState* ks, const int* active,
                                 cudaStream_t st, FoldArgs fold = FoldArgs());
-cudaError_t launch_qmr_scalar(int R, int nblk, const double* partials, KState* ks,
-                              int* active, cudaStream_t st);
 template <typename T>
 cudaError_t launch_qmr_flush(int64_t n, int R, cplx_t<T>* x, cplx_t<T>* d,
                              const cplx_t<T>* q, const KState* ks, cudaStream_t st);

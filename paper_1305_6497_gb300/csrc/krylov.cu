@@ -22,10 +22,6 @@ int reduce_blocks(int64_t n) {
 }
 
 __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-  const double d = b.x * b.x + b.y * b.y;
-  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
-}
 
 template <typename C> __device__ __forceinline__ C from_d2(double2 a) {
   return mk<C>(a.x, a.y);
@@ -131,58 +127,7 @@ cudaError_t launch_state_init(int R, int nblk, const double* partials, KState* k
   return cudaGetLastError();
 }
 
-template <typename T>
-__global__ void k_update_p(int64_t n, const cplx_t<T>* __restrict__ r, cplx_t<T>* __restrict__ p,
-                           const cplx_t<T>* __restrict__ v, const KState* __restrict__ ks,
-                           const int* __restrict__ active) {
-  using C = cplx_t<T>;
-  const int rr = blockIdx.y;
-  if (!active[rr]) return;
-  const C beta = from_d2<C>(ks[rr].beta);
-  const C omega = from_d2<C>(ks[rr].omega);
-  const int64_t off = (int64_t)rr * n;
-  GRID_LOOP(i, n) {
-    const C pv = csub(p[off + i], cmul(omega, v[off + i]));
-    p[off + i] = cadd(r[off + i], cmul(beta, pv));
-  }
-}
 
-template <typename T>
-cudaError_t launch_update_p(int64_t n, int R, const cplx_t<T>* r, cplx_t<T>* p,
-                            const cplx_t<T>* v, const KState* ks, const int* active,
-                            cudaStream_t st) {
-  dim3 g(reduce_blocks(n), R);
-  k_update_p<T><<<g, kThreads, 0, st>>>(n, r, p, v, ks, active);
-  note_launch();
-  return cudaGetLastError();
-}
-
-template <typename T>
-__global__ void k_dot_rhat_v(int64_t n, const cplx_t<T>* __restrict__ rhat,
-                             const cplx_t<T>* __restrict__ v, double* partials,
-                             const int* __restrict__ active) {
-  using C = cplx_t<T>;
-  const int rr = blockIdx.y;
-  if (!active[rr]) return;
-  const int64_t off = (int64_t)rr * n;
-  ChunkAcc<T, 2> acc;
-  GRID_LOOP(i, n) {
-    const C a = rhat[off + i], b = v[off + i];
-    acc.add(0, a.x * b.x + a.y * b.y);
-    acc.add(1, a.x * b.y - a.y * b.x);
-    acc.step();
-  }
-  acc.template write<2>(partials);
-}
-
-template <typename T>
-cudaError_t launch_dot_rhat_v(int64_t n, int R, const cplx_t<T>* rhat, const cplx_t<T>* v,
-                              double* partials, const int* active, cudaStream_t st) {
-  dim3 g(reduce_blocks(n), R);
-  k_dot_rhat_v<T><<<g, kThreads, 0, st>>>(n, rhat, v, partials, active);
-  note_launch();
-  return cudaGetLastError();
-}
 
 __global__ void k_scalar_alpha(int nblk, const double* partials, KState* ks, int* active) {
   const int r = blockIdx.x;
@@ -199,70 +144,8 @@ cudaError_t launch_scalar_alpha(int R, int nblk, const double* partials, KState*
   return cudaGetLastError();
 }
 
-template <typename T>
-__global__ void k_update_s(int64_t n, const cplx_t<T>* __restrict__ r,
-                           const cplx_t<T>* __restrict__ v, cplx_t<T>* __restrict__ s,
-                           const KState* __restrict__ ks, const int* __restrict__ active) {
-  using C = cplx_t<T>;
-  const int rr = blockIdx.y;
-  if (!active[rr]) return;
-  const C alpha = from_d2<C>(ks[rr].alpha);
-  const int64_t off = (int64_t)rr * n;
-  GRID_LOOP(i, n) s[off + i] = csub(r[off + i], cmul(alpha, v[off + i]));
-}
 
-template <typename T>
-cudaError_t launch_update_s(int64_t n, int R, const cplx_t<T>* r, const cplx_t<T>* v,
-                            cplx_t<T>* s, const KState* ks, const int* active,
-                            cudaStream_t st) {
-  dim3 g(reduce_blocks(n), R);
-  k_update_s<T><<<g, kThreads, 0, st>>>(n, r, v, s, ks, active);
-  note_launch();
-  return cudaGetLastError();
-}
 
-template <typename T>
-__global__ void k_dot_ts(int64_t n, const cplx_t<T>* __restrict__ t,
-                         const cplx_t<T>* __restrict__ s, double* partials,
-                         const int* __restrict__ active) {
-  using C = cplx_t<T>;
-  const int rr = blockIdx.y;
-  if (!active[rr]) return;
-  const int64_t off = (int64_t)rr * n;
-  ChunkAcc<T, 4> acc;
-  GRID_LOOP(i, n) {
-    const C a = t[off + i], b = s[off + i];
-    acc.add(0, a.x * b.x + a.y * b.y);
-    acc.add(1, a.x * b.y - a.y * b.x);
-    acc.add(2, a.x * a.x + a.y * a.y);
-    acc.step();
-  }
-  acc.template write<4>(partials);
-}
-
-template <typename T>
-cudaError_t launch_dot_ts(int64_t n, int R, const cplx_t<T>* t, const cplx_t<T>* s,
-                          double* partials, const int* active, cudaStream_t st) {
-  dim3 g(reduce_blocks(n), R);
-  k_dot_ts<T><<<g, kThreads, 0, st>>>(n, t, s, partials, active);
-  note_launch();
-  return cudaGetLastError();
-}
-
-__global__ void k_scalar_omega(int nblk, const double* partials, KState* ks, int* active) {
-  const int r = blockIdx.x;
-  if (!active[r]) return;
-  double tot[4];
-  sum_partials<4>(partials, nblk, r, tot);
-  if (threadIdx.x == 0) step_omega(tot, ks[r]);
-}
-
-cudaError_t launch_scalar_omega(int R, int nblk, const double* partials, KState* ks,
-                                int* active, cudaStream_t st) {
-  k_scalar_omega<<<R, kThreads, 0, st>>>(nblk, partials, ks, active);
-  note_launch();
-  return cudaGetLastError();
-}
 
 template <typename T>
 __global__ void k_update_xr(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __restrict__ r,
@@ -426,20 +309,6 @@ cudaError_t launch_qmr_state(int R, int nblk, const double* partials, KState* ks
   return cudaGetLastError();
 }
 
-__global__ void k_qmr_sigma(int nblk, const double* partials, KState* ks, int* active) {
-  const int r = blockIdx.x;
-  if (!active[r]) return;
-  double tot[2];
-  sum_partials<2>(partials, nblk, r, tot);
-  if (threadIdx.x == 0) step_qmr_sigma(tot, ks[r], active + r);
-}
-
-cudaError_t launch_qmr_sigma(int R, int nblk, const double* partials, KState* ks,
-                             int* active, cudaStream_t st) {
-  k_qmr_sigma<<<R, kThreads, 0, st>>>(nblk, partials, ks, active);
-  note_launch();
-  return cudaGetLastError();
-}
 
 template <typename T>
 __global__ void k_qmr_update_r(int64_t n, cplx_t<T>* __restrict__ r,
@@ -490,20 +359,6 @@ cudaError_t launch_qmr_update_r(int64_t n, int R, cplx_t<T>* r, const cplx_t<T>*
   return cudaGetLastError();
 }
 
-__global__ void k_qmr_scalar(int nblk, const double* partials, KState* ks, int* active) {
-  const int r = blockIdx.x;
-  if (!active[r]) return;
-  double tot[4];
-  sum_partials<4>(partials, nblk, r, tot);
-  if (threadIdx.x == 0) step_qmr(tot, ks[r], active + r);
-}
-
-cudaError_t launch_qmr_scalar(int R, int nblk, const double* partials, KState* ks,
-                              int* active, cudaStream_t st) {
-  k_qmr_scalar<<<R, kThreads, 0, st>>>(nblk, partials, ks, active);
-  note_launch();
-  return cudaGetLastError();
-}
 
 template <typename T>
 __global__ void k_qmr_flush(int64_t n, cplx_t<T>* __restrict__ x, cplx_t<T>* __restrict__ d,
@@ -709,17 +564,6 @@ cudaError_t launch_box_to_sites(int64_t N, int64_t nbox, int R, const int64_t* s
   template cudaError_t launch_bicg_init<T>(int64_t, int, const cplx_t<T>*, const cplx_t<T>*, \
                                            cplx_t<T>*, cplx_t<T>*, cplx_t<T>*, cplx_t<T>*,   \
                                            double*, cudaStream_t);                           \
-  template cudaError_t launch_update_p<T>(int64_t, int, const cplx_t<T>*, cplx_t<T>*,        \
-                                          const cplx_t<T>*, const KState*, const int*,       \
-                                          cudaStream_t);                                     \
-  template cudaError_t launch_dot_rhat_v<T>(int64_t, int, const cplx_t<T>*,                  \
-                                            const cplx_t<T>*, double*, const int*,           \
-                                            cudaStream_t);                                   \
-  template cudaError_t launch_update_s<T>(int64_t, int, const cplx_t<T>*, const cplx_t<T>*,  \
-                                          cplx_t<T>*, const KState*, const int*,             \
-                                          cudaStream_t);                                     \
-  template cudaError_t launch_dot_ts<T>(int64_t, int, const cplx_t<T>*, const cplx_t<T>*,    \
-                                        double*, const int*, cudaStream_t);                  \
   template cudaError_t launch_update_xr<T>(int64_t, int, cplx_t<T>*, cplx_t<T>*,             \
                                            const cplx_t<T>*, const cplx_t<T>*,               \
                                            const cplx_t<T>*, const cplx_t<T>*, double*,      \
