@@ -1997,9 +1997,13 @@ dda_status dda_set_schedule(dda_target* t, int precision, const int* in8) {
       zp < 3 * zt || zp > 3 * zt + 8 || (zg != 0 && zg != 1))
     return fail(DDA_ERR_INVALID_ARG, "schedule: x lines 1..64, y tile 1..64, z tile 2/4/8/16, "
                                      "z pitch 3*tile..3*tile+8, z staging 0/1");
-  for (int i = 5; i < 8; ++i)
-    if (in8[i] < 32 || in8[i] > 256 || in8[i] % 32)
-      return fail(DDA_ERR_INVALID_ARG, "schedule: threads per CTA must be 32..256, multiple of 32");
+  for (int i = 5; i < 8; ++i) {
+    // the FP32 z pass of a compiled radix plan takes up to 384 threads
+    const int tmax = (i == 7 && !f64 && z_fixed_applies(t->pz, zt)) ? 384 : 256;
+    if (in8[i] < 32 || in8[i] > tmax || in8[i] % 32)
+      return fail(DDA_ERR_INVALID_ARG, "schedule: threads per CTA must be a multiple of 32 in "
+                                       "32..256 (FP32 z pass of a compiled plan: ..384)");
+  }
   const size_t xinv = (size_t)t->Lx * (xl + 1) * cs + (size_t)2 * xl * t->nx * cs;
   const size_t ysm = (size_t)t->Ly * yt * cs;
   const size_t zsm = (((size_t)t->Lz * zp * cs + 15) & ~(size_t)15) +

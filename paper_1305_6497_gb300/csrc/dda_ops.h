@@ -90,6 +90,10 @@ struct KState {
 
 enum { KS_RUN = 0, KS_CONV = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3 };
 
+// True when the FP32 z pass of this axis plan and z tile runs a compiled-plan
+// kernel (matvec_fixed.cu), which takes up to 384 threads per CTA.
+bool z_fixed_applies(const AxisPlan& P, int tile);
+
 // A vector pass that finishes one of the Krylov scalar steps in its last
 // block (instead of a separate one-block kernel): `counter` holds one word per
 // RHS, zero between passes, counting the blocks that have written partials.

@@ -74,6 +74,12 @@ bool z_fixed_plan(const AxisPlan& a) {
   return dispatch_plan(a, ZPlans{}, [](auto) {});
 }
 
+bool z_fixed_applies(const AxisPlan& a, int tile) {
+  bool ok = false;
+  dispatch_plan(a, ZPlans{}, [&](auto plan) { ok = z_tile_compiled<decltype(plan)>(tile); });
+  return ok;
+}
+
 bool launch_z_fixed(const OpView<float>& op, const MatvecLaunch& L, int R, float2* scratch,
                     const int* active, cudaStream_t st) {
   bool done = false;

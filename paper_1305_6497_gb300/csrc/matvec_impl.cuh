@@ -567,8 +567,11 @@ k_fft_z_mul(OpView<T> op, cplx_t<T>* __restrict__ buf, int ps, const int* __rest
 // --------------------------------------------------------------------------
 template <int TILE> constexpr int zc_pitch() { return 3 * TILE + (TILE * 8 < 128 ? 1 : 0); }
 
+// Up to 384 threads (the same 85-register budget as 3 x 256): long lines
+// (three or more stages) stage a Ghat tile big enough to leave only two CTAs
+// per SM, and more threads per CTA keep the stages' butterfly counts busy.
 template <int TILE, bool GS, class P>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(384, 2)
 k_fft_z_mul_p(OpView<float> op, float2* __restrict__ buf, const int* __restrict__ active) {
   using C = float2;
   constexpr int L = P::L, NS = P::NS, R0 = P::radix(0), S0 = P::span(0);

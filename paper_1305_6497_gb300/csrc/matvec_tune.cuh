@@ -127,11 +127,14 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
     for (int tile : {2, 4, 8, 16})
       for (int gs = 0; gs < 2; ++gs)
         for (int pad = 0; pad < 4; ++pad)
-          for (int th : {64, 96, 128, 192, 256}) {
+          for (int th : {64, 96, 128, 192, 256, 384}) {
             MatvecLaunch c = best;
             fill_z<T>(op, c, tile, pad, gs != 0);
             // a compiled-plan z kernel sets its own pitch: one pad value is enough
             if (std::is_same<T, float>::value && z_fixed_plan(op.pz) && pad != 0) continue;
+            // 384 threads: compiled-plan z kernels only
+            if (th > 256 && !(std::is_same<T, float>::value && z_fixed_applies(op.pz, tile)))
+              continue;
             c.z_threads = th;
             if (c.z_smem > kMax) continue;
             const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);

@@ -64,3 +64,31 @@ def test_every_thread_count_gives_the_same_product(threads, precision, shape):
         t.set_schedule(dict(x_lines=8, y_tile=8, z_tile=8, z_pitch=24, z_stage_ghat=0,
                             x_threads=48, y_threads=64, z_threads=64), precision)
     t.close()
+
+
+@pytest.mark.parametrize("shape", [(13, 18, 64), (9, 7, 256)])
+def test_compiled_z_pass_takes_384_threads(shape):
+    """The FP32 z pass of a compiled radix plan accepts CTAs of 384 threads
+    (same product); other z tiles and the FP64 pass keep the 256 limit."""
+    from paper_1305_6497_gb300 import binding as B
+    occ, comp = tg.ellipsoid(*shape)
+    flat, pos = O.site_positions(occ)
+    x = O.box_to_sites(W.random_polarization(occ, 5)[0], flat)
+    t = B.Target(occ, comp, [1.5 + 0.1j], method="LDR")
+    kh, e = [1.0, 0, 0], [0, 1.0, 0]
+    y0 = t.matvec(0.4, x, kh, e, "fp32")
+    for zt, gs in ((4, 1), (8, 0)):
+        t.set_schedule(dict(x_lines=16, y_tile=16, z_tile=zt, z_pitch=3 * zt + 1,
+                            z_stage_ghat=gs, x_threads=128, y_threads=128, z_threads=384),
+                       "fp32")
+        assert t.schedule("fp32")["z_threads"] == 384
+        y1 = t.matvec(0.4, x, kh, e, "fp32")
+        assert np.abs(y1 - y0).max() <= 1e-6 * np.abs(y0).max()
+    with pytest.raises(B.DDAError):   # a 3-stage plan has no compiled 2-column tile
+        if shape[2] == 256:
+            t.set_schedule(dict(x_lines=16, y_tile=16, z_tile=2, z_pitch=7, z_stage_ghat=0,
+                                x_threads=128, y_threads=128, z_threads=384), "fp32")
+        else:
+            t.set_schedule(dict(x_lines=16, y_tile=16, z_tile=8, z_pitch=25, z_stage_ghat=0,
+                                x_threads=128, y_threads=128, z_threads=384), "fp64")
+    t.close()
