@@ -234,6 +234,23 @@ def run_reference(args, rank, world):
     return 0
 
 
+def aggregate_over_ranks(iters, dev_s, wall_s, world):
+    """Whole-job totals of N independent replicas: iterations summed over the
+    ranks, device and wall time the maximum over the ranks (every rank has
+    passed the same barriers around its timed steps)."""
+    tot = {"iters": float(iters), "dev_s": float(dev_s), "wall_s": float(wall_s)}
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        v = torch.tensor([tot["iters"], tot["dev_s"], tot["wall_s"]], dtype=torch.float64)
+        s_it = v.clone()
+        dist.all_reduce(s_it, op=dist.ReduceOp.SUM)
+        m_t = v.clone()
+        dist.all_reduce(m_t, op=dist.ReduceOp.MAX)
+        tot = {"iters": s_it[0].item(), "dev_s": m_t[1].item(), "wall_s": m_t[2].item()}
+    return tot
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -372,20 +389,12 @@ def run_gpu(args, rank, world, local_rank):
                   for p in B.PASSES})
 
     # ---- aggregate over ranks (replicas) ----
-    tot = {"iters": float(sum(iters)), "dev_s": dev_s, "wall_s": t_wall}
-    if world > 1:
-        import torch.distributed as dist
-        v = torch.tensor([tot["iters"], dev_s, t_wall], dtype=torch.float64)
-        s_it = v.clone()
-        dist.all_reduce(s_it, op=dist.ReduceOp.SUM)
-        m_t = v.clone()
-        dist.all_reduce(m_t, op=dist.ReduceOp.MAX)
-        tot = {"iters": s_it[0].item(), "dev_s": m_t[1].item(), "wall_s": m_t[2].item()}
+    tot = aggregate_over_ranks(float(sum(iters)), dev_s, t_wall, world)
     if rank != 0:
         return 0
     value = N * tot["iters"] / tot["dev_s"]
     cpu = None
-    if world == 1 or rank == 0:
+    if world == 1:  # the host-core oracle baseline is taken at one GPU only
         v_cpu, dt_cpu, setup_cpu, it_cpu, c_cpu, sample = oracle_sample(w, 3)
         cpu = {"value": v_cpu, "unit": UNIT, "cores": round(c_cpu, 2), "kind": "oracle",
                "sample": sample + "; cores = process CPU time / wall time"}
