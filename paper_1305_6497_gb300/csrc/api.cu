@@ -2006,7 +2006,10 @@ dda_status dda_set_schedule(dda_target* t, int precision, const int* in8) {
   }
   const size_t xinv = (size_t)t->Lx * (xl + 1) * cs + (size_t)2 * xl * t->nx * cs;
   const size_t ysm = (size_t)t->Ly * yt * cs;
-  const size_t zsm = (((size_t)t->Lz * zp * cs + 15) & ~(size_t)15) +
+  // a compiled-plan z kernel uses its own pitch, 3 tile (+1 below 128 B rows)
+  const int zpc = (!f64 && z_fixed_applies(t->pz, zt))
+                      ? std::max(zp, 3 * zt + (zt * (int)cs < 128 ? 1 : 0)) : zp;
+  const size_t zsm = (((size_t)t->Lz * zpc * cs + 15) & ~(size_t)15) +
                      (zg ? (size_t)6 * (t->Lz / 2 + 1) * zt * cs : 0);
   if (xinv > 200 * 1024 || ysm > 200 * 1024 || zsm > 200 * 1024)
     return fail(DDA_ERR_INVALID_ARG, "schedule: a pass would need more than 200 KB of shared memory");

@@ -137,6 +137,13 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
               continue;
             c.z_threads = th;
             if (c.z_smem > kMax) continue;
+            if (std::is_same<T, float>::value && z_fixed_applies(op.pz, tile)) {
+              // the compiled kernel's own pitch (see zc_pitch)
+              const int pc = 3 * tile + (tile * 8 < 128 ? 1 : 0);
+              const size_t zc = (((size_t)op.Lz * pc * 8 + 15) & ~(size_t)15) +
+                                (gs ? (size_t)6 * op.Hz * tile * 8 : 0);
+              if (zc > kMax) continue;
+            }
             const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);
             if (tt < bt) { bt = tt; best = c; }
           }
