@@ -267,9 +267,11 @@ dda_status dda_target_schedule(const dda_target* t, int precision, int* out8);
 /* Set the schedule of DDA_PREC_FP64 or (otherwise) FP32 explicitly, in the
  * layout dda_target_schedule returns (for instance one saved from an earlier
  * dda_autotune).  Values outside x lines 1..64, y tile 1..64, z tile 2/4/8/16,
- * z pitch 3*tile..3*tile+8, z staging 0/1, threads 32..256 (multiples of 32),
- * or needing more than 200 KB of shared memory: DDA_ERR_INVALID_ARG.  The
- * schedule changes tiling and launch shape only, not the arithmetic. */
+ * z pitch 3*tile..3*tile+8, z staging 0/1, threads 32..256 (multiples of 32;
+ * up to 384 for the FP32 z pass when the target's z length has a compiled
+ * radix plan for that tile), or needing more than 200 KB of shared memory:
+ * DDA_ERR_INVALID_ARG.  The schedule changes tiling and launch shape only, not
+ * the arithmetic. */
 dda_status dda_set_schedule(dda_target* t, int precision, const int* in8);
 
 /* Kernels launched by this library since the process started (all threads). */
