@@ -1,0 +1,106 @@
+"""More Krylov methods for the oracle -- TEST INFRASTRUCTURE ONLY.
+
+Plain FP64 numpy restatements of two more of the guide's iterative options
+(Sec. "Choice of Iterative Algorithm"), each written from its published
+definition, so that tests can compare the GPU iterates with them step by step.
+Only the tests may import this module; the CUDA library never does.
+
+  gpbicg -- GPBi-CG (Zhang 1997), the guide's GPBICG option
+  cgnr   -- conjugate gradients on the normal equations A^H A x = A^H b
+            (Petravic & Kuo-Petravic 1979), the guide's PETRKP option
+
+Both take the matrix as a function v -> A v.  <a, b> = sum conj(a) b.
+"""
+import numpy as np
+
+
+def _dot(a, b):
+    return np.vdot(a, b)
+
+
+def gpbicg(matvec, b, maxiter, tol=0.0):
+    """GPBi-CG from x0 = 0 with shadow vector rt = r0 = b.
+
+    Iteration n (t, u, z, A t, A p start at zero and beta at 0):
+      p = r + beta (p - u);  w = A t_{n-1} + beta A p_{n-1}
+      alpha = <rt, r> / <rt, A p>
+      y = t_{n-1} - r - alpha w + alpha A p;  t = r - alpha A p
+      (zeta, eta) minimise ||t - zeta A t - eta y|| (eta = 0 at n = 0):
+        the 2x2 normal equations [<At,At> <At,y>; <y,At> <y,y>] (zeta, eta)
+        = (<At,t>, <y,t>)
+      u = zeta A p + eta (t_{n-1} - r + beta u);  z = zeta r + eta z - alpha u
+      x = x + alpha p + z;  r = t - eta y - zeta A t
+      beta = (alpha / zeta) <rt, r_new> / <rt, r>
+    Stops after `maxiter` iterations or when ||r|| <= tol ||b||.
+    Returns (x, iterations)."""
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b)
+    r = b.copy()
+    rt = r.copy()
+    p = np.zeros_like(b)
+    u = np.zeros_like(b)
+    z = np.zeros_like(b)
+    t_old = np.zeros_like(b)
+    at_old = np.zeros_like(b)
+    ap_old = np.zeros_like(b)
+    beta = 0.0
+    rho = _dot(rt, r)
+    bn = np.linalg.norm(b)
+    n = 0
+    while n < maxiter and np.linalg.norm(r) > tol * bn:
+        p = r + beta * (p - u)
+        w = at_old + beta * ap_old
+        ap = matvec(p)
+        alpha = rho / _dot(rt, ap)
+        y = t_old - r - alpha * w + alpha * ap
+        t = r - alpha * ap
+        at = matvec(t)
+        aa = _dot(at, at).real
+        if n == 0:
+            zeta, eta = _dot(at, t) / aa, 0.0
+        else:
+            yy = _dot(y, y).real
+            ay = _dot(at, y)
+            m = np.array([[aa, ay], [np.conj(ay), yy]])
+            zeta, eta = np.linalg.solve(m, np.array([_dot(at, t), _dot(y, t)]))
+        u = zeta * ap + eta * (t_old - r + beta * u)
+        z = zeta * r + eta * z - alpha * u
+        x = x + alpha * p + z
+        r_new = t - eta * y - zeta * at
+        rho_new = _dot(rt, r_new)
+        beta = (alpha / zeta) * rho_new / rho
+        r, rho = r_new, rho_new
+        t_old, at_old, ap_old = t, at, ap
+        n += 1
+    return x, n
+
+
+def cgnr(matvec, b, maxiter, tol=0.0):
+    """Conjugate gradients on A^H A x = A^H b from x0 = 0, for complex-symmetric
+    A (A^T = A), so that A^H v = conj(A conj(v)):
+      r = b;  p = A^H r;  gamma = ||A^H r||^2
+      w = A p;  alpha = gamma / ||w||^2;  x += alpha p;  r -= alpha w
+      s = A^H r;  beta = ||s||^2 / gamma;  gamma = ||s||^2;  p = s + beta p
+    Stops after `maxiter` iterations or when ||r|| <= tol ||b||.
+    Returns (x, iterations)."""
+    b = np.asarray(b, dtype=np.complex128)
+    ah = lambda v: np.conj(matvec(np.conj(v)))
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = ah(r)
+    gamma = _dot(p, p).real
+    bn = np.linalg.norm(b)
+    n = 0
+    while n < maxiter and np.linalg.norm(r) > tol * bn:
+        w = matvec(p)
+        alpha = gamma / _dot(w, w).real
+        x = x + alpha * p
+        r = r - alpha * w
+        n += 1
+        if np.linalg.norm(r) <= tol * bn:
+            break
+        s = ah(r)
+        g_new = _dot(s, s).real
+        p = s + (g_new / gamma) * p
+        gamma = g_new
+    return x, n

@@ -395,3 +395,34 @@ def test_gpbicg_batched_circular_and_fallback(B):
         assert q["status"] == B.DDA_OK
         assert np.allclose(q["Qext"], b["Qext"], rtol=1e-8)
     t.close()
+
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_gpbicg_iterates_match_oracle(B, k):
+    """The GPU's k-th GPBi-CG iterate (FP64) equals the oracle's (oracle/krylov.py),
+    the same recurrences from the same start, up to FFT rounding."""
+    from oracle import krylov as K
+    w = W.small_ellipsoid(6, 7, 8, m=1.5 + 0.1j, kd=0.4, method="LDR")
+    E, mv = _linear_system(w)
+    xo, n = K.gpbicg(mv, E.reshape(-1), maxiter=k)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    g = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=1, tol=1e-14, max_iter=k,
+                precision="fp64", solver="gpbicg")
+    assert n == k and g["iters"][0] == k
+    assert np.abs(g["P"][0].reshape(-1) - xo).max() <= 1e-9 * np.abs(xo).max()
+    t.close()
+
+
+@pytest.mark.parametrize("k", [3, 8])
+def test_petrkp_iterates_match_oracle(B, k):
+    """The GPU's k-th normal-equation CG iterate (FP64) equals the oracle's."""
+    from oracle import krylov as K
+    w = W.small_ellipsoid(6, 7, 8, m=1.5 + 0.1j, kd=0.4, method="LDR")
+    E, mv = _linear_system(w)
+    xo, n = K.cgnr(mv, E.reshape(-1), maxiter=k)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    g = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=1, tol=1e-14, max_iter=k,
+                precision="fp64", solver="petrkp")
+    assert n == k and g["iters"][0] == k
+    assert np.abs(g["P"][0].reshape(-1) - xo).max() <= 1e-9 * np.abs(xo).max()
+    t.close()
