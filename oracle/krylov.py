@@ -1,15 +1,17 @@
 """More Krylov methods for the oracle -- TEST INFRASTRUCTURE ONLY.
 
-Plain FP64 numpy restatements of two more of the guide's iterative options
+Plain FP64 numpy restatements of three more of the guide's iterative options
 (Sec. "Choice of Iterative Algorithm"), each written from its published
 definition, so that tests can compare the GPU iterates with them step by step.
 Only the tests may import this module; the CUDA library never does.
 
+  qmr_sym -- QMR for complex-symmetric A (Freund 1992; coupled two-term
+            recurrences, Freund & Nachtigal 1994), the guide's QMRCCG option
   gpbicg -- GPBi-CG (Zhang 1997), the guide's GPBICG option
   cgnr   -- conjugate gradients on the normal equations A^H A x = A^H b
             (Petravic & Kuo-Petravic 1979), the guide's PETRKP option
 
-Both take the matrix as a function v -> A v.  <a, b> = sum conj(a) b.
+Each takes the matrix as a function v -> A v.  <a, b> = sum conj(a) b.
 """
 import numpy as np
 
@@ -104,3 +106,45 @@ def cgnr(matvec, b, maxiter, tol=0.0):
         p = s + (g_new / gamma) * p
         gamma = g_new
     return x, n
+
+
+def qmr_sym(matvec, b, maxiter, tol=0.0):
+    """QMR for A = A^T from x0 = 0: the Lanczos process on the bilinear form
+    x^T y, whose vectors are the BiCG residuals, with the quasi-residual
+    minimised by Givens rotations in the coupled two-term form:
+      r = b;  q = r;  tau = ||r||;  theta = 0;  rho = r^T r;  d = 0
+      t = A q;  alpha = rho / (q^T t);  r -= alpha t
+      theta' = ||r|| / tau;  c^2 = 1 / (1 + theta'^2);  tau = tau theta' c
+      d = c^2 theta^2 d + c^2 alpha q;  x += d;  theta = theta'
+      rho' = r^T r;  beta = rho' / rho;  q = r + beta q
+    Stops after `maxiter` iterations or when tau sqrt(k + 1) <= tol ||b||.
+    Returns (x, iterations, taus) with taus[k] the tau after iteration k + 1."""
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b)
+    r = b.copy()
+    q = r.copy()
+    d = np.zeros_like(b)
+    tau = np.linalg.norm(r)
+    theta = 0.0
+    rho = np.sum(r * r)
+    bn = np.linalg.norm(b)
+    taus = []
+    n = 0
+    while n < maxiter:
+        t = matvec(q)
+        alpha = rho / np.sum(q * t)
+        r = r - alpha * t
+        th = np.linalg.norm(r) / tau
+        c2 = 1.0 / (1.0 + th * th)
+        tau = tau * th * np.sqrt(c2)
+        d = c2 * theta * theta * d + c2 * alpha * q
+        x = x + d
+        theta = th
+        n += 1
+        taus.append(tau)
+        if tau * np.sqrt(n + 1) <= tol * bn:
+            break
+        rho_new = np.sum(r * r)
+        q = r + (rho_new / rho) * q
+        rho = rho_new
+    return x, n, taus

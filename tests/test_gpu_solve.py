@@ -426,3 +426,19 @@ def test_petrkp_iterates_match_oracle(B, k):
     assert n == k and g["iters"][0] == k
     assert np.abs(g["P"][0].reshape(-1) - xo).max() <= 1e-9 * np.abs(xo).max()
     t.close()
+
+
+@pytest.mark.parametrize("k", [3, 7])
+def test_qmr_iterates_match_oracle(B, k):
+    """The GPU's k-th QMR iterate (FP64; its pending d/x update flushed) equals
+    the oracle's complex-symmetric QMR."""
+    from oracle import krylov as K
+    w = W.small_ellipsoid(6, 7, 8, m=1.5 + 0.1j, kd=0.4, method="LDR")
+    E, mv = _linear_system(w)
+    xo, n, _ = K.qmr_sym(mv, E.reshape(-1), maxiter=k)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    g = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=1, tol=1e-14, max_iter=k,
+                precision="fp64", solver="qmr")
+    assert n == k and g["iters"][0] == k
+    assert np.abs(g["P"][0].reshape(-1) - xo).max() <= 1e-9 * np.abs(xo).max()
+    t.close()

@@ -68,3 +68,18 @@ def test_cgnr_monotone_residual_and_n_step_termination():
     assert all(r2 <= r1 * (1 + 1e-12) for r1, r2 in zip(res, res[1:]))
     # CG on the n x n normal equations reaches the solution in n steps
     assert res[-1] <= 1e-8 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_qmr_solves_and_keeps_its_residual_bound(seed):
+    """QMR for A = A^T reaches the dense solution, and after every iteration k
+    the true residual stays below tau_k sqrt(k + 1), the bound its stopping
+    rule relies on."""
+    a, b = _system(30, 10.0, seed)
+    mv = lambda v: a @ v
+    x, it, _ = K.qmr_sym(mv, b, maxiter=400, tol=1e-12)
+    ref = np.linalg.solve(a, b)
+    assert np.abs(x - ref).max() <= 1e-9 * np.abs(ref).max()
+    for k in range(1, 25):
+        xk, _, taus = K.qmr_sym(mv, b, maxiter=k)
+        assert np.linalg.norm(b - a @ xk) <= taus[-1] * np.sqrt(k + 1) * (1 + 1e-10)
