@@ -1,12 +1,14 @@
 """More Krylov methods for the oracle -- TEST INFRASTRUCTURE ONLY.
 
-Plain FP64 numpy restatements of three more of the guide's iterative options
+Plain FP64 numpy restatements of four more of the guide's iterative options
 (Sec. "Choice of Iterative Algorithm"), each written from its published
 definition, so that tests can compare the GPU iterates with them step by step.
 Only the tests may import this module; the CUDA library never does.
 
   qmr_sym -- QMR for complex-symmetric A (Freund 1992; coupled two-term
             recurrences, Freund & Nachtigal 1994), the guide's QMRCCG option
+  bicgstab2 -- BiCGstab(l) with l = 2 (Sleijpen & van der Vorst 1993), the
+            guide's PBCGS2 option
   gpbicg -- GPBi-CG (Zhang 1997), the guide's GPBICG option
   cgnr   -- conjugate gradients on the normal equations A^H A x = A^H b
             (Petravic & Kuo-Petravic 1979), the guide's PETRKP option
@@ -20,7 +22,7 @@ def _dot(a, b):
     return np.vdot(a, b)
 
 
-def gpbicg(matvec, b, maxiter, tol=0.0):
+def gpbicg(matvec, b, maxiter, tol=0.0, return_r=False):
     """GPBi-CG from x0 = 0 with shadow vector rt = r0 = b.
 
     Iteration n (t, u, z, A t, A p start at zero and beta at 0):
@@ -34,7 +36,7 @@ def gpbicg(matvec, b, maxiter, tol=0.0):
       x = x + alpha p + z;  r = t - eta y - zeta A t
       beta = (alpha / zeta) <rt, r_new> / <rt, r>
     Stops after `maxiter` iterations or when ||r|| <= tol ||b||.
-    Returns (x, iterations)."""
+    Returns (x, iterations), and the recursively updated r when return_r."""
     b = np.asarray(b, dtype=np.complex128)
     x = np.zeros_like(b)
     r = b.copy()
@@ -74,7 +76,7 @@ def gpbicg(matvec, b, maxiter, tol=0.0):
         r, rho = r_new, rho_new
         t_old, at_old, ap_old = t, at, ap
         n += 1
-    return x, n
+    return (x, n, r) if return_r else (x, n)
 
 
 def cgnr(matvec, b, maxiter, tol=0.0):
@@ -148,3 +150,51 @@ def qmr_sym(matvec, b, maxiter, tol=0.0):
         q = r + (rho_new / rho) * q
         rho = rho_new
     return x, n, taus
+
+
+def bicgstab2(matvec, b, ncycles, tol=0.0):
+    """BiCGstab(2) from x0 = 0 with shadow vector rt = r0 = b.  Each cycle
+    (four matvecs, counted as two iterations):
+      rho0 = -omega rho0
+      for j = 0, 1:
+        rho1 = <rt, r_j>;  beta = alpha rho1 / rho0;  rho0 = rho1
+        u_i = r_i - beta u_i (i <= j);  u_{j+1} = A u_j
+        alpha = rho0 / <rt, u_{j+1}>
+        r_i = r_i - alpha u_{i+1} (i <= j);  r_{j+1} = A r_j;  x = x + alpha u_0
+      (g1, g2) minimise ||r_0 - g1 r_1 - g2 r_2|| (2x2 normal equations)
+      u_0 -= g1 u_1 + g2 u_2;  x += g1 r_0 + g2 r_1;  r_0 -= g1 r_1 + g2 r_2;
+      omega = g2
+    Starts from rho0 = 1, alpha = 0, omega = 1, u_0 = 0.  Stops after
+    `ncycles` cycles or when ||r_0|| <= tol ||b||.  Returns (x, cycles, r0),
+    r0 the recursively updated residual."""
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b)
+    r = [b.copy(), None, None]
+    u = [np.zeros_like(b), None, None]
+    rt = b.copy()
+    rho0, alpha, omega = 1.0 + 0j, 0.0 + 0j, 1.0 + 0j
+    bn = np.linalg.norm(b)
+    c = 0
+    while c < ncycles and np.linalg.norm(r[0]) > tol * bn:
+        rho0 = -omega * rho0
+        for j in range(2):
+            rho1 = _dot(rt, r[j])
+            beta = alpha * rho1 / rho0
+            rho0 = rho1
+            for i in range(j + 1):
+                u[i] = r[i] - beta * u[i]
+            u[j + 1] = matvec(u[j])
+            alpha = rho0 / _dot(rt, u[j + 1])
+            for i in range(j + 1):
+                r[i] = r[i] - alpha * u[i + 1]
+            r[j + 1] = matvec(r[j])
+            x = x + alpha * u[0]
+        m = np.array([[_dot(r[1], r[1]), _dot(r[1], r[2])],
+                      [_dot(r[2], r[1]), _dot(r[2], r[2])]])
+        g1, g2 = np.linalg.solve(m, np.array([_dot(r[1], r[0]), _dot(r[2], r[0])]))
+        u[0] = u[0] - g1 * u[1] - g2 * u[2]
+        x = x + g1 * r[0] + g2 * r[1]
+        r[0] = r[0] - g1 * r[1] - g2 * r[2]
+        omega = g2
+        c += 1
+    return x, c, r[0]

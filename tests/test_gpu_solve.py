@@ -442,3 +442,19 @@ def test_qmr_iterates_match_oracle(B, k):
     assert n == k and g["iters"][0] == k
     assert np.abs(g["P"][0].reshape(-1) - xo).max() <= 1e-9 * np.abs(xo).max()
     t.close()
+
+
+@pytest.mark.parametrize("cycles", [1, 3])
+def test_bicgstab2_iterates_match_oracle(B, cycles):
+    """The GPU's BiCGstab(2) iterate after k cycles (2k iterations, FP64) equals
+    the oracle's."""
+    from oracle import krylov as K
+    w = W.small_ellipsoid(6, 7, 8, m=1.5 + 0.1j, kd=0.4, method="LDR")
+    E, mv = _linear_system(w)
+    xo, c, _ = K.bicgstab2(mv, E.reshape(-1), ncycles=cycles)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    g = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=1, tol=1e-14, max_iter=2 * cycles,
+                precision="fp64", solver="bicgstab2")
+    assert c == cycles and g["iters"][0] == 2 * cycles
+    assert np.abs(g["P"][0].reshape(-1) - xo).max() <= 1e-9 * np.abs(xo).max()
+    t.close()

@@ -83,3 +83,29 @@ def test_qmr_solves_and_keeps_its_residual_bound(seed):
     for k in range(1, 25):
         xk, _, taus = K.qmr_sym(mv, b, maxiter=k)
         assert np.linalg.norm(b - a @ xk) <= taus[-1] * np.sqrt(k + 1) * (1 + 1e-10)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bicgstab2_solves_and_its_recursive_residual_is_true(seed):
+    """BiCGstab(2) reaches the dense solution, and after every cycle the
+    recursively updated residual equals b - A x (a dropped or mis-signed term in
+    any of the updates breaks this identity)."""
+    a, b = _system(30, 10.0, seed)
+    mv = lambda v: a @ v
+    x, c, _ = K.bicgstab2(mv, b, ncycles=300, tol=1e-12)
+    ref = np.linalg.solve(a, b)
+    assert np.abs(x - ref).max() <= 1e-9 * np.abs(ref).max()
+    for k in range(1, 6):
+        xk, _, rk = K.bicgstab2(mv, b, ncycles=k)
+        assert np.abs(rk - (b - a @ xk)).max() <= 1e-11 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_gpbicg_recursive_residual_is_true(seed):
+    """GPBi-CG's coupled x, z, u and r updates keep r = b - A x after every
+    iteration."""
+    a, b = _system(30, 10.0, seed)
+    mv = lambda v: a @ v
+    for k in range(1, 8):
+        xk, _, rk = K.gpbicg(mv, b, maxiter=k, return_r=True)
+        assert np.abs(rk - (b - a @ xk)).max() <= 1e-11 * np.linalg.norm(b)
