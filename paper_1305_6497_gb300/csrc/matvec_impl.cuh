@@ -777,8 +777,9 @@ static void launch_z_pass(const OpView<T>& op, const MatvecLaunch& L, int R,
 // x pass, inverse + diagonal term: y = ainv * x - conv on occupied sites
 // grid: (row tiles, R)
 // --------------------------------------------------------------------------
-// Epilogue of the last pass, fused with BiCGSTAB inner products (FP64-accumulated,
-// per-block partials [R][gridDim.x][NV]):
+// Epilogue of the last pass, fused with the Krylov inner products (block sums
+// as in ChunkAcc, FP64 per-block partials [R][gridDim.x][NV]; with a FoldArgs
+// the last block of each RHS row also runs the scalar step those sums feed):
 //   XOUT_PLAIN : none;
 //   XOUT_RV    : <rhat, y>              (y = v = A p)
 //   XOUT_TS    : <y, x>, <y, y>         (y = t = A s, x = s)
