@@ -285,13 +285,15 @@ def dense_matrix(pos: np.ndarray, ainv: np.ndarray, kd: float, method: str = "LD
     return T.transpose(0, 2, 1, 3).reshape(3 * N, 3 * N)
 
 
-def fft_grid_green(shape_box, grid, kd, method="LDR"):
+def fft_grid_green(shape_box, grid, kd, method="LDR", z_range=None):
     """The 6 unique components (xx, xy, xz, yy, yz, zz) of G(Delta) laid on the
     periodic FFT grid: entry (i, j, l) holds G at the lattice offset
     Delta = (i or i - Lx, ...) when |Delta| fits the target box, else 0; Delta =
-    0 is 0 (the self term sits in alpha^{-1}).  Returns [6, Lz, Ly, Lx]."""
+    0 is 0 (the self term sits in alpha^{-1}).  Returns [6, Lz, Ly, Lx], or the
+    grid planes z0 <= i_z < z1 only for z_range = (z0, z1)."""
     nx, ny, nz = shape_box
     Lx, Ly, Lz = grid
+    z0, z1 = (0, Lz) if z_range is None else z_range
 
     def offs(n, L):
         o = np.arange(L)
@@ -302,6 +304,7 @@ def fft_grid_green(shape_box, grid, kd, method="LDR"):
     dx, vx = offs(nx, Lx)
     dy, vy = offs(ny, Ly)
     dz, vz = offs(nz, Lz)
+    dz, vz = dz[z0:z1], vz[z0:z1]
     DZ, DY, DX = np.meshgrid(dz, dy, dx, indexing="ij")
     valid = vz[:, None, None] & vy[None, :, None] & vx[None, None, :]
     valid &= ~((DX == 0) & (DY == 0) & (DZ == 0))
@@ -348,6 +351,79 @@ class FFTOperator:
         eh = np.stack([sum(full[a][b] * ph[b] for b in range(3)) for a in range(3)])
         field = np.fft.ifftn(eh, axes=(1, 2, 3))[:, :nz, :ny, :nx]
         out = self.ainv[None] * Pbox - field
+        return out * self.occ[None]
+
+
+class FFTOperatorLowMem:
+    """The same A.P as FFTOperator, for grids where FFTOperator's arrays holding
+    all components at once do not fit in host memory (the 512^3 grid of a 256^3
+    box: its [3, 3] tensor on the grid alone is 19 GB).  Only the grouping of
+    the work changes, not the arithmetic of any element:
+      * G is laid on the grid a few z-planes at a time (fft_grid_green with a
+        z_range) and each of its six components is transformed on its own;
+      * each polarization component is padded and transformed on its own, and
+        each output component's sum_b Ghat_ab Phat_b is formed and inverted on
+        its own;
+      * the FFTs are scipy.fft's (the library primitive, on `workers` host
+        threads) and the element-wise products run over z-slabs on host
+        threads.
+    Memory: 6 + 3 + 2 grid arrays of complex128 (26 GB on a 512^3 grid)."""
+
+    def __init__(self, occ, ainv_box, kd, method="LDR", grid=None, workers=None,
+                 slab=8):
+        import os
+        from concurrent.futures import ThreadPoolExecutor
+        from scipy import fft as sfft
+        self._sfft = sfft
+        nz, ny, nx = occ.shape
+        self.occ = occ != 0
+        self.box = (nx, ny, nz)
+        self.grid = tuple(grid) if grid is not None else default_grid(self.box)
+        for n, L in zip(self.box, self.grid):
+            if L < 2 * n - 1:
+                raise ValueError("FFT grid smaller than 2n-1 wraps the convolution")
+        self.ainv = ainv_box
+        self.workers = workers or os.cpu_count() or 1
+        self._pool = ThreadPoolExecutor(self.workers)
+        Lx, Ly, Lz = self.grid
+        self.ghat = np.empty((6, Lz, Ly, Lx), dtype=np.complex128)
+        for z0 in range(0, Lz, slab):
+            z1 = min(Lz, z0 + slab)
+            self.ghat[:, z0:z1] = fft_grid_green(self.box, self.grid, kd, method, (z0, z1))
+        for c in range(6):
+            self.ghat[c] = sfft.fftn(self.ghat[c], workers=self.workers, overwrite_x=True)
+        self._slabs = [(z0, min(Lz, z0 + slab)) for z0 in range(0, Lz, slab)]
+
+    def _pointwise_sum(self, out, pairs):
+        """out = sum over (g, p) in pairs of g * p, z-slab by z-slab."""
+        def work(zr):
+            z0, z1 = zr
+            g, p = pairs[0]
+            np.multiply(g[z0:z1], p[z0:z1], out=out[z0:z1])
+            for g, p in pairs[1:]:
+                out[z0:z1] += g[z0:z1] * p[z0:z1]
+        list(self._pool.map(work, self._slabs))
+
+    def __call__(self, Pbox: np.ndarray) -> np.ndarray:
+        """Pbox [3, nz, ny, nx] complex (zero on vacant sites) -> A.P, same shape."""
+        nx, ny, nz = self.box
+        Lx, Ly, Lz = self.grid
+        sfft = self._sfft
+        ph = np.empty((3, Lz, Ly, Lx), dtype=np.complex128)
+        for b in range(3):
+            pad = np.zeros((Lz, Ly, Lx), dtype=np.complex128)
+            pad[:nz, :ny, :nx] = Pbox[b]
+            ph[b] = sfft.fftn(pad, workers=self.workers, overwrite_x=True)
+            del pad
+        g = self.ghat
+        full = [[g[0], g[1], g[2]], [g[1], g[3], g[4]], [g[2], g[4], g[5]]]
+        out = np.empty((3, nz, ny, nx), dtype=np.complex128)
+        eh = np.empty((Lz, Ly, Lx), dtype=np.complex128)
+        for a in range(3):
+            self._pointwise_sum(eh, [(full[a][b], ph[b]) for b in range(3)])
+            field = sfft.ifftn(eh, workers=self.workers)[:nz, :ny, :nx]
+            out[a] = self.ainv * Pbox[a] - field
+            del field
         return out * self.occ[None]
 
 
@@ -469,10 +545,14 @@ def sites_to_box(v: np.ndarray, flat: np.ndarray, shape) -> np.ndarray:
 
 
 def solve_target(occ, comp, m_list, kd, khat, yhat, e01, method="LDR", npol=2,
-                 tol=1e-11, dirs=None, operator="fft", maxiter=20000, grid=None):
+                 tol=1e-11, dirs=None, operator="fft", maxiter=20000, grid=None,
+                 workers=None, on_matvec=None):
     """Solve A P = E_inc for each incident polarization of one incidence.
 
-    operator: 'fft' (FFT convolution), 'direct' (O(N^2) sum) or 'dense' (LU).
+    operator: 'fft' (FFT convolution), 'fft_lowmem' (the same with
+    FFTOperatorLowMem), 'direct' (O(N^2) sum) or 'dense' (LU).
+    workers: host threads of FFTOperatorLowMem; on_matvec: optional callable
+    invoked after every product (progress reporting only).
     Returns a dict with P (list of [N,3]), Qext/Qabs/Qsca, iters, resid, famp.
     """
     flat, pos = site_positions(occ)
@@ -494,15 +574,22 @@ def solve_target(occ, comp, m_list, kd, khat, yhat, e01, method="LDR", npol=2,
                 return matvec_direct(x.reshape(-1, 3), pos, ainv, kd, method).reshape(-1)
             x, it, res = bicgstab(mv, E.reshape(-1), tol, maxiter)
             P = x.reshape(-1, 3)
-        elif operator == "fft":
+        elif operator in ("fft", "fft_lowmem"):
             ainv_box = np.zeros(occ.size, dtype=np.complex128)
             ainv_box[flat] = ainv
-            op = FFTOperator(occ, ainv_box.reshape(occ.shape), kd, method, grid)
+            if operator == "fft":
+                op = FFTOperator(occ, ainv_box.reshape(occ.shape), kd, method, grid)
+            else:
+                op = FFTOperatorLowMem(occ, ainv_box.reshape(occ.shape), kd, method, grid,
+                                       workers)
             shape = occ.shape
 
             def mv(x):
                 xb = sites_to_box(x.reshape(-1, 3), flat, shape)
-                return box_to_sites(op(xb), flat).reshape(-1)
+                y = box_to_sites(op(xb), flat).reshape(-1)
+                if on_matvec is not None:
+                    on_matvec()
+                return y
             x, it, res = bicgstab(mv, E.reshape(-1), tol, maxiter)
             P = x.reshape(-1, 3)
         else:

@@ -88,9 +88,10 @@ def test_fft_embedding_equals_direct_sum(method, dims):
     ainv_box = np.zeros(occ.size, np.complex128)
     ainv_box[flat] = ainv
     for grid in (None, (2 * nx + 3, 2 * ny + 1, 2 * nz + 5)):
-        op = dda.FFTOperator(occ, ainv_box.reshape(occ.shape), kd, method, grid)
-        got = dda.box_to_sites(op(P), flat)
-        assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+        for cls in (dda.FFTOperator, dda.FFTOperatorLowMem):
+            op = cls(occ, ainv_box.reshape(occ.shape), kd, method, grid)
+            got = dda.box_to_sites(op(P), flat)
+            assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
 
 
 def test_fft_grid_too_small_is_refused():
