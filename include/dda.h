@@ -167,11 +167,15 @@ dda_status dda_matvec(dda_target* t, double kd, const double* khat, const double
  * Limit: 3*nz*Ly*Lx complex values of the chosen precision must fit in 64 MiB
  * minus 4 KiB (with L = 2n: cubic boxes up to 88^3 in FP32, 70^3 in FP64);
  * larger targets get DDA_ERR_INVALID_ARG with the sizes in dda_last_error().
- * The first call on each device looks up the device address of the static
- * array; make that first call before any stream capture.  All calls on a device
- * share the array and see whatever the previous call left there (nothing in it
- * needs to start at zero): calls that overlap on the GPU (other streams, other
- * threads) race on it and must be serialized by the caller. */
+ * The 64 MiB are committed on a device when the first target is created there:
+ * dda_target_create looks up the array's device address (which loads the part
+ * of the library that holds it), so this call does not.  CUDA loads each kernel
+ * on its first launch; a dda_matvec with the same precision beforehand (as the
+ * Green-transform rule above already asks) has launched them all.  The call is
+ * synchronous: it returns after its work on the stream has finished.  All calls
+ * on a device share the array and see whatever the previous call left there
+ * (nothing in it needs to start at zero): calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialized by the caller. */
 dda_status dda_matvec_noalloc(dda_target* t, double kd, const double* khat, const double* e,
                               const void* x_dev, void* y_dev, dda_precision precision,
                               void* cuda_stream);
@@ -204,6 +208,13 @@ typedef struct {
                             residuals E - A P with FP64 box vectors and FFT passes in
                             double-float arithmetic (pairs of FP32 values, ~48 bits,
                             run at FP32 rates); 1 uses FP64 arithmetic throughout */
+  void* cuda_stream;     /* optional cudaStream_t of the caller (created on the
+                            target's device; not cudaStreamLegacy/PerThread:
+                            DDA_ERR_INVALID_ARG).  dda_solve then enqueues all its
+                            device work on that stream -- after whatever the caller
+                            queued there before -- and returns once it has finished;
+                            the stream must not be under capture.  NULL: the
+                            target's own stream.  dda_nearfield ignores it.        */
 } dda_solve_params;
 
 /* Results.  Every array is caller-allocated HOST memory; a NULL pointer means
@@ -387,9 +398,23 @@ dda_status dda_orient_average(dda_target* t, const dda_orient_params* p, dda_ori
 /* Number of occupied sites N of a target (-1 for NULL). */
 int64_t dda_target_num_dipoles(const dda_target* t);
 
-/* Upper bound on the device bytes dda_solve(t, params, ...) allocates beyond
- * what the target already holds (admission control); -1 on bad arguments. */
+/* Upper bound on the device bytes dda_solve(t, params) allocates on the target
+ * besides its creation arrays and a Green transform it already holds: the
+ * solve's workspace and, when the transform for (kd, method) is not built
+ * yet, its transient build grids (admission control); -1 on bad arguments. */
 int64_t dda_solve_hbm_bytes(const dda_target* t, const dda_solve_params* params);
+
+/* Upper bound on the device bytes a NEW target of this shape holds at the
+ * peak of its first dda_solve(params): creation arrays, the kept Green
+ * transform, its transient build grids and the workspace.  Host-only (no
+ * device work, no allocation), so a scheduler can admit a request before the
+ * target exists.  method: dda_pol_method.  -1 on bad arguments. */
+int64_t dda_estimate_solve_bytes(int nx, int ny, int nz, int64_t n_dipoles, int ncomp,
+                                 int method, const dda_solve_params* params);
+
+/* Device bytes target t holds now (creation arrays, Green transforms,
+ * workspace kept from earlier solves, near-field box); -1 for NULL. */
+int64_t dda_target_device_bytes(const dda_target* t);
 
 /* FFT grid chosen for a target: the smallest 2^a 3^b 5^c lengths >= 2n-1 per
  * axis (Sec. "Choice of FFT Algorithm": the guide's GPFA grid sizes). */

@@ -30,7 +30,8 @@ class SolveParams(ct.Structure):
                 ("e01", _dp), ("npol", ct.c_int), ("tol", ct.c_double),
                 ("max_iter", ct.c_int), ("precision", ct.c_int), ("inner_tol", ct.c_double),
                 ("n_dirs", ct.c_int), ("dirs", _dp), ("P0", _dp), ("profile", ct.c_int),
-                ("solver", ct.c_int), ("fp64_residual", ct.c_int)]
+                ("solver", ct.c_int), ("fp64_residual", ct.c_int),
+                ("cuda_stream", ct.c_void_p)]
 
 
 class SolveResult(ct.Structure):
@@ -90,6 +91,11 @@ def _load():
     lib.dda_target_num_dipoles.restype = ct.c_int64
     lib.dda_solve_hbm_bytes.argtypes = [vp, ct.POINTER(SolveParams)]
     lib.dda_solve_hbm_bytes.restype = ct.c_int64
+    lib.dda_estimate_solve_bytes.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int64,
+                                             ct.c_int, ct.c_int, ct.POINTER(SolveParams)]
+    lib.dda_estimate_solve_bytes.restype = ct.c_int64
+    lib.dda_target_device_bytes.argtypes = [vp]
+    lib.dda_target_device_bytes.restype = ct.c_int64
     lib.dda_target_grid.argtypes = [vp, _ip, _ip, _ip]
     lib.dda_target_grid.restype = ct.c_int
     lib.dda_launch_count.argtypes = []
@@ -220,7 +226,7 @@ def dda_matvec_noalloc(h, kd: float, x_dev_ptr: int, y_dev_ptr: int, khat=None, 
 
 
 def _params(kd, khat, e01, yhat, npol, tol, max_iter, precision, inner_tol, dirs, P0,
-            profile=False, solver="bicgstab", fp64_residual=False):
+            profile=False, solver="bicgstab", fp64_residual=False, stream_ptr=0):
     keep = []
 
     def arr(a, dtype=np.float64):
@@ -242,7 +248,8 @@ def _params(kd, khat, e01, yhat, npol, tol, max_iter, precision, inner_tol, dirs
                       inner_tol=float(inner_tol), n_dirs=0 if d is None else d.shape[0],
                       dirs=_ptr(d), P0=None if p0 is None else _ptr(p0.view(np.float64)),
                       profile=1 if profile else 0, solver=SOLVER[solver],
-                      fp64_residual=1 if fp64_residual else 0)
+                      fp64_residual=1 if fp64_residual else 0,
+                      cuda_stream=ct.c_void_p(stream_ptr) if stream_ptr else None)
     return prm, keep, n_inc
 
 
@@ -253,18 +260,38 @@ def dda_solve_hbm_bytes(h, kd, khat, e01, npol=2, precision="fp64", dirs=None,
     return int(lib.dda_solve_hbm_bytes(h, ct.byref(prm)))
 
 
+def dda_estimate_solve_bytes(occ, ncomp, method, kd, khat, e01, npol=2,
+                             precision="fp64", dirs=None, solver="bicgstab") -> int:
+    """Device bytes a new target of this occupancy needs at the peak of its first
+    solve (host-only: nothing is allocated)."""
+    nz, ny, nx = np.asarray(occ).shape
+    prm, keep, _ = _params(kd, khat, e01, None, npol, 1e-8, 1, precision, 0.0, dirs, None,
+                           solver=solver)
+    b = int(lib.dda_estimate_solve_bytes(nx, ny, nz, int(np.count_nonzero(occ)), int(ncomp),
+                                         POL[method], ct.byref(prm)))
+    if b < 0:
+        raise DDAError(DDA_ERR_INVALID_ARG, "bad arguments to dda_estimate_solve_bytes")
+    return b
+
+
+def dda_target_device_bytes(h) -> int:
+    return int(lib.dda_target_device_bytes(h))
+
+
 def dda_solve(h, kd, khat, e01, yhat=None, npol=2, tol=1e-8, max_iter=2000,
               precision="fp64", inner_tol=0.0, dirs=None, P0=None, want_P=True,
               want_famp=True, raise_on_noconv=False, profile=False,
-              solver="bicgstab", fp64_residual=False) -> dict:
+              solver="bicgstab", fp64_residual=False, stream_ptr: int = 0) -> dict:
     """Solve for every incidence x polarization.  Returns a dict of numpy arrays.
     solver: "bicgstab" (two matvecs per iteration), "qmr" (complex-symmetric
     QMR, one matvec per iteration), "bicgstab2" (BiCGstab(2), four matvecs per
     two-iteration cycle), "gpbicg" (GPBi-CG, two matvecs per iteration) or
     "petrkp" (conjugate gradients on the normal equations, two matvecs per
-    iteration)."""
+    iteration).  stream_ptr: a cudaStream_t (e.g. torch.cuda.Stream().cuda_stream)
+    on which the library runs the solve; 0 = the target's own stream."""
     prm, keep, n_inc = _params(kd, khat, e01, yhat, npol, tol, max_iter, precision,
-                               inner_tol, dirs, P0, profile, solver, fp64_residual)
+                               inner_tol, dirs, P0, profile, solver, fp64_residual,
+                               stream_ptr)
     N = dda_target_num_dipoles(h)
     R = n_inc * npol
     D = prm.n_dirs + 1
@@ -428,6 +455,10 @@ class Target:
 
     def hbm_bytes(self, kd, khat, e01, **kw):
         return dda_solve_hbm_bytes(self.h, kd, khat, e01, **kw)
+
+    @property
+    def device_bytes(self):
+        return dda_target_device_bytes(self.h)
 
     def orient_average(self, kd, **kw):
         return dda_orient_average(self.h, kd, **kw)

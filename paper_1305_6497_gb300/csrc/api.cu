@@ -19,6 +19,12 @@ using namespace dda;
 using cd = std::complex<double>;
 
 #include <atomic>
+namespace {
+// Device address of the allocation-free matvec's static scratch array on a
+// device (defined with the array, below dda_matvec_noalloc's helpers).
+cudaError_t static_scratch_address(int dev, void** out);
+}  // namespace
+
 static std::atomic<long long> g_launches{0};
 void dda::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 static void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -176,13 +182,19 @@ struct Workspace {
   DevBuf pol, ph, ainv64, ainv32, ainvdf, wabs, fph, sitebuf;
   DevBuf extra64, extra32;  // extra Krylov vectors of BiCGstab(2), GPBi-CG (on first use)
   DevBuf fold;              // per-RHS block counters of the passes that end a scalar step
-  void release_all() {
+  template <class F> void each(F f) {
     for (DevBuf* b : {&b64, &x64, &r64, &rh64, &p64, &v64, &s64, &t64, &scr64, &x32, &r32,
                       &rh32, &p32, &v32, &s32, &t32, &scr32, &b32, &partials, &ks, &active,
                       &active_outer, &norms, &sums, &pol, &ph, &ainv64, &ainv32, &ainvdf, &wabs, &fph,
                       &extra64, &extra32, &fold,
                       &sitebuf})
-      b->release();
+      f(*b);
+  }
+  void release_all() { each([](DevBuf& b) { b.release(); }); }
+  int64_t bytes() {
+    int64_t n = 0;
+    each([&n](DevBuf& b) { n += (int64_t)b.bytes; });
+    return n;
   }
 };
 
@@ -1242,6 +1254,14 @@ dda_status dda_target_create(int nx, int ny, int nz, const uint8_t* occ, const u
     t->Ly = smooth_at_least(2 * ny - 1);
     t->Lz = smooth_at_least(2 * nz - 1);
     CK(cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking));
+    {
+      // Resolve the static scratch array of dda_matvec_noalloc here, where
+      // allocating is allowed: the lookup loads the module that holds it and
+      // commits its device memory (once per device), so that the
+      // allocation-free entry point itself never does.
+      void* scratch = nullptr;
+      CK(static_scratch_address(t->device, &scratch));
+    }
     CK(cudaEventCreate(&t->ev0));
     CK(cudaEventCreate(&t->ev1));
     t->comp.ensure(nbox);
@@ -1315,9 +1335,53 @@ int64_t dda_solve_hbm_bytes(const dda_target* t, const dda_solve_params* p) {
   const int filtered = t->method == DDA_POL_FCD ? 1 : 0;
   if (!(t->have_green && t->green_kd == p->kd && t->green_filtered == filtered)) {
     const int64_t M = (int64_t)t->Lx * t->Ly * t->Lz;
-    b += 2 * 6 * M * 16;  // transient setup grids
+    b += 2 * 6 * M * 16;                            // transient setup grids
+    b += 6 * octant_size(t) * (16 + 8 + 16);        // the kept octant (FP64, FP32, df)
   }
   return b;
+}
+
+// Device bytes a target holds now: resident arrays, Green transforms,
+// workspace and its near-field box.
+static int64_t held_bytes(dda_target* t) {
+  int64_t b = 0;
+  for (const DevBuf* d : {&t->comp, &t->site, &t->tw64, &t->tw32, &t->twdf, &t->perm, &t->g64,
+                          &t->g32, &t->gdf, &t->h64})
+    b += (int64_t)d->bytes;
+  b += t->ws.bytes();
+  if (t->nf) b += held_bytes(t->nf);
+  return b;
+}
+
+int64_t dda_target_device_bytes(const dda_target* t) {
+  return t ? held_bytes(const_cast<dda_target*>(t)) : -1;
+}
+
+int64_t dda_estimate_solve_bytes(int nx, int ny, int nz, int64_t n_dipoles, int ncomp,
+                                 int method, const dda_solve_params* p) {
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 1024 || ny > 1024 || nz > 1024 || ncomp < 1 ||
+      ncomp > 255 || method < DDA_POL_CM || method > DDA_POL_FCD)
+    return -1;
+  const int64_t nbox = (int64_t)nx * ny * nz;
+  if (n_dipoles < 1 || n_dipoles > nbox) return -1;
+  // a host-only description of the target (nothing is allocated)
+  dda_target d;
+  d.nx = nx; d.ny = ny; d.nz = nz;
+  d.nbox = nbox;
+  d.N = n_dipoles;
+  d.ncomp = ncomp;
+  d.method = (dda_pol_method)method;
+  d.Lx = smooth_at_least(2 * nx - 1);
+  d.Ly = smooth_at_least(2 * ny - 1);
+  d.Lz = smooth_at_least(2 * nz - 1);
+  // workspace, transient build grids and the kept transform
+  const int64_t solve = dda_solve_hbm_bytes(&d, p);
+  if (solve < 0) return -1;
+  const int64_t Lsum = (int64_t)d.Lx + d.Ly + d.Lz;
+  // dda_target_create: composition grid, site list, twiddles (FP64, FP32,
+  // double-float) and the frequency/position tables
+  const int64_t created = nbox + 8 * n_dipoles + Lsum * (16 + 8 + 16) + 2 * Lsum * 4 + 3 * 256;
+  return created + solve;
 }
 
 static dda_status check_kd(const dda_target* t, double kd) {
@@ -1415,6 +1479,9 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
     return fail(DDA_ERR_INVALID_ARG, "unknown solver");
   const int R = p->n_inc * p->npol;
   if (R > 4096) return fail(DDA_ERR_INVALID_ARG, "at most 4096 right-hand sides");
+  if (p->cuda_stream == (void*)cudaStreamLegacy || p->cuda_stream == (void*)cudaStreamPerThread)
+    return fail(DDA_ERR_INVALID_ARG,
+                "cuda_stream must be a created stream (not the legacy or per-thread default)");
   std::vector<Incidence> incs(p->n_inc);
   for (int i = 0; i < p->n_inc; ++i) {
     s = make_incidence(p, i, incs[i]);
@@ -1425,6 +1492,16 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
   const int64_t n = 3 * nbox;
   const int D = p->n_dirs + 1;
   dda_status result_status = DDA_OK;
+  // With a caller's stream every launch, copy and graph of this call goes to
+  // that stream instead of the target's own one (restored on return).
+  struct StreamSwap {
+    dda_target* t;
+    cudaStream_t saved;
+    StreamSwap(dda_target* tt, void* s) : t(tt), saved(tt->stream) {
+      if (s) t->stream = (cudaStream_t)s;
+    }
+    ~StreamSwap() { t->stream = saved; }
+  } stream_swap(t, p->cuda_stream);
   try {
     CK(cudaSetDevice(t->device));
     cudaStream_t st = t->stream;
@@ -2110,7 +2187,7 @@ dda_status dda_matvec_noalloc(dda_target* t, double kd, const double* khat, cons
   try {
     CK(cudaSetDevice(t->device));
     void* base = nullptr;
-    CK(static_scratch_address(t->device, &base));
+    CK(static_scratch_address(t->device, &base));  // resolved by dda_target_create
     cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : t->stream;
     unsigned char* area = reinterpret_cast<unsigned char*>(base);
     // alpha^{-1} per composition (entry 0 unused) at the start of the area

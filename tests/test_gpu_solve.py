@@ -458,3 +458,27 @@ def test_bicgstab2_iterates_match_oracle(B, cycles):
     assert c == cycles and g["iters"][0] == 2 * cycles
     assert np.abs(g["P"][0].reshape(-1) - xo).max() <= 1e-9 * np.abs(xo).max()
     t.close()
+
+
+def test_solve_on_a_callers_stream_is_bit_identical(B):
+    """dda_solve_params.cuda_stream: the solve runs on a caller's (torch) stream,
+    after the caller's earlier work there, with the same results bit for bit."""
+    import torch
+    w = W.small_ellipsoid(8, 12, 32, m=1.5 + 0.1j, kd=0.4, method="LDR", n_orient=2)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    kw = dict(yhat=w.yhat, npol=2, tol=1e-10, precision="fp32_refined", dirs=w.dirs)
+    ref = t.solve(w.kd, w.khat, w.e01, **kw)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        # queue work ahead on the caller's stream; the solve must order after it
+        a = torch.randn(4096, 4096, device="cuda")
+        b = a @ a
+    out = t.solve(w.kd, w.khat, w.e01, stream_ptr=s.cuda_stream, **kw)
+    assert s.query()                       # the call returned after its work finished
+    torch.cuda.synchronize()
+    del a, b
+    for key in ("Qext", "Qabs", "iters", "resid"):
+        assert np.array_equal(out[key], ref[key]), key
+    assert np.array_equal(out["P"], ref["P"])
+    assert np.array_equal(out["famp"], ref["famp"])
+    t.close()
