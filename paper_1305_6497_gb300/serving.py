@@ -4,14 +4,20 @@ Each request is a target (occupancy, composition, refractive indices) with its
 incident waves.  The server keeps up to ``max_slots`` solves in flight on the
 GPU at once, each on its own ``dda_target`` and therefore its own CUDA stream,
 so their kernels overlap on the device.  A request is admitted as soon as a
-slot is free AND the device bytes it needs fit in the HBM budget: the bytes are
-the library's own estimate (``dda_solve_hbm_bytes``: workspace, Green-tensor
-transform and its transient build grids) plus the target's resident arrays.
-Finished solves return their bytes at once, so requests that arrive while
-others run start as room appears -- not a queue drained one at a time.
+slot is free AND the device bytes it needs fit in the HBM budget.  Its bytes
+are the library's host-only estimate for a new target of its shape
+(``dda_estimate_solve_bytes``: creation arrays, Green-tensor transform with its
+transient build grids, solve workspace); nothing is allocated before
+admission.  Finished solves return their reservation at once, so requests that
+arrive while others run start as room appears -- not a queue drained one at a
+time.
 
-Targets are cached by geometry and optical constants (LRU, within the budget),
-so a repeated target reuses its resident Green-tensor transform.
+Targets are cached by geometry and optical constants (LRU), so a repeated
+target reuses its resident Green-tensor transform.  An idle cached target keeps
+its device memory (``dda_target_device_bytes``), and that memory counts against
+the same budget: reservations of running solves plus the bytes of idle cached
+targets never exceed it.  When a request does not fit, idle cached targets are
+evicted, least recently used first, before the request waits.
 
 The GPU work is in libdda.so; the binding's ctypes calls release the GIL, so
 worker threads run their solves concurrently.  ``solver`` can be replaced (the
@@ -78,7 +84,12 @@ class Result:
 
 
 class GpuSolver:
-    """Runs requests through libdda.so with an LRU cache of targets."""
+    """Runs requests through libdda.so with an LRU cache of idle targets.
+
+    Interface used by Server: estimate_bytes(req) (host-only), acquire(req) ->
+    handle, solve_on(handle, req), release(handle) (the target becomes an idle
+    cache entry), cached_bytes() and evict(nbytes).  solve(req) runs all three
+    steps for callers without a Server."""
 
     def __init__(self, precision="fp32_refined", tol=1e-8, max_iter=5000, cache_targets=8):
         from . import binding as B
@@ -86,69 +97,79 @@ class GpuSolver:
         self.precision = precision
         self.tol = tol
         self.max_iter = max_iter
-        self.cache = collections.OrderedDict()
+        self.cache = collections.OrderedDict()   # key -> (Target, device bytes), idle only
         self.cache_targets = cache_targets
         self.lock = threading.Lock()
-        self.busy = set()
-
-    def target_bytes(self, req: Request) -> int:
-        nbox = req.occ.size
-        N = int(np.count_nonzero(req.occ))
-        return int(nbox + 8 * N + 64 * sum(req.occ.shape) + (1 << 20))
-
-    def _target(self, req):
-        k = req.key()
-        with self.lock:
-            t = self.cache.pop(k, None)
-            if t is not None and id(t) not in self.busy:
-                self.busy.add(id(t))
-                return t, k
-            if t is not None:
-                self.cache[k] = t  # in use by another worker: make a private one
-        t = self.B.Target(req.occ, req.comp, req.m, method=req.method)
-        with self.lock:
-            self.busy.add(id(t))
-        return t, k
-
-    def _release(self, t, k):
-        with self.lock:
-            self.busy.discard(id(t))
-            if k not in self.cache:
-                self.cache[k] = t
-                while len(self.cache) > self.cache_targets:
-                    _, old = self.cache.popitem(last=False)
-                    if id(old) not in self.busy:
-                        old.close()
-            else:
-                t.close()
 
     def estimate_bytes(self, req: Request) -> int:
-        t, k = self._target(req)
-        try:
-            b = t.hbm_bytes(req.kd, req.khat, req.e01, npol=req.npol, precision=self.precision)
-        finally:
-            self._release(t, k)
-        return int(b) + self.target_bytes(req)
+        return self.B.dda_estimate_solve_bytes(
+            req.occ, len(req.m), req.method, req.kd, req.khat, req.e01, npol=req.npol,
+            precision=self.precision)
+
+    def acquire(self, req: Request):
+        k = req.key()
+        with self.lock:
+            hit = self.cache.pop(k, None)
+        t = hit[0] if hit is not None else self.B.Target(req.occ, req.comp, req.m,
+                                                          method=req.method)
+        return (t, k)
+
+    def solve_on(self, handle, req: Request) -> dict:
+        t, _ = handle
+        return t.solve(req.kd, req.khat, req.e01, yhat=req.yhat, npol=req.npol, tol=self.tol,
+                       max_iter=self.max_iter, precision=self.precision, want_P=False,
+                       want_famp=False)
+
+    def release(self, handle) -> None:
+        t, k = handle
+        nbytes = t.device_bytes
+        drop = []
+        with self.lock:
+            if k in self.cache:
+                drop.append(t)           # another copy is already cached
+            else:
+                self.cache[k] = (t, nbytes)
+                while len(self.cache) > self.cache_targets:
+                    drop.append(self.cache.popitem(last=False)[1][0])
+        for old in drop:
+            old.close()
+
+    def cached_bytes(self) -> int:
+        with self.lock:
+            return sum(b for _, b in self.cache.values())
+
+    def evict(self, nbytes: int) -> int:
+        """Free idle cached targets, oldest first, until nbytes are freed or the
+        cache is empty.  Returns the bytes freed."""
+        freed, drop = 0, []
+        with self.lock:
+            while self.cache and freed < nbytes:
+                _, (t, b) = self.cache.popitem(last=False)
+                drop.append(t)
+                freed += b
+        for t in drop:
+            t.close()
+        return freed
 
     def solve(self, req: Request) -> dict:
-        t, k = self._target(req)
+        h = self.acquire(req)
         try:
-            out = t.solve(req.kd, req.khat, req.e01, yhat=req.yhat, npol=req.npol,
-                          tol=self.tol, max_iter=self.max_iter, precision=self.precision,
-                          want_P=False, want_famp=False)
+            return self.solve_on(h, req)
         finally:
-            self._release(t, k)
-        return out
+            self.release(h)
 
     def close(self):
         with self.lock:
-            for t in self.cache.values():
+            for t, _ in self.cache.values():
                 t.close()
             self.cache.clear()
 
 
 class Server:
-    """Admission by slots and HBM bytes; worker threads run admitted solves."""
+    """Admission by slots and HBM bytes; worker threads run admitted solves.
+
+    Invariant (checked at every admission and release): the reservations of
+    admitted solves plus the solver's idle cached bytes stay within budget."""
 
     def __init__(self, solver, hbm_budget_bytes: int, max_slots: int = 8):
         self.solver = solver
@@ -158,7 +179,9 @@ class Server:
         self.in_use = 0
         self.slots = 0
         self.peak_in_use = 0
+        self.peak_total = 0
         self.peak_slots = 0
+        self.evicted_bytes = 0
         self.queue_depth_max = 0
         self.work = queue.Queue()
         self.results = []
@@ -168,25 +191,33 @@ class Server:
         for th in self.workers:
             th.start()
 
+    def _note_total_locked(self):
+        total = self.in_use + self.solver.cached_bytes()
+        self.peak_total = max(self.peak_total, total)
+        return total
+
     def _admit(self, nbytes):
-        """Block until a slot and `nbytes` of budget are free; False if the
-        request can never fit (it is rejected, not queued forever)."""
+        """Block until a slot and `nbytes` of budget are free (evicting idle
+        cached targets first); False if the request can never fit (it is
+        rejected, not queued forever)."""
         if nbytes > self.budget:
             return False
         with self.cv:
-            while self.slots >= self.max_slots or self.in_use + nbytes > self.budget:
+            while True:
+                if self.slots < self.max_slots:
+                    over = self.in_use + self.solver.cached_bytes() + nbytes - self.budget
+                    if over > 0:
+                        self.evicted_bytes += self.solver.evict(over)
+                        over = self.in_use + self.solver.cached_bytes() + nbytes - self.budget
+                    if over <= 0:
+                        break
                 self.cv.wait()
             self.slots += 1
             self.in_use += nbytes
             self.peak_in_use = max(self.peak_in_use, self.in_use)
             self.peak_slots = max(self.peak_slots, self.slots)
+            self._note_total_locked()
         return True
-
-    def _free(self, nbytes):
-        with self.cv:
-            self.slots -= 1
-            self.in_use -= nbytes
-            self.cv.notify_all()
 
     def _worker(self):
         while True:
@@ -195,8 +226,10 @@ class Server:
                 return
             req, t0, nbytes, t_admit = item
             t_start = time.perf_counter() - t0
+            handle = None
             try:
-                out = self.solver.solve(req)
+                handle = self.solver.acquire(req)
+                out = self.solver.solve_on(handle, req)
                 t_fin = time.perf_counter() - t0
                 self.results.append(Result(
                     req.id, np.asarray(out["Qext"]), np.asarray(out["Qabs"]),
@@ -207,7 +240,15 @@ class Server:
             except Exception as e:  # noqa: BLE001 -- reported, never hides a result
                 self.errors.append((req.id, repr(e)))
             finally:
-                self._free(nbytes)
+                # the target turns into an idle cache entry and the reservation
+                # ends in one step, so the two are never counted apart
+                with self.cv:
+                    if handle is not None:
+                        self.solver.release(handle)
+                    self.slots -= 1
+                    self.in_use -= nbytes
+                    self._note_total_locked()
+                    self.cv.notify_all()
 
     def run(self, requests, realtime=True):
         """Replay `requests` (sorted by t_arrival); returns the results."""
@@ -264,6 +305,8 @@ class Server:
             "queue_depth_max": self.queue_depth_max,
             "peak_concurrent_solves": self.peak_slots,
             "peak_hbm_reserved_bytes": self.peak_in_use,
+            "peak_hbm_reserved_plus_cached_bytes": self.peak_total,
+            "evicted_bytes": self.evicted_bytes,
             "hbm_budget_bytes": self.budget,
         }
 
