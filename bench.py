@@ -1,19 +1,22 @@
 #!/usr/bin/env python
-"""Benchmark of the DDA solve on the sphere-64^3 workload.
+"""Benchmark of the DDA solve (default: the sphere-256^3 workload).
 
-Workload: sphere on a 64^3 lattice (N = 137,376 dipoles, FFT grid 128^3),
-m = 1.5 + 0.02i, x = 2 pi a_eff / lambda = 5, LATTDR polarizability, incidence
-along x with both polarizations (2 right-hand sides), tolerance 1e-8 on the
-FP64 relative residual.  A step is one complete solve of both polarizations
-(every BiCGSTAB iteration, the FP64 refinement residuals, the final FP64 true
-residual and the cross sections and forward amplitudes), FFT-convolution
-matvec in complex FP32 inside FP64 iterative refinement.  The plain FP64
-solve is timed beside it on the same GPU and both are checked for equal
-Q_ext (relative difference <= 1e-6).
+Default workload: sphere on a 256^3 lattice (N = 8,783,848 dipoles, FFT grid
+512^3), m = 1.33 + 0.01i, x = 2 pi a_eff / lambda = 25, LATTDR polarizability,
+incidence along x with both polarizations (2 right-hand sides), tolerance 1e-8
+on the FP64 relative residual -- the largest single-GPU configuration of the
+refined-FP32-versus-FP64 comparison.  A step is one complete solve of both
+polarizations (every BiCGSTAB iteration, the FP64 refinement residuals, the
+final FP64 true residual and the cross sections and forward amplitudes),
+FFT-convolution matvec in complex FP32 inside FP64 iterative refinement.  The
+plain FP64 solve is timed beside it on the same GPU and both are checked for
+equal Q_ext (relative difference <= 1e-6).  --workload picks another
+configuration (sphere16, sphere64, ellipsoid).
 
-Prints one JSON line (rank 0).  --impl reference times the CPU oracle
-(numpy FFT-convolution BiCGSTAB in FP64) on bounded samples of the same
-workload on the host cores.
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on
+bounded samples of the same workload on the host cores (FFT-convolution
+BiCGSTAB in FP64 up to 2 M dipoles, the direct sum on sampled rows,
+extrapolated, above).
 """
 from __future__ import annotations
 
@@ -33,7 +36,7 @@ if ROOT not in sys.path:
 
 METRIC = "dipole*iters/s"
 UNIT = "dipole*iterations/s"
-# --workload choices (the default is the configuration the metric is quoted on)
+# --workload choices (the default is the largest single-GPU configuration)
 WORKLOADS = {
     "sphere64": ("c2_sphere64", "sphere64^3 N=137376, m=1.5+0.02i, x=5, LDR, 2 pol, tol 1e-8"),
     "sphere16": ("c1_sphere16", "sphere16^3 N=2176, m=1.33+0.01i, x=1, LDR, 2 pol, tol 1e-8"),
@@ -205,6 +208,51 @@ def _workload(name):
     return getattr(W, fn)(), desc
 
 
+def _smooth_at_least(m):
+    """Smallest 2^a 3^b 5^c >= m (the FFT grid rule of the library)."""
+    n = max(1, m)
+    while True:
+        k = n
+        for f in (2, 3, 5):
+            while k % f == 0:
+                k //= f
+        if k == 1:
+            return n
+        n += 1
+
+
+def _config(w, desc, world):
+    """The `config` object of both arms' JSON lines (identical for a workload)."""
+    return {"workload": desc, "N": w.n_dipoles, "box": list(w.shape),
+            "grid": [_smooth_at_least(2 * n - 1) for n in w.shape], "rhs": w.n_rhs,
+            "precision": "fp32_refined", "tol": w.tol,
+            "l2": "flushed between steps (256 MB write)",
+            "parallelism": "replicas" if world > 1 else "1 GPU"}
+
+
+def _host_cpu():
+    """(logical cores, CPU model) of the host running the oracle."""
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return os.cpu_count(), model or platform.machine()
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -218,14 +266,16 @@ def run_reference(args, rank, world):
         times.append(dt)
         cores.append(c)
     value = statistics.mean(vals)
+    ncpu, model = _host_cpu()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": desc, "N": w.n_dipoles},
+        "config": _config(w, desc, world),
         "cpu_baseline": {"value": value, "unit": UNIT,
                          "cores": round(statistics.mean(cores), 2), "kind": "oracle",
+                         "host_cores": ncpu, "cpu_model": model,
                          "sample": sample + " per step; cores = process CPU time / wall time"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -335,11 +385,13 @@ def run_gpu(args, rank, world, local_rank):
     q64 = o64["Qext"]
     qerr = float(np.max(np.abs(qext / q64 - 1)))
 
-    # ---- the other Krylov methods on the same refined FP32 solve ----
+    # ---- the other Krylov methods on the same refined FP32 solve (on request) ----
     solver_cmp = {}
     # normal-equation CG needs many more iterations; it is timed on the smaller
     # workloads only
     others = ["bicgstab", "qmr", "bicgstab2", "gpbicg"] + (["petrkp"] if N <= 1_000_000 else [])
+    if not args.compare_solvers:
+        others = []
     for other in [s for s in others if s != args.solver]:
         kwo = dict(kw, solver=other)
         t.solve(w.kd, w.khat, w.e01, precision="fp32_refined", want_P=False, **kwo)
@@ -396,7 +448,9 @@ def run_gpu(args, rank, world, local_rank):
     cpu = None
     if world == 1:  # the host-core oracle baseline is taken at one GPU only
         v_cpu, dt_cpu, setup_cpu, it_cpu, c_cpu, sample = oracle_sample(w, 3)
+        ncpu, model = _host_cpu()
         cpu = {"value": v_cpu, "unit": UNIT, "cores": round(c_cpu, 2), "kind": "oracle",
+               "host_cores": ncpu, "cpu_model": model,
                "sample": sample + "; cores = process CPU time / wall time"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -404,11 +458,8 @@ def run_gpu(args, rank, world, local_rank):
         "ms_per_step": 1e3 * tot["dev_s"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 inner / c128 refinement", "data": "synthetic",
-        "config": {"workload": desc, "N": N, "box": list(w.shape), "grid": list(grid),
-                   "rhs": R, "precision": "fp32_refined", "tol": w.tol,
-                   "l2": "flushed between steps (256 MB write)",
-                   "schedule": schedule,
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "config": _config(w, desc, world),
+        "schedule": schedule,
         "solves_per_s": R * args.steps * world / tot["dev_s"],
         "latency_ms": {"p50": statistics.median(step_ms),
                        "p99": sorted(step_ms)[min(len(step_ms) - 1,
@@ -425,7 +476,7 @@ def run_gpu(args, rank, world, local_rank):
             "qext_rel_diff": qerr, "qext": [float(q) for q in qext],
             "resid_refined": [float(r) for r in resid]},
         "solver": args.solver,
-        "other_solvers": solver_cmp,
+        "other_solvers": solver_cmp or None,
         "setup_ms": setup["t_setup_ms"],
         "roofline": {"bound": "hbm", "kernel": f"k_fft_{dom} (fp32)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -452,7 +503,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="sphere64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sphere256", choices=sorted(WORKLOADS))
+    ap.add_argument("--compare-solvers", action="store_true",
+                    help="also time QMR, BiCGstab(2), GPBi-CG (and PETRKP up to 1 M dipoles)")
     ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "qmr", "bicgstab2", "gpbicg", "petrkp"],
                     help="Krylov method of the timed solves (the others are timed beside)")
     args = ap.parse_args()

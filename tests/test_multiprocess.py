@@ -87,3 +87,10 @@ def test_reference_arm_single_rank_line():
     assert d["impl"] == "reference" and d["n_gpus"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["cpu_baseline"]["host_cores"] >= 1 and d["cpu_baseline"]["cpu_model"]
+    # the same config object the GPU arm prints for this workload
+    sys.path.insert(0, ROOT)
+    import bench
+    from dda_inputs import workloads as W
+    assert d["config"] == bench._config(W.c1_sphere16(), bench.WORKLOADS["sphere16"][1], 1)
+    assert d["config"]["grid"] == [32, 32, 32]
