@@ -30,10 +30,11 @@ Contents, each citing the passage it follows:
                               "Near-Field Calculations", eq. macro_vs_micro)
 
 Readings where the guide is silent or garbled are stated at each function and
-collected in the design notes.  Parity of ``polarizability('LDR')``'s three
-coefficients b1, b2, b3 is unpinned (they come from Draine & Goodman 1993,
-which the guide cites without printing them); everything else is pinned by
-tests against closed forms, invariants or independent library routines.
+collected in the design notes.  LATTDR's coefficients b1, b2, b3 (Draine &
+Goodman 1993, cited by the guide without printing them) and the GKDLDR tensor
+form are pinned by the dispersion relation of the infinite lattice, evaluated
+by Ewald summation in the tests; everything else is pinned by tests against
+closed forms, invariants or independent library routines.
 """
 from __future__ import annotations
 
@@ -43,12 +44,14 @@ import numpy as np
 from scipy import special
 
 # LATTDR coefficients of Draine & Goodman (1993), cited by the guide (Sec.
-# "Point Dipoles: Options LATTDR and GKDLDR") without printing them.
+# "Point Dipoles: Options LATTDR and GKDLDR") without printing them.  They are
+# the (kd)^2 coefficients of the infinite cubic lattice's dipole sum for a wave
+# of index m (tests/test_oracle_lattice_dispersion.py derives them).
 LDR_B1 = -1.8915316
 LDR_B2 = 0.1648469
 LDR_B3 = -1.7700004
 
-METHODS = ("CM", "LDR", "FCD")
+METHODS = ("CM", "LDR", "FCD", "GKDLDR")
 
 
 # --------------------------------------------------------------------------
@@ -114,6 +117,8 @@ def polarizability(method: str, m: complex, kd: float, khat=None, e=None) -> com
         S = ldr_s(khat, e)
         return a0 / (1.0 + a0 * ((LDR_B1 + m2 * LDR_B2 + m2 * LDR_B3 * S) * k ** 2
                                  - (2.0 / 3.0) * 1j * k ** 3))
+    if method == "GKDLDR":
+        raise ValueError("GKDLDR is a tensor: use polarizability_tensor")
     if method == "FCD":
         logt = math.log((math.pi - k) / (math.pi + k))
         return a0 / (1.0 - a0 * ((4.0 / 3.0) * k ** 2
@@ -122,10 +127,49 @@ def polarizability(method: str, m: complex, kd: float, khat=None, e=None) -> com
     raise ValueError(f"unknown polarizability method {method!r}")
 
 
+def polarizability_tensor(method: str, m: complex, kd: float, khat=None, e=None):
+    """Diagonal of the polarizability tensor on the lattice axes x, y, z.
+
+    GKDLDR (Sec. "Point Dipoles: Options LATTDR and GKDLDR": the lattice
+    dispersion relation as corrected by Gutkowicz-Krusin & Draine 2004; the
+    guide does not print it):
+        alpha_a = alpha_CM / {1 + alpha_CM [(b1 + m^2 b2 + m^2 b3 khat_a^2)(kd)^2
+                                           - (2/3) i (kd)^3]},   a = x, y, z.
+    Reading: the lattice must carry a wave of index m along khat for BOTH
+    transverse polarizations, so the transverse block of 1/alpha must equal
+    that of the lattice's dipole sum; its (kd)^2 term is
+    (b1 + m^2 b2) I + m^2 b3 diag(khat_a^2) there (the Ewald test), which a
+    tensor diagonal on the lattice axes matches with khat_a^2 in place of
+    LATTDR's S = sum_a (khat_a e_a)^2 (S = e . diag(khat_a^2) . e for real e).
+    It does not depend on the polarization.  The scalar methods return their
+    alpha on all three axes.  Returns a complex [3] array (units d^3)."""
+    if method != "GKDLDR":
+        return np.full(3, polarizability(method, m, kd, khat, e), dtype=np.complex128)
+    a0 = alpha_cm(m)
+    k = float(kd)
+    m2 = complex(m) ** 2
+    kh = np.asarray(khat, dtype=np.float64)
+    kh = kh / np.linalg.norm(kh)
+    return np.array([a0 / (1.0 + a0 * ((LDR_B1 + m2 * LDR_B2 + m2 * LDR_B3 * kh[a] ** 2)
+                                       * k ** 2 - (2.0 / 3.0) * 1j * k ** 3))
+                     for a in range(3)])
+
+
 def site_alpha_inverse(comp_sites: np.ndarray, m_list, method, kd, khat=None, e=None):
-    """1/alpha_j for each occupied site (comp_sites in 1..ncomp)."""
+    """1/alpha_j for each occupied site (comp_sites in 1..ncomp): [N] for the
+    scalar methods, [N, 3] (the tensor's diagonal) for GKDLDR."""
+    idx = np.asarray(comp_sites, dtype=np.int64) - 1
+    if method == "GKDLDR":
+        inv = np.array([1.0 / polarizability_tensor(method, mm, kd, khat, e) for mm in m_list])
+        return inv[idx]
     inv = np.array([1.0 / polarizability(method, mm, kd, khat, e) for mm in m_list])
-    return inv[np.asarray(comp_sites, dtype=np.int64) - 1]
+    return inv[idx]
+
+
+def _per_axis(ainv: np.ndarray) -> np.ndarray:
+    """[N] or [N, 3] inverse polarizabilities as [N, 3]."""
+    ainv = np.asarray(ainv)
+    return np.repeat(ainv[:, None], 3, axis=1) if ainv.ndim == 1 else ainv
 
 
 # --------------------------------------------------------------------------
@@ -222,7 +266,8 @@ def green_fcd(dr: np.ndarray, kd: float) -> np.ndarray:
 
 
 def green(kind: str):
-    """Interaction tensor for a polarizability method: FCD uses the filtered one."""
+    """Interaction tensor for a polarizability method: FCD uses the filtered
+    one, the others (CM, LDR, GKDLDR) the point-dipole tensor."""
     return green_fcd if kind == "FCD" else green_point
 
 
@@ -254,6 +299,7 @@ def matvec_direct(P: np.ndarray, pos: np.ndarray, ainv: np.ndarray, kd: float,
     """
     G = green(method)
     N = pos.shape[0]
+    ai = _per_axis(ainv)
     rows = np.arange(N) if rows is None else np.asarray(rows)
     cb = N if col_block is None else int(col_block)
     out = np.empty((len(rows), 3), dtype=np.complex128)
@@ -268,7 +314,7 @@ def matvec_direct(P: np.ndarray, pos: np.ndarray, ainv: np.ndarray, kd: float,
             T = G(dr, kd)                                       # [b, n, 3, 3]
             T[self_mask] = 0.0
             field += np.einsum("bnij,nj->bi", T, P[cols])
-        out[s:s + block] = ainv[rb, None] * P[rb] - field
+        out[s:s + block] = ai[rb] * P[rb] - field
     return out
 
 
@@ -280,8 +326,9 @@ def dense_matrix(pos: np.ndarray, ainv: np.ndarray, kd: float, method: str = "LD
     dr[eye_mask] = 1.0
     T = -green(method)(dr, kd)
     T[eye_mask] = 0.0
+    ai = _per_axis(ainv)
     for j in range(N):
-        T[j, j] = ainv[j] * np.eye(3)
+        T[j, j] = np.diag(ai[j])
     return T.transpose(0, 2, 1, 3).reshape(3 * N, 3 * N)
 
 
@@ -335,7 +382,8 @@ class FFTOperator:
         for n, L in zip(self.box, self.grid):
             if L < 2 * n - 1:
                 raise ValueError("FFT grid smaller than 2n-1 wraps the convolution")
-        self.ainv = ainv_box  # [nz, ny, nx] complex (0 on vacant sites)
+        # [nz, ny, nx] complex (0 on vacant sites), or [3, nz, ny, nx] per axis
+        self.ainv = ainv_box if np.ndim(ainv_box) == 4 else np.asarray(ainv_box)[None]
         gg = fft_grid_green(self.box, self.grid, kd, method)
         self.ghat = np.fft.fftn(gg, axes=(1, 2, 3))
 
@@ -350,7 +398,7 @@ class FFTOperator:
         full = [[g[0], g[1], g[2]], [g[1], g[3], g[4]], [g[2], g[4], g[5]]]
         eh = np.stack([sum(full[a][b] * ph[b] for b in range(3)) for a in range(3)])
         field = np.fft.ifftn(eh, axes=(1, 2, 3))[:, :nz, :ny, :nx]
-        out = self.ainv[None] * Pbox - field
+        out = self.ainv * Pbox - field
         return out * self.occ[None]
 
 
@@ -382,7 +430,7 @@ class FFTOperatorLowMem:
         for n, L in zip(self.box, self.grid):
             if L < 2 * n - 1:
                 raise ValueError("FFT grid smaller than 2n-1 wraps the convolution")
-        self.ainv = ainv_box
+        self.ainv = ainv_box if np.ndim(ainv_box) == 4 else np.asarray(ainv_box)[None]
         self.workers = workers or os.cpu_count() or 1
         self._pool = ThreadPoolExecutor(self.workers)
         Lx, Ly, Lz = self.grid
@@ -422,7 +470,7 @@ class FFTOperatorLowMem:
         for a in range(3):
             self._pointwise_sum(eh, [(full[a][b], ph[b]) for b in range(3)])
             field = sfft.ifftn(eh, workers=self.workers)[:nz, :ny, :nx]
-            out[a] = self.ainv * Pbox[a] - field
+            out[a] = self.ainv[a if len(self.ainv) == 3 else 0] * Pbox[a] - field
             del field
         return out * self.occ[None]
 
@@ -474,7 +522,9 @@ def cross_sections(P: np.ndarray, E: np.ndarray, ainv: np.ndarray, kd: float):
     """(Q_ext, Q_abs, Q_sca) for one incident polarization with |E_0| = 1.
 
     C_ext = 4 pi k sum_j Im(E_inc,j^* . P_j)
-    C_abs = 4 pi k sum_j |P_j|^2 [-Im(1/alpha_j) - (2/3) k^3]     (scalar alpha)
+    C_abs = 4 pi k sum_j sum_a |P_ja|^2 [-Im(1/alpha_ja) - (2/3) k^3]
+    (the work done on each dipole component; for a scalar alpha the familiar
+    |P_j|^2 [-Im(1/alpha_j) - (2/3) k^3])
     Q = C / (pi a_eff^2), Q_sca = Q_ext - Q_abs (Sec. "What Does It
     Calculate?": Q_ext = Q_sca + Q_abs).
     """
@@ -482,8 +532,8 @@ def cross_sections(P: np.ndarray, E: np.ndarray, ainv: np.ndarray, kd: float):
     N = P.shape[0]
     aeff = effective_radius(N)
     cext = 4.0 * math.pi * k * float(np.sum(np.imag(np.conj(E) * P)))
-    p2 = np.sum(np.abs(P) ** 2, axis=1)
-    cabs = 4.0 * math.pi * k * float(np.sum(p2 * (-np.imag(ainv) - (2.0 / 3.0) * k ** 3)))
+    cabs = 4.0 * math.pi * k * float(np.sum(np.abs(P) ** 2 * (-np.imag(_per_axis(ainv))
+                                                              - (2.0 / 3.0) * k ** 3)))
     g = math.pi * aeff * aeff
     qext, qabs = cext / g, cabs / g
     return qext, qabs, qext - qabs
@@ -575,13 +625,13 @@ def solve_target(occ, comp, m_list, kd, khat, yhat, e01, method="LDR", npol=2,
             x, it, res = bicgstab(mv, E.reshape(-1), tol, maxiter)
             P = x.reshape(-1, 3)
         elif operator in ("fft", "fft_lowmem"):
-            ainv_box = np.zeros(occ.size, dtype=np.complex128)
-            ainv_box[flat] = ainv
+            ainv_box = np.zeros((3, occ.size), dtype=np.complex128)
+            ainv_box[:, flat] = _per_axis(ainv).T
             if operator == "fft":
-                op = FFTOperator(occ, ainv_box.reshape(occ.shape), kd, method, grid)
+                op = FFTOperator(occ, ainv_box.reshape((3,) + occ.shape), kd, method, grid)
             else:
-                op = FFTOperatorLowMem(occ, ainv_box.reshape(occ.shape), kd, method, grid,
-                                       workers)
+                op = FFTOperatorLowMem(occ, ainv_box.reshape((3,) + occ.shape), kd, method,
+                                       grid, workers)
             shape = occ.shape
 
             def mv(x):

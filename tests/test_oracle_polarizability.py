@@ -1,12 +1,14 @@
 """Pins for the oracle's polarizabilities (CPU only).
 
 The guide prints alpha_CM and the FLTRCD correction (Sec. "Filtered Coupled
-Dipole"); LATTDR's coefficients come from a cited paper.  What the physics fixes
-independently of those formulas: every prescription tends to Clausius-Mossotti
-as kd -> 0; a lossless material (real m) absorbs nothing, so
--Im(1/alpha) - (2/3) k^3 = 0 (the per-dipole absorption weight of C_abs); a
-lossy one absorbs (weight > 0); and a physical response obeys
-alpha(-k) = conj(alpha(k)) for real m.
+Dipole"); LATTDR's and GKDLDR's coefficients come from cited papers (they are
+derived from the lattice's dipole sum in test_oracle_lattice_dispersion.py).
+What the physics fixes independently of those formulas: every prescription
+tends to Clausius-Mossotti as kd -> 0; a lossless material (real m) absorbs
+nothing, so -Im(1/alpha) - (2/3) k^3 = 0 on every axis (the per-dipole
+absorption weight of C_abs); a lossy one absorbs (weight > 0); and a physical
+response obeys alpha(-k) = conj(alpha(k)) for real m.  Every check runs on the
+diagonal of the polarizability tensor (the scalar methods repeat alpha on it).
 """
 import math
 
@@ -35,8 +37,8 @@ def test_alpha_cm_limits():
 @pytest.mark.parametrize("method", dda.METHODS)
 @pytest.mark.parametrize("m", [1.33 + 0.01j, 1.7 + 0.1j, 0.9656 + 1.8628j])
 def test_static_limit_is_clausius_mossotti(method, m):
-    a = dda.polarizability(method, m, 1e-6, KH, EY)
-    assert abs(a / dda.alpha_cm(m) - 1.0) < 1e-9
+    a = dda.polarizability_tensor(method, m, 1e-6, np.array([0.36, 0.48, 0.8]), EY)
+    assert np.all(np.abs(a / dda.alpha_cm(m) - 1.0) < 1e-9)
 
 
 @pytest.mark.parametrize("method", dda.METHODS)
@@ -44,24 +46,24 @@ def test_static_limit_is_clausius_mossotti(method, m):
 @pytest.mark.parametrize("kd", [0.05, 0.2, 0.6])
 def test_lossless_material_does_not_absorb(method, m, kd):
     for e in (EY, np.array([0.0, 0.6, 0.8]), np.array([0, 1, 1j]) / math.sqrt(2)):
-        a = dda.polarizability(method, m, kd, np.array([0.6, 0.8, 0.0]) if method == "LDR"
-                               else KH, e)
-        assert abs(absorption_weight(a, kd)) < 1e-13 * abs(1.0 / a)
+        a = dda.polarizability_tensor(method, m, kd, np.array([0.6, 0.8, 0.0]), e)
+        assert np.all(np.abs(absorption_weight(a, kd)) < 1e-13 * np.abs(1.0 / a))
 
 
 @pytest.mark.parametrize("method", dda.METHODS)
 @pytest.mark.parametrize("m", [1.33 + 0.01j, 1.7 + 0.1j, 0.9656 + 1.8628j])
 def test_lossy_material_absorbs(method, m):
-    a = dda.polarizability(method, m, 0.3, KH, EY)
-    assert absorption_weight(a, 0.3) > 0.0
+    a = dda.polarizability_tensor(method, m, 0.3, np.array([0.6, 0.0, 0.8]), EY)
+    assert np.all(absorption_weight(a, 0.3) > 0.0)
 
 
 @pytest.mark.parametrize("method", dda.METHODS)
 def test_reality_condition(method):
     for kd in (0.1, 0.4, 0.9):
-        ap = dda.polarizability(method, 1.6, kd, KH, EY)
-        am = dda.polarizability(method, 1.6, -kd, KH, EY)
-        assert abs(am - np.conj(ap)) < 1e-14 * abs(ap)
+        kh = np.array([0.6, 0.0, 0.8])
+        ap = dda.polarizability_tensor(method, 1.6, kd, kh, EY)
+        am = dda.polarizability_tensor(method, 1.6, -kd, kh, EY)
+        assert np.all(np.abs(am - np.conj(ap)) < 1e-14 * np.abs(ap))
 
 
 def test_literal_fltrcd_formula_fails_the_physical_pins():
@@ -84,13 +86,14 @@ def test_ldr_s_factor():
     assert abs(dda.ldr_s(kh, e) - 1.0 / 3.0) < 1e-15
 
 
-def test_ldr_absorption_weight_closed_form():
-    """With alpha = alpha_CM / (1 + alpha_CM c), 1/alpha = 1/alpha_CM + c, so the
-    absorption weight is -Im(1/alpha_CM) - Im(b2 + b3 S) m^2 (kd)^2."""
+def test_gkdldr_equals_ldr_on_the_axes_of_a_linear_polarization():
+    """For a wave along a lattice axis with e along another, GKDLDR's alpha on
+    the two transverse axes equals LATTDR's (S = 0 = khat_a^2 there); along the
+    propagation axis it differs (khat_x^2 = 1)."""
     m, kd = 1.5 + 0.2j, 0.25
-    kh = np.array([0.0, 0.6, 0.8])
-    e = np.array([1.0, 0.0, 0.0])
-    a = dda.polarizability("LDR", m, kd, kh, e)
-    S = dda.ldr_s(kh, e)
-    expect = -np.imag(1 / dda.alpha_cm(m)) - np.imag((dda.LDR_B2 + dda.LDR_B3 * S) * m * m) * kd ** 2
-    assert abs(absorption_weight(a, kd) - expect) < 1e-13
+    a = dda.polarizability_tensor("GKDLDR", m, kd, KH, EY)
+    ldr = dda.polarizability("LDR", m, kd, KH, EY)
+    assert abs(a[1] / ldr - 1) < 1e-15 and abs(a[2] / ldr - 1) < 1e-15
+    assert abs(a[0] / ldr - 1) > 1e-3
+    with pytest.raises(ValueError):
+        dda.polarizability("GKDLDR", m, kd, KH, EY)
