@@ -59,9 +59,23 @@ typedef enum {
  *       Dipole", read with the sign and (kd)^3 factor that make a lossless
  *       material absorb nothing), and the interaction tensor is the filtered one,
  *       (k^2 + grad grad) of the outgoing Green function with spatial
- *       frequencies above pi/d removed.  CM and LDR use the point-dipole tensor
+ *       frequencies above pi/d removed.
+ *  GKDLDR: the lattice dispersion relation as corrected by Gutkowicz-Krusin &
+ *       Draine (2004), the guide's recommended option (Sec. "Point Dipoles:
+ *       Options LATTDR and GKDLDR"): a polarizability TENSOR, diagonal on the
+ *       lattice axes, alpha_a = alpha_CM / {1 + alpha_CM [(b1 + m^2 b2 +
+ *       m^2 b3 khat_a^2)(kd)^2 - (2/3) i (kd)^3]} for a = x, y, z, with LATTDR's
+ *       coefficients; it depends on each incident direction, not on the
+ *       polarization, and makes the infinite lattice carry a wave of index m
+ *       for both transverse polarizations.
+ *  CM, LDR and GKDLDR use the point-dipole tensor
  *       G(r) P = e^{ikr}/r^3 {k^2 r^2 (rhat x P) x rhat + (1-ikr)[3 rhat(rhat.P) - P]}. */
-typedef enum { DDA_POL_CM = 0, DDA_POL_LDR = 1, DDA_POL_FCD = 2 } dda_pol_method;
+typedef enum {
+  DDA_POL_CM = 0,
+  DDA_POL_LDR = 1,
+  DDA_POL_FCD = 2,
+  DDA_POL_GKDLDR = 3
+} dda_pol_method;
 
 /* Arithmetic of the solve.
  *  FP64        : every step in FP64.
@@ -137,8 +151,8 @@ dda_status dda_set_polarizability(dda_target* t, dda_pol_method method);
 
 /* y = A x for one incident wave (the hot loop's operator, eq. AP=E).
  *  kd        : k d (> 0, < pi for FCD).
- *  khat, e   : incident direction [3] and polarization [3][2] (only LDR reads
- *              them; may be NULL otherwise).
+ *  khat, e   : incident direction [3] and polarization [3][2] (LDR reads both,
+ *              GKDLDR khat only; may be NULL otherwise).
  *  x, y      : [N][3][2] on the occupied sites in flat-index order (host).
  *  precision : DDA_PREC_FP64, DDA_PREC_DF64 (FP64 vectors, double-float FFT
  *              passes) or DDA_PREC_FP32 (FP32_REFINED acts as FP32). */
@@ -165,7 +179,7 @@ dda_status dda_matvec(dda_target* t, double kd, const double* khat, const double
  *  cuda_stream  : cudaStream_t to run on, or NULL for the target's own stream;
  *                 the call returns after the work on that stream has finished.
  * Limit: 3*nz*Ly*Lx complex values of the chosen precision must fit in 64 MiB
- * minus 4 KiB (with L = 2n: cubic boxes up to 88^3 in FP32, 70^3 in FP64);
+ * minus 12 KiB (with L = 2n: cubic boxes up to 88^3 in FP32, 70^3 in FP64);
  * larger targets get DDA_ERR_INVALID_ARG with the sizes in dda_last_error().
  * The 64 MiB are committed on a device when the first target is created there:
  * dda_target_create looks up the array's device address (which loads the part

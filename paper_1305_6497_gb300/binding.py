@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libdda.so")
 
 DDA_OK, DDA_ERR_INVALID_ARG, DDA_ERR_OOM, DDA_ERR_CUDA, DDA_ERR_NOCONV, \
     DDA_ERR_BREAKDOWN, DDA_ERR_TIMEOUT = range(7)
-POL = {"CM": 0, "LDR": 1, "FCD": 2}
+POL = {"CM": 0, "LDR": 1, "FCD": 2, "GKDLDR": 3}
 PREC = {"fp64": 0, "fp32": 1, "fp32_refined": 2, "df64": 3}
 SOLVER = {"bicgstab": 0, "qmr": 1, "bicgstab2": 2, "gpbicg": 3, "petrkp": 4}
 

@@ -409,6 +409,51 @@ static cd alpha_of(dda_pol_method meth, cd m, double kd, const double* khat, con
                            (2.0 / 3.0) * I * k3));
 }
 
+// The polarizability tensor's diagonal on the lattice axes x, y, z.  GKDLDR
+// (Sec. "Point Dipoles: Options LATTDR and GKDLDR"; Gutkowicz-Krusin & Draine
+// 2004): alpha_a = alpha_CM / {1 + alpha_CM [(b1 + m^2 b2 + m^2 b3 khat_a^2)
+// (kd)^2 - (2/3) i (kd)^3]} -- the lattice dispersion relation satisfied for
+// both transverse polarizations of a wave along khat (LATTDR's S replaced by
+// khat_a^2 on each axis); it does not depend on the polarization.  The scalar
+// prescriptions put their alpha on all three axes.
+static void alpha3_of(dda_pol_method meth, cd m, double kd, const double* khat, const cd* e,
+                      cd out[3]) {
+  if (meth != DDA_POL_GKDLDR) {
+    out[0] = out[1] = out[2] = alpha_of(meth, m, kd, khat, e);
+    return;
+  }
+  const double pi = 3.14159265358979323846;
+  const cd m2 = m * m;
+  const cd a0 = 3.0 / (4.0 * pi) * (m2 - 1.0) / (m2 + 2.0);
+  const cd I(0.0, 1.0);
+  const double k3 = kd * kd * kd;
+  for (int a = 0; a < 3; ++a)
+    out[a] = a0 / (1.0 + a0 * ((kLdrB1 + m2 * kLdrB2 + m2 * kLdrB3 * khat[a] * khat[a]) * kd * kd -
+                               (2.0 / 3.0) * I * k3));
+}
+
+// One right-hand side's alpha^{-1} table, [ncomp+1][3] (entry 0 unused, 0):
+// FP64 and FP32 copies and, when wabs is given, the absorption weights
+// -Im(alpha^{-1}) - (2/3) k^3 of C_abs on each axis.
+static void ainv_table(const dda_target* t, double kd, const double* khat, const cd* e,
+                       double2* a64, float2* a32, double* wabs) {
+  for (int a = 0; a < 3; ++a) {
+    a64[a] = make_double2(0, 0);
+    a32[a] = make_float2(0, 0);
+    if (wabs) wabs[a] = 0.0;
+  }
+  for (int c = 1; c <= t->ncomp; ++c) {
+    cd al[3];
+    alpha3_of(t->method, t->m[c - 1], kd, khat, e, al);
+    for (int a = 0; a < 3; ++a) {
+      const cd v = 1.0 / al[a];
+      a64[3 * c + a] = make_double2(v.real(), v.imag());
+      a32[3 * c + a] = make_float2((float)v.real(), (float)v.imag());
+      if (wabs) wabs[3 * c + a] = -v.imag() - (2.0 / 3.0) * kd * kd * kd;
+    }
+  }
+}
+
 struct Incidence {
   double khat[3];
   double yhat[3];
@@ -1142,10 +1187,10 @@ static void ensure_workspace(dda_target* t, int R, dda_precision prec, int ndir)
   w.sums.ensure(sizeof(double) * 6 * (size_t)std::max(R, 2 * (ndir + 1)));
   w.pol.ensure(sizeof(double2) * 3 * R);
   w.ph.ensure(sizeof(double2) * (size_t)R * (t->nx + t->ny + t->nz));
-  w.ainv64.ensure(sizeof(double2) * (size_t)R * (t->ncomp + 1));
-  w.ainv32.ensure(sizeof(float2) * (size_t)R * (t->ncomp + 1));
-  w.ainvdf.ensure(sizeof(df64c) * (size_t)R * (t->ncomp + 1));
-  w.wabs.ensure(sizeof(double) * (size_t)R * (t->ncomp + 1));
+  w.ainv64.ensure(sizeof(double2) * (size_t)R * (t->ncomp + 1) * 3);
+  w.ainv32.ensure(sizeof(float2) * (size_t)R * (t->ncomp + 1) * 3);
+  w.ainvdf.ensure(sizeof(df64c) * (size_t)R * (t->ncomp + 1) * 3);
+  w.wabs.ensure(sizeof(double) * (size_t)R * (t->ncomp + 1) * 3);
   w.fph.ensure(sizeof(double2) * (size_t)(ndir + 1) * (t->nx + t->ny + t->nz));
   w.sitebuf.ensure(sizeof(double2) * 3 * (size_t)t->N * R);
   w.R = R;
@@ -1319,7 +1364,8 @@ dda_status dda_target_create(int nx, int ny, int nz, const uint8_t* occ, const u
 
 dda_status dda_set_polarizability(dda_target* t, dda_pol_method method) {
   if (!t) return fail(DDA_ERR_INVALID_ARG, "target is NULL");
-  if (method != DDA_POL_CM && method != DDA_POL_LDR && method != DDA_POL_FCD)
+  if (method != DDA_POL_CM && method != DDA_POL_LDR && method != DDA_POL_FCD &&
+      method != DDA_POL_GKDLDR)
     return fail(DDA_ERR_INVALID_ARG, "unknown polarizability method");
   t->method = method;
   return DDA_OK;
@@ -1360,7 +1406,7 @@ int64_t dda_target_device_bytes(const dda_target* t) {
 int64_t dda_estimate_solve_bytes(int nx, int ny, int nz, int64_t n_dipoles, int ncomp,
                                  int method, const dda_solve_params* p) {
   if (nx < 1 || ny < 1 || nz < 1 || nx > 1024 || ny > 1024 || nz > 1024 || ncomp < 1 ||
-      ncomp > 255 || method < DDA_POL_CM || method > DDA_POL_FCD)
+      ncomp > 255 || method < DDA_POL_CM || method > DDA_POL_GKDLDR)
     return -1;
   const int64_t nbox = (int64_t)nx * ny * nz;
   if (n_dipoles < 1 || n_dipoles > nbox) return -1;
@@ -1384,6 +1430,23 @@ int64_t dda_estimate_solve_bytes(int nx, int ny, int nz, int64_t n_dipoles, int 
   return created + solve;
 }
 
+// The incident direction and polarization a single-wave call needs for the
+// target's polarizability (LDR reads both, GKDLDR the direction only).
+static dda_status incidence_of(const dda_target* t, const double* khat, const double* e,
+                               double kh[3], cd ev[3]) {
+  const bool need_k = t->method == DDA_POL_LDR || t->method == DDA_POL_GKDLDR;
+  const bool need_e = t->method == DDA_POL_LDR;
+  if (!need_k) return DDA_OK;
+  if (!khat || (need_e && !e)) return fail(DDA_ERR_INVALID_ARG, "LDR needs khat and e, GKDLDR khat");
+  const double kn = std::sqrt(khat[0] * khat[0] + khat[1] * khat[1] + khat[2] * khat[2]);
+  if (!(kn > 0)) return fail(DDA_ERR_INVALID_ARG, "khat is zero");
+  for (int c = 0; c < 3; ++c) {
+    kh[c] = khat[c] / kn;
+    if (need_e) ev[c] = cd(e[2 * c], e[2 * c + 1]);
+  }
+  return DDA_OK;
+}
+
 static dda_status check_kd(const dda_target* t, double kd) {
   if (!(kd > 0.0) || !std::isfinite(kd)) return fail(DDA_ERR_INVALID_ARG, "kd must be > 0");
   if (t->method == DDA_POL_FCD && !(kd < 3.14159265358979323846))
@@ -1399,12 +1462,8 @@ dda_status dda_matvec(dda_target* t, double kd, const double* khat, const double
   if (s != DDA_OK) return s;
   double kh[3] = {1, 0, 0};
   cd ev[3] = {0.0, 1.0, 0.0};
-  if (t->method == DDA_POL_LDR) {
-    if (!khat || !e) return fail(DDA_ERR_INVALID_ARG, "LDR needs khat and e");
-    double kn = std::sqrt(khat[0] * khat[0] + khat[1] * khat[1] + khat[2] * khat[2]);
-    if (!(kn > 0)) return fail(DDA_ERR_INVALID_ARG, "khat is zero");
-    for (int c = 0; c < 3; ++c) { kh[c] = khat[c] / kn; ev[c] = cd(e[2 * c], e[2 * c + 1]); }
-  }
+  s = incidence_of(t, khat, e, kh, ev);
+  if (s != DDA_OK) return s;
   try {
     CK(cudaSetDevice(t->device));
     const int filtered = t->method == DDA_POL_FCD ? 1 : 0;
@@ -1414,13 +1473,9 @@ dda_status dda_matvec(dda_target* t, double kd, const double* khat, const double
     ensure_workspace(t, 1, f32 ? DDA_PREC_FP32 : DDA_PREC_FP64, 0);
     configure(t);
     Workspace& w = t->ws;
-    std::vector<double2> ai(t->ncomp + 1, make_double2(0, 0));
-    std::vector<float2> ai32(t->ncomp + 1, make_float2(0, 0));
-    for (int c = 1; c <= t->ncomp; ++c) {
-      cd a = 1.0 / alpha_of(t->method, t->m[c - 1], kd, kh, ev);
-      ai[c] = make_double2(a.real(), a.imag());
-      ai32[c] = make_float2((float)a.real(), (float)a.imag());
-    }
+    std::vector<double2> ai(3 * (t->ncomp + 1));
+    std::vector<float2> ai32(3 * (t->ncomp + 1));
+    ainv_table(t, kd, kh, ev, ai.data(), ai32.data(), nullptr);
     cudaStream_t st = t->stream;
     CK(cudaMemcpyAsync(w.ainv64.p, ai.data(), sizeof(double2) * ai.size(),
                        cudaMemcpyHostToDevice, st));
@@ -1522,23 +1577,19 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
     CK(cudaEventRecord(t->ev0, st));
     // ---- per-RHS tables ----
     const int nc1 = t->ncomp + 1;
-    std::vector<double2> pol(3 * R), ph, ai(R * nc1), fph;
-    std::vector<float2> ai32(R * nc1);
-    std::vector<double> wabs(R * nc1, 0.0);
+    // alpha^{-1} tables [R][ncomp+1][3]: one entry per lattice axis
+    std::vector<double2> pol(3 * R), ph, ai(3 * R * nc1), fph;
+    std::vector<float2> ai32(3 * R * nc1);
+    std::vector<double> wabs(3 * R * nc1, 0.0);
     const double k3 = kd * kd * kd;
     for (int i = 0; i < p->n_inc; ++i)
       for (int l = 0; l < p->npol; ++l) {
         const int r = i * p->npol + l;
         for (int c = 0; c < 3; ++c)
           pol[3 * r + c] = make_double2(incs[i].e[l][c].real(), incs[i].e[l][c].imag());
-        ai[r * nc1] = make_double2(0, 0);
-        ai32[r * nc1] = make_float2(0, 0);
-        for (int c = 1; c < nc1; ++c) {
-          const cd a = 1.0 / alpha_of(t->method, t->m[c - 1], kd, incs[i].khat, incs[i].e[l]);
-          ai[r * nc1 + c] = make_double2(a.real(), a.imag());
-          ai32[r * nc1 + c] = make_float2((float)a.real(), (float)a.imag());
-          wabs[r * nc1 + c] = -a.imag() - (2.0 / 3.0) * k3;
-        }
+        const size_t o = (size_t)3 * r * nc1;
+        ainv_table(t, kd, incs[i].khat, incs[i].e[l], ai.data() + o, ai32.data() + o,
+                   wabs.data() + o);
       }
     // phases: all x tables, then y, then z
     for (int r = 0; r < R; ++r) axis_phase(t->nx, kd, incs[r / p->npol].khat[0], 1.0, ph);
@@ -2122,7 +2173,7 @@ dda_status dda_target_schedule(const dda_target* t, int precision, int* out8) {
 namespace {
 
 constexpr size_t kStaticScratchBytes = 64ull << 20;  // 64 MiB per device
-constexpr size_t kStaticAinvBytes = 4096;            // 256 complex FP64 entries
+constexpr size_t kStaticAinvBytes = 12288;           // 256 x 3 complex FP64 entries
 
 // Held by every GPU that loads this library, until the process exits.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -2178,28 +2229,20 @@ dda_status dda_matvec_noalloc(dda_target* t, double kd, const double* khat, cons
                 "dda_matvec or dda_solve once with them first (building it allocates)");
   double kh[3] = {1, 0, 0};
   cd ev[3] = {0.0, 1.0, 0.0};
-  if (t->method == DDA_POL_LDR) {
-    if (!khat || !e) return fail(DDA_ERR_INVALID_ARG, "LDR needs khat and e");
-    double kn = std::sqrt(khat[0] * khat[0] + khat[1] * khat[1] + khat[2] * khat[2]);
-    if (!(kn > 0)) return fail(DDA_ERR_INVALID_ARG, "khat is zero");
-    for (int c = 0; c < 3; ++c) { kh[c] = khat[c] / kn; ev[c] = cd(e[2 * c], e[2 * c + 1]); }
-  }
+  s = incidence_of(t, khat, e, kh, ev);
+  if (s != DDA_OK) return s;
   try {
     CK(cudaSetDevice(t->device));
     void* base = nullptr;
     CK(static_scratch_address(t->device, &base));  // resolved by dda_target_create
     cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : t->stream;
     unsigned char* area = reinterpret_cast<unsigned char*>(base);
-    // alpha^{-1} per composition (entry 0 unused) at the start of the area
-    double2 ai64[256];
-    float2 ai32[256];
-    for (int c = 0; c <= t->ncomp; ++c) { ai64[c] = make_double2(0, 0); ai32[c] = make_float2(0, 0); }
-    for (int c = 1; c <= t->ncomp; ++c) {
-      const cd a = 1.0 / alpha_of(t->method, t->m[c - 1], kd, kh, ev);
-      ai64[c] = make_double2(a.real(), a.imag());
-      ai32[c] = make_float2((float)a.real(), (float)a.imag());
-    }
-    const size_t nai = (size_t)(t->ncomp + 1);
+    // alpha^{-1} per composition and lattice axis (entry 0 unused) at the
+    // start of the area
+    double2 ai64[3 * 256];
+    float2 ai32[3 * 256];
+    ainv_table(t, kd, kh, ev, ai64, ai32, nullptr);
+    const size_t nai = (size_t)3 * (t->ncomp + 1);
     // the spectral scratch needs no clearing: every element the passes read was
     // written earlier in the same call
     if (f32) {

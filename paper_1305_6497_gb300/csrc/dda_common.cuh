@@ -160,7 +160,8 @@ template <typename T> struct OpView {
   int64_t nbox;                   // nx*ny*nz
   const uint8_t* comp;            // [nbox] 0 = vacant, else composition 1..ncomp
   const C* ghat;                  // [Hz][Hy][Hx][6], already divided by Lx*Ly*Lz
-  const C* ainv;                  // [R][ncomp+1] alpha^{-1} per RHS, entry 0 unused
+  const C* ainv;                  // [R][ncomp+1][3] alpha^{-1} per RHS and lattice axis
+                                  // (the polarizability tensor's diagonal), entry 0 unused
   int ncomp1;                     // ncomp + 1
   const C* twx; const C* twy; const C* twz;
   const int* kx_at; const int* ky_at; const int* kz_at;  // frequency held at each

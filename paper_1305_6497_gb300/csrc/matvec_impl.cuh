@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   // only positions < nx <= Lx/2 are used below
   if constexpr (std::is_void<P>::value) fft_smem<C, true>(s, nlines, ps, op.px, op.twx, 2 * nx <= Lx);
   else fft_smem_p<C, true, P>(s, nlines, div_nl, ps, op.twx, 2 * nx <= Lx);
-  const C* ai = op.ainv + (int64_t)r * op.ncomp1;
+  const C* ai = op.ainv + (int64_t)r * op.ncomp1 * 3;
   IO* yr = yout + g0;
   // (df64 passes only run the plain epilogue; their accumulator type is unused)
   ChunkAcc<std::conditional_t<std::is_same<T, df64>::value, double, T>, 4> acc;
@@ -854,10 +854,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
       if (e < nin && MODE != XOUT_FIELD) {
         const int line = fast_div(e, op.div_nx), p = e - line * nx;
         const int row = row0 + line;
-        // row = (c nz + z) ny + y  ->  site (z ny + y) nx + p
+        // row = (c nz + z) ny + y  ->  site (z ny + y) nx + p; the alpha^{-1}
+        // entry of composition cm on axis c is 3 cm + c (0: vacant)
         const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
-        const int z = plane - fast_div(plane, op.div_nz) * op.nz;
-        cms[u] = op.comp[((int64_t)z * op.ny + y) * nx + p];
+        const int c = fast_div(plane, op.div_nz);
+        const int z = plane - c * op.nz;
+        const int cm = op.comp[((int64_t)z * op.ny + y) * nx + p];
+        cms[u] = cm ? 3 * cm + c : 0;
       }
     }
 #pragma unroll

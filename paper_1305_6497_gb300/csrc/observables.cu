@@ -1,7 +1,8 @@
 // Cross sections and scattering amplitudes from the solved dipole moments.
 //
 //  C_ext = 4 pi k sum_j Im(E_inc,j^* . P_j)
-//  C_abs = 4 pi k sum_j |P_j|^2 [-Im(1/alpha_j) - (2/3) k^3]
+//  C_abs = 4 pi k sum_j sum_a |P_ja|^2 [-Im(1/alpha_ja) - (2/3) k^3]  (a: lattice
+//          axis; alpha's diagonal, equal on the axes except for GKDLDR)
 //  (Sec. "What Does It Calculate?": Q = C / (pi a_eff^2), Q_ext = Q_sca + Q_abs)
 //  F(n) = sum_j P_j exp(-i k n . r_j), f_ml = k^3 e_m . F  (eq. f_ml_def)
 //
@@ -38,9 +39,9 @@ __global__ void k_cross_sections(int nx, int ny, int nz, const uint8_t* __restri
       double2 ep = cadd(cadd(cmulc(e0, p0), cmulc(e1, p1)), cmulc(e2, p2));
       ep = cmulc(ph, ep);
       acc[0] += ep.y;
-      const double pp = p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y +
-                        p2.x * p2.x + p2.y * p2.y;
-      acc[1] += pp * wabs[r * ncomp1 + cm];
+      const double* wa = wabs + ((int64_t)r * ncomp1 + cm) * 3;
+      acc[1] += (p0.x * p0.x + p0.y * p0.y) * wa[0] + (p1.x * p1.x + p1.y * p1.y) * wa[1] +
+                (p2.x * p2.x + p2.y * p2.y) * wa[2];
     }
   }
   write_partials<2>(acc, partials);

@@ -4,8 +4,8 @@ FP64: max |y_gpu - y_oracle| / max |y_oracle| <= 1e-10 (the tolerance the
 method is held to for A.P).  FP32: <= 2e-5 (single-precision FFT of lengths up
 to a few hundred: ~log2(L) * 2^-24 per pass, times five passes, with margin).
 Cases span several tiles, ragged edges, vacancies, two materials, degenerate
-one-site and one-line boxes, 2/3/5-smooth grids and all three polarizability
-prescriptions.
+one-site and one-line boxes, 2/3/5-smooth grids and all four polarizability
+prescriptions (GKDLDR's tensor: a different alpha^{-1} on each lattice axis).
 """
 import numpy as np
 import pytest
@@ -37,9 +37,9 @@ def _case(occ, comp, m, kd, method, khat, e, seed=5):
 def _ref(occ, pos, ainv, x, kd, method, flat):
     if len(pos) <= 3000:
         return O.matvec_direct(x, pos, ainv, kd, method)
-    ainv_box = np.zeros(occ.size, np.complex128)
-    ainv_box[flat] = ainv
-    op = O.FFTOperator(occ, ainv_box.reshape(occ.shape), kd, method)
+    ainv_box = np.zeros((3, occ.size), np.complex128)
+    ainv_box[:, flat] = (np.repeat(ainv[:, None], 3, axis=1) if ainv.ndim == 1 else ainv).T
+    op = O.FFTOperator(occ, ainv_box.reshape((3,) + occ.shape), kd, method)
     return O.box_to_sites(op(O.sites_to_box(x, flat, occ.shape)), flat)
 
 
@@ -77,7 +77,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("name,mk,m", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("method", ["LDR", "CM", "FCD"])
+@pytest.mark.parametrize("method", ["LDR", "CM", "FCD", "GKDLDR"])
 def test_matvec_fp64_matches_oracle(B, name, mk, m, method):
     occ, comp = mk()
     kd = 0.37

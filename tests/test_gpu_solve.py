@@ -39,7 +39,7 @@ def _check(out, ref, r0=0, tolq=1e-6, tolp=1e-6):
         assert perr < tolp, (r, perr)
 
 
-@pytest.mark.parametrize("method", ["LDR", "CM", "FCD"])
+@pytest.mark.parametrize("method", ["LDR", "CM", "FCD", "GKDLDR"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
 def test_solve_small_ellipsoid(B, method, precision):
     w = W.small_ellipsoid(6, 10, 12, m=1.5 + 0.1j, kd=0.4, method=method)
@@ -482,3 +482,31 @@ def test_solve_on_a_callers_stream_is_bit_identical(B):
     assert np.array_equal(out["P"], ref["P"])
     assert np.array_equal(out["famp"], ref["famp"])
     t.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32_refined", "fp64"])
+def test_guide_worked_example_gkdldr(B, precision):
+    """The guide's appendix example (RCTGLPRSM 16x32x32 Au brick, GKDLDR, k d =
+    0.19635, m = 0.9656 + 1.8628i): Q_ext 3.6134, Q_abs 1.4308, Q_sca 2.1827,
+    S_11(0) 75.115, S_11(180) 18.591 as printed, to 1e-4 relative, and the
+    oracle's values to 1e-6."""
+    occ, comp = tg.rect_prism(16, 32, 32)
+    kd = 3.093665 * 0.06346821
+    m = 0.9656 + 1.8628j
+    t = B.Target(occ, comp, [m], method="GKDLDR")
+    out = t.solve(kd, [1, 0, 0], [0, 1, 0], yhat=[0, 1, 0], npol=2, tol=1e-8,
+                  precision=precision, dirs=np.array([(math.pi, 0.0)]), want_P=False)
+    t.close()
+    assert out["status"] == B.DDA_OK
+    f = out["famp"][0]
+    s11 = 0.5 * np.sum(np.abs(f) ** 2, axis=(1, 2))
+    qext, qabs = np.mean(out["Qext"]), np.mean(out["Qabs"])
+    got = dict(qext=qext, qabs=qabs, qsca=qext - qabs, s0=s11[0], s180=s11[1])
+    printed = dict(qext=3.6134, qabs=1.4308, qsca=2.1827, s0=75.115, s180=18.591)
+    for key, v in printed.items():
+        assert abs(got[key] / v - 1) < 1e-4, (key, got[key], v)
+    ref = O.solve_target(occ, comp, [m], kd, [1, 0, 0], [0, 1, 0], [0, 1, 0], "GKDLDR",
+                         tol=1e-11)
+    for l in range(2):
+        assert abs(out["Qext"][l] / ref["Qext"][l] - 1) < 1e-6
+        assert abs(out["Qabs"][l] / ref["Qabs"][l] - 1) < 1e-6

@@ -35,7 +35,7 @@ def _err(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("method", ["LDR", "FCD"])
+@pytest.mark.parametrize("method", ["LDR", "FCD", "GKDLDR"])
 def test_noalloc_matvec_matches_matvec_twice(method):
     import torch
     from paper_1305_6497_gb300 import binding as B
