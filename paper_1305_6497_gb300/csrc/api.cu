@@ -264,6 +264,14 @@ struct IterGraph {
   }
 };
 
+// A device-side loop over blocks of iterations: a CUDA graph whose while-node
+// runs the block (captured once) until every right-hand side is frozen or a
+// cap on the blocks is reached, so a whole solve is one graph launch.
+struct LoopGraph {
+  IterGraph g;
+  long long body_kernels = 0;  // kernels per body run (incl. the loop test)
+};
+
 struct dda_target {
   int nx = 0, ny = 0, nz = 0;
   int64_t nbox = 0, N = 0;
@@ -292,6 +300,9 @@ struct dda_target {
   Workspace ws;
   Profiler prof;
   IterGraph graphs[2];  // FP32, FP64 (for the solver that ran last)
+  LoopGraph loops[2];   // the same blocks as device-side loops
+  DevBuf loopctl;       // [2] ints: blocks run, block cap
+  int loopctl_host[2] = {0, 0};
   int schedule_gen = 0;  // bumped when the launch schedule changes
   // near field: the target embedded in an extended box (vacant around it)
   dda_target* nf = nullptr;
@@ -322,6 +333,7 @@ static OpView<T> make_view(const dda_target* t, const void* ghat, const void* ai
   v.kx_at = pm;
   v.ky_at = pm + t->Lx;
   v.kz_at = pm + t->Lx + t->Ly;
+  v.ypos_at = pm + (t->Lx + t->Ly + t->Lz) + t->Lx;
   v.px = t->px; v.py = t->py; v.pz = t->pz;
   auto magic = [](int d) { return ((1ull << 36) + (unsigned long long)d - 1) / (unsigned long long)d; };
   v.div_nx = magic(v.nx); v.div_ny = magic(v.ny); v.div_nz = magic(v.nz); v.div_Lx = magic(v.Lx);
@@ -509,6 +521,70 @@ static void axis_phase(int n, double kd, double u, double sgn, std::vector<doubl
   }
 }
 
+// Runs blocks of iterations (enqueue() queues one block) on the device until
+// no right-hand side is active or max_blocks blocks have run, as ONE launch of
+// a CUDA graph with a while-node (built on first use, rebuilt when `sig`
+// changes); then refreshes hact.  Returns the blocks run.  Without profiling
+// only: event records are not allowed inside a while-node's body.
+template <class ENQ>
+static int run_device_loop(dda_target* t, int slot, const std::vector<uintptr_t>& sig,
+                           int max_blocks, std::vector<int>& hact, const ENQ& enqueue) {
+  cudaStream_t st = t->stream;
+  int* act = t->ws.active.as<int>();
+  const int R = (int)hact.size();
+  t->loopctl.ensure(2 * sizeof(int));
+  int* ctl = t->loopctl.as<int>();
+  LoopGraph& lg = t->loops[slot];
+  if (lg.g.exec && lg.g.sig != sig) lg.g.reset();
+  if (!lg.g.exec) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaGraphCreate(&graph, 0));
+    try {
+      cudaGraphConditionalHandle h;
+      CK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams np{};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      CK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      const long long before = launch_count();
+      CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal));
+      try {
+        enqueue();
+        CK(launch_loop_continue(h, act, R, ctl, st));
+      } catch (...) {
+        cudaGraph_t broken = nullptr;
+        cudaStreamEndCapture(st, &broken);
+        throw;
+      }
+      cudaGraph_t captured = nullptr;
+      CK(cudaStreamEndCapture(st, &captured));
+      lg.body_kernels = launch_count() - before;
+      note_launches(-lg.body_kernels);  // captured, not run
+      CK(cudaGraphInstantiate(&lg.g.exec, graph, 0));
+    } catch (...) {
+      cudaGraphDestroy(graph);
+      throw;
+    }
+    cudaGraphDestroy(graph);
+    lg.g.sig = sig;
+  }
+  t->loopctl_host[0] = 0;
+  t->loopctl_host[1] = max_blocks;
+  CK(cudaMemcpyAsync(ctl, t->loopctl_host, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaGraphLaunch(lg.g.exec, st));
+  CK(cudaMemcpyAsync(t->loopctl_host, ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int blocks = t->loopctl_host[0];
+  note_launches(lg.body_kernels * blocks);
+  return blocks;
+}
+
 // ---------------------------------------------------------------------------
 // BiCGSTAB driver, R RHS in lockstep on the device.  Returns the number of
 // iterations per RHS through `its` and the status per RHS.
@@ -593,6 +669,19 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
     g.kernels = launch_count() - before;
     note_launches(-g.kernels);  // captured, not run
     g.sig = sig;
+  }
+  // without per-pass profiling the full blocks run as one device-side loop
+  // (a single graph launch); the host loop below then only runs a remainder
+  // shorter than a block, or every block when profiling
+  if (!t->prof.on && nact > 0 && max_iter - iter >= kCheckEvery) {
+    std::vector<uintptr_t> wsig = sig;
+    wsig.push_back(7);
+    const int nb = run_device_loop(t, sizeof(T) == 4 ? 0 : 1, wsig,
+                                   (max_iter - iter) / kCheckEvery, hact,
+                                   [&]() { enqueue_block(kCheckEvery); });
+    iter += nb * kCheckEvery;
+    nact = 0;
+    for (int a : hact) nact += a;
   }
   while (nact > 0 && iter < max_iter) {
     // kCheckEvery iterations are queued back to back; a converged RHS is frozen
@@ -701,6 +790,19 @@ static void qmr(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R
     g.kernels = launch_count() - before;
     note_launches(-g.kernels);
     g.sig = sig;
+  }
+  // without per-pass profiling the full blocks run as one device-side loop
+  // (a single graph launch); the host loop below then only runs a remainder
+  // shorter than a block, or every block when profiling
+  if (!t->prof.on && nact > 0 && max_iter - iter >= kCheckEvery) {
+    std::vector<uintptr_t> wsig = sig;
+    wsig.push_back(7);
+    const int nb = run_device_loop(t, sizeof(T) == 4 ? 0 : 1, wsig,
+                                   (max_iter - iter) / kCheckEvery, hact,
+                                   [&]() { enqueue_block(kCheckEvery); });
+    iter += nb * kCheckEvery;
+    nact = 0;
+    for (int a : hact) nact += a;
   }
   while (nact > 0 && iter < max_iter) {
     const int nq = std::min(kCheckEvery, max_iter - iter);
@@ -825,6 +927,16 @@ static void bicgstab2(dda_target* t, const OpView<T>& op, const MatvecLaunch& L,
     g.sig = sig;
   }
   int iter = 0;
+  if (!t->prof.on && nact > 0) {
+    std::vector<uintptr_t> wsig = sig;
+    wsig.push_back(7);
+    const int nb = run_device_loop(t, sizeof(T) == 4 ? 0 : 1, wsig,
+                                   (max_iter + 2 * kCycles - 1) / (2 * kCycles), hact,
+                                   [&]() { enqueue_block(kCycles); });
+    iter += nb * 2 * kCycles;
+    nact = 0;
+    for (int a : hact) nact += a;
+  }
   while (nact > 0 && iter < max_iter) {
     CK(cudaGraphLaunch(g.exec, st));
     note_launches(g.kernels);
@@ -880,6 +992,15 @@ static void run_graph_loop(dda_target* t, const std::vector<uintptr_t>& sig, int
     g.sig = sig;
   }
   int iter = 0;
+  if (!t->prof.on && nact > 0) {
+    std::vector<uintptr_t> wsig = sig;
+    wsig.push_back(7);
+    const int nb = run_device_loop(t, sizeof(T) == 4 ? 0 : 1, wsig,
+                                   (max_iter + per_block - 1) / per_block, hact, enqueue);
+    iter += nb * per_block;
+    nact = 0;
+    for (int a : hact) nact += a;
+  }
   while (nact > 0 && iter < max_iter) {
     CK(cudaGraphLaunch(g.exec, st));
     note_launches(g.kernels);
@@ -1251,6 +1372,9 @@ void dda_target_destroy(dda_target* t) {
   t->prof.destroy();
   t->graphs[0].reset();
   t->graphs[1].reset();
+  t->loops[0].g.reset();
+  t->loops[1].g.reset();
+  t->loopctl.release();
   if (t->ev0) cudaEventDestroy(t->ev0);
   if (t->ev1) cudaEventDestroy(t->ev1);
   if (t->stream) cudaStreamDestroy(t->stream);
@@ -1954,14 +2078,16 @@ void apply_schedule(const dda_target* t, MatvecLaunch& L, const std::vector<int>
   L.y_smem = (size_t)t->Ly * v[1] * sizeof(C);
   L.z_tile = v[2];
   L.z_ps = v[3];
-  L.z_gs = v[4] != 0;
+  // z staging 2, 3: the column-pair kernel, Ghat through L2 (2) or staged (3)
+  L.z_pair = v[4] >= 2 ? 1 : 0;
+  L.z_gs = v[4] == 1 || v[4] == 3;
   const int Hz = t->Lz / 2 + 1;
   L.z_smem = (((size_t)t->Lz * L.z_ps * sizeof(C) + 15) & ~(size_t)15) +
              (L.z_gs ? (size_t)6 * Hz * L.z_tile * sizeof(C) : 0);
 }
 
 std::vector<int> schedule_of(const MatvecLaunch& L) {
-  return {L.x_lines, L.y_tile, L.z_tile, L.z_ps, L.z_gs ? 1 : 0,
+  return {L.x_lines, L.y_tile, L.z_tile, L.z_ps, (L.z_pair ? 2 : 0) + (L.z_gs ? 1 : 0),
           L.x_threads, L.y_threads, L.z_threads};
 }
 }  // namespace
@@ -2122,9 +2248,12 @@ dda_status dda_set_schedule(dda_target* t, int precision, const int* in8) {
   const bool f64 = precision == DDA_PREC_FP64;
   const size_t cs = f64 ? sizeof(double2) : sizeof(float2);
   if (xl < 1 || xl > 64 || yt < 1 || yt > 64 || (zt != 2 && zt != 4 && zt != 8 && zt != 16) ||
-      zp < 3 * zt || zp > 3 * zt + 8 || (zg != 0 && zg != 1))
+      zp < 3 * zt || zp > 3 * zt + 8 || zg < 0 || zg > 3)
     return fail(DDA_ERR_INVALID_ARG, "schedule: x lines 1..64, y tile 1..64, z tile 2/4/8/16, "
-                                     "z pitch 3*tile..3*tile+8, z staging 0/1");
+                                     "z pitch 3*tile..3*tile+8, z staging 0..3");
+  if (zg >= 2 && (f64 || !z_pair_applies(t->pz, t->Lx, zt)))
+    return fail(DDA_ERR_INVALID_ARG, "schedule: z staging 2/3 (column-pair z kernel) needs "
+                                     "FP32, an even Lx, a compiled z plan and tile 4, 8 or 16");
   for (int i = 5; i < 8; ++i) {
     // the FP32 z pass of a compiled radix plan takes up to 384 threads
     const int tmax = (i == 7 && !f64 && z_fixed_applies(t->pz, zt)) ? 384 : 256;
@@ -2137,8 +2266,10 @@ dda_status dda_set_schedule(dda_target* t, int precision, const int* in8) {
   // a compiled-plan z kernel uses its own pitch, 3 tile (+1 below 128 B rows)
   const int zpc = (!f64 && z_fixed_applies(t->pz, zt))
                       ? std::max(zp, 3 * zt + (zt * (int)cs < 128 ? 1 : 0)) : zp;
-  const size_t zsm = (((size_t)t->Lz * zpc * cs + 15) & ~(size_t)15) +
-                     (zg ? (size_t)6 * (t->Lz / 2 + 1) * zt * cs : 0);
+  const size_t zsm = zg >= 2 ? (size_t)t->Lz * 3 * zt * cs +
+                                   (zg == 3 ? (size_t)6 * (t->Lz / 2 + 1) * zt * cs : 0)
+                             : (((size_t)t->Lz * zpc * cs + 15) & ~(size_t)15) +
+                                   (zg ? (size_t)6 * (t->Lz / 2 + 1) * zt * cs : 0);
   if (xinv > 200 * 1024 || ysm > 200 * 1024 || zsm > 200 * 1024)
     return fail(DDA_ERR_INVALID_ARG, "schedule: a pass would need more than 200 KB of shared memory");
   try {

@@ -16,7 +16,8 @@ struct MatvecLaunch {
   int x_lines, x_threads; size_t x_smem, xinv_smem;
   int y_tile, y_threads; size_t y_smem;
   int z_tile, z_ps, z_threads; size_t z_smem;
-  bool z_gs;  // Ghat tile staged in shared memory
+  bool z_gs;   // Ghat tile staged in shared memory
+  int z_pair;  // FP32 compiled plans: the column-pair z kernel (k_fft_z_pairs)
 };
 
 template <typename T> MatvecLaunch plan_matvec(const OpView<T>& op);
@@ -93,6 +94,8 @@ enum { KS_RUN = 0, KS_CONV = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3 };
 // True when the FP32 z pass of this axis plan and z tile runs a compiled-plan
 // kernel (matvec_fixed.cu), which takes up to 384 threads per CTA.
 bool z_fixed_applies(const AxisPlan& P, int tile);
+// The column-pair FP32 z kernel applies: a compiled z plan, Lx even, tile 4, 8 or 16.
+bool z_pair_applies(const AxisPlan& pz, int Lx, int tile);
 
 // A vector pass that finishes one of the Krylov scalar steps in its last
 // block (instead of a separate one-block kernel): `counter` holds one word per
@@ -157,6 +160,10 @@ cudaError_t launch_bicg_init(int64_t n, int R, const cplx_t<T>* b, const cplx_t<
                              double* partials, cudaStream_t st);
 cudaError_t launch_state_init(int R, int nblk, const double* partials, KState* ks,
                               int* active, double tol, int max_iter, cudaStream_t st);
+// Body end of a device-side iteration loop: ctl[0] += 1, and the while-node's
+// condition h stays set while any active[r] != 0 and ctl[0] < ctl[1].
+cudaError_t launch_loop_continue(cudaGraphConditionalHandle h, const int* active, int R,
+                                 int* ctl, cudaStream_t st);
 cudaError_t launch_scalar_alpha(int R, int nblk, const double* partials, KState* ks,
                                 int* active, cudaStream_t st);
 template <typename T>

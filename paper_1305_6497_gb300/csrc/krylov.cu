@@ -127,6 +127,34 @@ cudaError_t launch_state_init(int R, int nblk, const double* partials, KState* k
   return cudaGetLastError();
 }
 
+// The last node of a device-side iteration loop (the body of a CUDA-graph
+// while-node): counts the block of iterations just run in ctl[0] and keeps the
+// loop going while some right-hand side is still active and fewer than ctl[1]
+// blocks have run -- so the loop ends after at most ctl[1] blocks whatever the
+// flags say.
+__global__ void k_loop_continue(cudaGraphConditionalHandle h, const int* __restrict__ active,
+                                int R, int* ctl) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int a = 0;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) a |= active[r];
+  if (a) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int done = ctl[0] + 1;
+    ctl[0] = done;
+    cudaGraphSetConditional(h, (any && done < ctl[1]) ? 1u : 0u);
+  }
+}
+
+cudaError_t launch_loop_continue(cudaGraphConditionalHandle h, const int* active, int R,
+                                 int* ctl, cudaStream_t st) {
+  k_loop_continue<<<1, kThreads, 0, st>>>(h, active, R, ctl);
+  note_launch();
+  return cudaGetLastError();
+}
+
 
 
 __global__ void k_scalar_alpha(int nblk, const double* partials, KState* ks, int* active) {

@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "matvec_impl.cuh"
+#include "zpass_pair.cuh"
 
 namespace dda {
 
@@ -80,9 +81,34 @@ bool z_fixed_applies(const AxisPlan& a, int tile) {
   return ok;
 }
 
+bool z_pair_applies(const AxisPlan& pz, int Lx, int tile) {
+  return (tile == 4 || tile == 8 || tile == 16) && Lx % 2 == 0 && z_fixed_plan(pz);
+}
+
 bool launch_z_fixed(const OpView<float>& op, const MatvecLaunch& L, int R, float2* scratch,
                     const int* active, cudaStream_t st) {
   bool done = false;
+  if (L.z_pair) {
+    if (!z_pair_applies(op.pz, op.Lx, L.z_tile)) return false;
+    dispatch_plan(op.pz, ZPlans{}, [&](auto plan) {
+      using P = decltype(plan);
+      const dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly / 2 + 1);
+      auto go = [&](auto tile) {
+        constexpr int TT = decltype(tile)::value;
+        if (L.z_gs)
+          k_fft_z_pairs<TT, P, true><<<gz, L.z_threads, zpair_smem<TT, P, true>(), st>>>(
+              op, scratch, R, active);
+        else
+          k_fft_z_pairs<TT, P, false><<<gz, L.z_threads, zpair_smem<TT, P, false>(), st>>>(
+              op, scratch, R, active);
+        done = true;
+      };
+      if (L.z_tile == 4) go(IC<4>{});
+      else if (L.z_tile == 8) go(IC<8>{});
+      else go(IC<16>{});
+    });
+    return done;
+  }
   dispatch_plan(op.pz, ZPlans{}, [&](auto plan) {
     using P = decltype(plan);
     if (!z_tile_compiled<P>(L.z_tile)) return;
@@ -175,6 +201,16 @@ cudaError_t configure_fixed_kernels() {
     });
   };
   zcfg(P16x8{}); zcfg(P16x4{}); zcfg(P16x8x4{}); zcfg(P8x4x3x3{});
+  auto zpcfg = [&](auto plan) {
+    using P = decltype(plan);
+    ok(set_smem((const void*)k_fft_z_pairs<4, P, false>));
+    ok(set_smem((const void*)k_fft_z_pairs<8, P, false>));
+    ok(set_smem((const void*)k_fft_z_pairs<16, P, false>));
+    ok(set_smem((const void*)k_fft_z_pairs<4, P, true>));
+    ok(set_smem((const void*)k_fft_z_pairs<8, P, true>));
+    ok(set_smem((const void*)k_fft_z_pairs<16, P, true>));
+  };
+  zpcfg(P16x8{}); zpcfg(P16x4{}); zpcfg(P16x8x4{}); zpcfg(P8x4x3x3{});
   auto ycfg = [&](auto plan) {
     using P = decltype(plan);
     for_y_variants([&](auto tile, auto iv) {

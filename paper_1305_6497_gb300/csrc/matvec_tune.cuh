@@ -130,6 +130,7 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
           for (int th : {64, 96, 128, 192, 256, 384}) {
             MatvecLaunch c = best;
             fill_z<T>(op, c, tile, pad, gs != 0);
+            c.z_pair = 0;
             // a compiled-plan z kernel sets its own pitch: one pad value is enough
             if (std::is_same<T, float>::value && z_fixed_plan(op.pz) && pad != 0) continue;
             // 384 threads: compiled-plan z kernels only
@@ -147,6 +148,23 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
             const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);
             if (tt < bt) { bt = tt; best = c; }
           }
+    // the column-pair kernel (FP32, compiled z plans)
+    if (std::is_same<T, float>::value)
+      for (int tile : {4, 8, 16})
+        for (int gs = 0; gs < 2; ++gs)
+        for (int th : {128, 192, 256}) {
+          if (!z_pair_applies(op.pz, op.Lx, tile)) continue;
+          const size_t zs = (size_t)op.Lz * 3 * tile * sizeof(C) +
+                            (gs ? (size_t)6 * op.Hz * tile * sizeof(C) : 0);
+          if (zs > kMax) continue;
+          MatvecLaunch c = best;
+          fill_z<T>(op, c, tile, 0, gs != 0);
+          c.z_pair = 1;
+          c.z_smem = zs;
+          c.z_threads = th;
+          const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);
+          if (tt < bt) { bt = tt; best = c; }
+        }
   }
   (void)sizeof(C);
   cudaStreamSynchronize(st);

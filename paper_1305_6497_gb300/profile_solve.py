@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--precision", default="fp32_refined")
     ap.add_argument("--solver", default="bicgstab")
+    ap.add_argument("--z-schedule", default="",
+                    help="tile,staging,threads: override the tuned FP32 z pass (staging 0/1/2)")
     args = ap.parse_args()
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
@@ -46,6 +48,11 @@ def main():
         w = getattr(W, fn)()
     t = B.Target(w.occ, w.comp, w.m, method=w.method)
     t.autotune(w.kd, w.n_rhs)
+    if args.z_schedule:
+        tile, stage, threads = (int(v) for v in args.z_schedule.split(","))
+        sch = t.schedule("fp32")
+        sch.update(z_tile=tile, z_pitch=3 * tile, z_stage_ghat=stage, z_threads=threads)
+        t.set_schedule(sch, "fp32")
     kw = dict(yhat=w.yhat, npol=2, tol=w.tol, max_iter=5000, precision=args.precision,
               want_P=False, solver=args.solver)
     for _ in range(args.warmup):
@@ -55,6 +62,7 @@ def main():
     outs = [t.solve(w.kd, w.khat, w.e01, profile=True, **kw) for _ in range(args.solves)]
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
+    sched = t.schedule("fp32")
     t.close()
     print(json.dumps({
         "workload": w.name, "N": w.n_dipoles, "rhs": w.n_rhs, "precision": args.precision,
@@ -63,6 +71,7 @@ def main():
         "rhs_matvecs": [int(o["matvecs"]) for o in outs],
         "pass_ms": {f"{p}:{k}": v for (p, k), v in outs[-1]["kernel_ms"].items()},
         "pass_calls": {f"{p}:{k}": v for (p, k), v in outs[-1]["kernel_calls"].items()},
+        "schedule_fp32": sched,
     }))
 
 

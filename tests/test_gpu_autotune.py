@@ -92,3 +92,63 @@ def test_compiled_z_pass_takes_384_threads(shape):
             t.set_schedule(dict(x_lines=16, y_tile=16, z_tile=8, z_pitch=25, z_stage_ghat=0,
                                 x_threads=128, y_threads=128, z_threads=384), "fp64")
     t.close()
+
+
+@pytest.mark.parametrize("shape", [(11, 18, 32), (12, 18, 64), (20, 7, 256), (10, 9, 144),
+                                   (6, 40, 256)])
+def test_column_pair_z_kernel_is_bit_identical(shape):
+    """z staging 2 and 3 select the column-pair z kernel (each CTA: two columns
+    per thread, both rows of an octant row, every right-hand side; Ghat read
+    through L2, or staged once in shared memory): the same
+    butterflies, twiddles and multiply per column as the compiled-plan kernel,
+    so the FP32 product is bit-identical, over 1 and 3 right-hand sides, ragged
+    column tiles and odd box sides; it also matches the oracle."""
+    from paper_1305_6497_gb300 import binding as B
+    occ, comp = tg.ellipsoid(*shape)
+    flat, pos = O.site_positions(occ)
+    x = O.box_to_sites(W.random_polarization(occ, 7)[0], flat)
+    t = B.Target(occ, comp, [1.5 + 0.1j], method="GKDLDR")
+    kh, e = np.array([0.36, 0.48, 0.8]), [0.8, -0.6, 0]
+    assert t.grid[0] % 2 == 0
+    for zt in (4, 8, 16):
+        base = dict(x_lines=16, y_tile=16, z_tile=zt, z_pitch=3 * zt, x_threads=128,
+                    y_threads=128, z_threads=256)
+        t.set_schedule(dict(base, z_stage_ghat=0), "fp32")
+        y0 = t.matvec(0.4, x, kh, e, "fp32")
+        for th, zg in ((128, 2), (256, 2), (192, 3), (256, 3)):
+            try:
+                t.set_schedule(dict(base, z_stage_ghat=zg, z_threads=th), "fp32")
+            except B.DDAError as ex:   # 16 columns of 512 points with Ghat staged
+                assert "shared memory" in str(ex)
+                continue
+            assert t.schedule("fp32")["z_stage_ghat"] == zg
+            y1 = t.matvec(0.4, x, kh, e, "fp32")
+            assert np.array_equal(y1, y0), (zt, th, zg, np.abs(y1 - y0).max())
+    ainv = O.site_alpha_inverse(comp.reshape(-1)[flat], [1.5 + 0.1j], "GKDLDR", 0.4, kh)
+    rows = np.arange(0, len(flat), 7)
+    ref = O.matvec_direct(x, pos, ainv, 0.4, "GKDLDR", rows=rows)
+    assert np.abs(y1[rows] - ref).max() <= 2e-5 * np.abs(ref).max()
+    # batched solves (several right-hand sides, some converging first) agree
+    w = W.small_ellipsoid(*shape, m=1.5 + 0.1j, kd=0.4, method="LDR", n_orient=3, seed=9)
+    t2 = B.Target(w.occ, w.comp, w.m, method="LDR")
+    kw = dict(yhat=w.yhat, npol=2, tol=1e-9, precision="fp32_refined", want_P=True)
+    sched = dict(x_lines=16, y_tile=16, z_tile=8, z_pitch=24, x_threads=128, y_threads=128,
+                 z_threads=256)
+    t2.set_schedule(dict(sched, z_stage_ghat=0), "fp32")
+    a = t2.solve(w.kd, w.khat, w.e01, **kw)
+    for zg in (2, 3):
+        t2.set_schedule(dict(sched, z_stage_ghat=zg), "fp32")
+        b = t2.solve(w.kd, w.khat, w.e01, **kw)
+        assert np.array_equal(a["P"], b["P"]) and np.array_equal(a["iters"], b["iters"])
+    t.close()
+    t2.close()
+
+
+def test_column_pair_z_kernel_needs_a_compiled_plan_and_even_x_length():
+    from paper_1305_6497_gb300 import binding as B
+    occ, comp = tg.ellipsoid(13, 10, 11)      # Lx = 25 (odd), Lz = 24: no compiled plan
+    t = B.Target(occ, comp, [1.5 + 0.1j], method="CM")
+    with pytest.raises(B.DDAError):
+        t.set_schedule(dict(x_lines=16, y_tile=16, z_tile=4, z_pitch=12, z_stage_ghat=2,
+                            x_threads=128, y_threads=128, z_threads=128), "fp32")
+    t.close()

@@ -7,12 +7,18 @@ E_sca, E_macro and B_sca to 1e-10 of the largest value, E_inc and B_inc to
 converged P the identity P_j = alpha_j (E_inc + E_sca)_j holds at target sites
 to the solve's tolerance.
 """
+import math
+import os
+import sys
+
 import numpy as np
 import pytest
 
 from dda_inputs import targets as tg
 from dda_inputs import workloads as W
 from oracle import dda as O
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 pytestmark = pytest.mark.gpu
 
@@ -107,3 +113,36 @@ def test_nearfield_rejects_bad_arguments(B):
     with pytest.raises(ValueError):
         t.nearfield(0.3, [1, 0, 0], [0, 1, 0], sol["P"][:1], [0] * 6)
     t.close()
+
+
+def test_guide_nearfield_track_through_the_au_sphere(B):
+    """The guide's ddpostprocess example on the GPU (59728-dipole Au
+    pseudosphere, GKDLDR, 96^3 near-field box): the library's E on the sites
+    around the x-axis track equals the oracle's direct sums for the same dipoles
+    to 1e-9, and the interpolated E_y follows the printed track as in the
+    oracle's test (4.5% of max |E| illuminated side and inside, 7% shadow side)."""
+    import nearfield_track as T
+    occ, comp = tg.sphere(48, T.DIAMETER)
+    N = int(occ.sum())
+    kd = T.X_SIZE / O.effective_radius(N)
+    t = B.Target(occ, comp, [T.M_AU], method="GKDLDR")
+    out = t.solve(kd, [1, 0, 0], [0, 1, 0], yhat=[0, 1, 0], npol=1, tol=1e-8,
+                  precision="fp32_refined")
+    nf = t.nearfield(kd, [1, 0, 0], [0, 1, 0], out["P"], T.EXT, npol=1,
+                     want=("E_inc", "E_sca"))
+    t.close()
+    dims, lo = nf["dims"], nf["lo"]
+    assert tuple(dims) == (96, 96, 96)
+    etot = (nf["E_inc"] + nf["E_sca"])[0, 1].reshape(-1)
+    d_um = T.LAMBDA_UM * kd / (2 * math.pi)
+    x_um, e_pr = T.printed()
+    pts = sorted({i for x in x_um for i, _ in T.corners(x / d_um, lo, 48, dims)})
+    ref = O.nearfield(occ, comp, [T.M_AU], kd, [1, 0, 0], [0, 1, 0], "GKDLDR", out["P"][0],
+                      T.EXT, points=np.array(pts))
+    eref = (ref["E_inc"] + ref["E_sca"])[:, 1]
+    assert np.abs(etot[pts] - eref).max() <= 1e-9 * np.abs(eref).max()
+    inner, shadow = T.compare(x_um, e_pr, lambda xd: sum(w * etot[i] for i, w in
+                                                         T.corners(xd, lo, 48, dims)),
+                              d_um, 0.5 * T.DIAMETER)
+    assert inner < 0.045, inner
+    assert shadow < 0.07, shadow

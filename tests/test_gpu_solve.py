@@ -510,3 +510,29 @@ def test_guide_worked_example_gkdldr(B, precision):
     for l in range(2):
         assert abs(out["Qext"][l] / ref["Qext"][l] - 1) < 1e-6
         assert abs(out["Qabs"][l] / ref["Qabs"][l] - 1) < 1e-6
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "qmr", "bicgstab2", "gpbicg", "petrkp"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refined"])
+def test_device_loop_equals_host_checked_blocks(B, solver, precision):
+    """Without profiling a Krylov solve runs its blocks of iterations as one
+    device-side loop (a CUDA-graph while-node that stops when every right-hand
+    side is frozen); with per-pass profiling the host checks the flags after
+    each block.  Both run the same kernels on the same data: bit-identical P,
+    iterations and residuals, also when max_iter stops the solve mid-way (a
+    remainder shorter than a block runs on the host)."""
+    w = W.small_ellipsoid(8, 12, 32, m=1.5 + 0.1j, kd=0.4, method="LDR", n_orient=3)
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    kw = dict(yhat=w.yhat, npol=2, tol=1e-9, precision=precision, solver=solver)
+    a = t.solve(w.kd, w.khat, w.e01, profile=False, **kw)
+    b = t.solve(w.kd, w.khat, w.e01, profile=True, **kw)
+    assert a["status"] == B.DDA_OK
+    for key in ("P", "iters", "resid", "Qext"):
+        assert np.array_equal(a[key], b[key]), key
+    if precision == "fp64":
+        c = t.solve(w.kd, w.khat, w.e01, profile=False, max_iter=10, **dict(kw, tol=1e-14))
+        d = t.solve(w.kd, w.khat, w.e01, profile=True, max_iter=10, **dict(kw, tol=1e-14))
+        assert c["status"] == B.DDA_ERR_NOCONV
+        assert np.array_equal(c["P"], d["P"]) and np.array_equal(c["iters"], d["iters"])
+        assert np.all(c["iters"] <= 10 + (1 if solver == "bicgstab2" else 0))
+    t.close()

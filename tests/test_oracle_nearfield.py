@@ -11,6 +11,8 @@
 * The extended box follows the r1..r6 definition with rounding to nearest.
 """
 import math
+import os
+import sys
 
 import numpy as np
 import pytest
@@ -18,6 +20,8 @@ import pytest
 from dda_inputs import targets as tg
 from dda_inputs import workloads as W
 from oracle import dda as O
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_extended_box_definition():
@@ -153,3 +157,39 @@ def test_filtered_magnetic_vector_tends_to_the_point_one_far_away():
     hp = O.magnetic_vector(np.array([1.0, 0, 0]), 0.4, "LDR")
     hf = O.magnetic_vector(np.array([1.0, 0, 0]), 0.4, "FCD")
     assert np.abs(hf - hp).max() > 0.05 * np.abs(hp).max()
+
+
+@pytest.mark.slow
+def test_guide_nearfield_track_through_the_au_sphere():
+    """The guide's ddpostprocess example (Sec. "The Program ddpostprocess"):
+    the 59728-dipole Au pseudosphere (m = 0.96 + 1.01i, x = 5, k d = 0.20619,
+    GKDLDR), E_y along the x axis through its centre on the 96^3 near-field
+    box.  The oracle's microscopic field, interpolated trilinearly between
+    sites, follows the printed values to 4.5% of the track's largest |E| on the
+    illuminated side and inside the sphere, and to 7% on the shadow side
+    (points within one spacing of the surface, where interpolation straddles
+    the discontinuity, are skipped).  The printed shadow-side values match the
+    oracle's one printed row (1.455 d) further from the sphere; the cause is
+    not known, hence the looser bound there."""
+    import nearfield_track as T
+    occ, comp = tg.sphere(48, T.DIAMETER)
+    N = int(occ.sum())
+    assert N == 59728
+    kd = T.X_SIZE / O.effective_radius(N)
+    assert abs(kd - 0.20619) < 5e-6            # the printed k_inc d
+    r = O.solve_target(occ, comp, [T.M_AU], kd, [1, 0, 0], [0, 1, 0], [0, 1, 0], "GKDLDR",
+                       npol=1, tol=1e-8)
+    dims, lo = O.nearfield_box(occ.shape, T.EXT)
+    assert dims == (96, 96, 96)
+    d_um = T.LAMBDA_UM * kd / (2 * math.pi)
+    x_um, e_pr = T.printed()
+    pts = sorted({i for x in x_um for i, _ in T.corners(x / d_um, lo, 48, dims)})
+    nf = O.nearfield(occ, comp, [T.M_AU], kd, [1, 0, 0], [0, 1, 0], "GKDLDR", r["P"][0],
+                     T.EXT, points=np.array(pts))
+    etot = (nf["E_inc"] + nf["E_sca"])[:, 1]
+    at = dict(zip(pts, etot))
+    inner, shadow = T.compare(x_um, e_pr, lambda xd: sum(w * at[i] for i, w in
+                                                         T.corners(xd, lo, 48, dims)),
+                              d_um, 0.5 * T.DIAMETER)
+    assert inner < 0.045, inner
+    assert shadow < 0.07, shadow
