@@ -124,11 +124,32 @@ static std::vector<int> factor_radices(int L) {
 // which frequency ends up at each position after the forward (decimation in
 // frequency) transform: position sum_t m_t S_t holds sum_t m_t N_t with
 // S_t = B_t/rs[t] and N_t = rs[0]...rs[t-1].
+static AxisPlan make_plan_radices(int L, const std::vector<int>& rs,
+                                  std::vector<long double>& twr, std::vector<long double>& twi,
+                                  std::vector<int>& k_at);
+
 static AxisPlan make_plan(int L, std::vector<long double>& twr, std::vector<long double>& twi,
                           std::vector<int>& k_at) {
+  return make_plan_radices(L, factor_radices(L), twr, twi, k_at);
+}
+
+// The radix plan the column-pair z kernel compiles for a z length (radices of
+// at most 8, which keeps its registers low), or an empty list.
+static std::vector<int> pair_plan_radices(int L) {
+  switch (L) {
+    case 64: return {8, 8};
+    case 128: return {8, 4, 4};
+    case 288: return {8, 4, 3, 3};
+    case 512: return {8, 8, 8};
+    default: return {};
+  }
+}
+
+static AxisPlan make_plan_radices(int L, const std::vector<int>& rs,
+                                  std::vector<long double>& twr, std::vector<long double>& twi,
+                                  std::vector<int>& k_at) {
   AxisPlan P{};
   P.L = L;
-  std::vector<int> rs = factor_radices(L);
   P.nstage = (int)rs.size();
   int B = L, off = 0;
   twr.clear(); twi.clear();
@@ -283,6 +304,7 @@ struct dda_target {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   DevBuf comp, site, tw64, tw32, twdf, perm;  // perm: k_at x|y|z, then pos x|y|z
+  DevBuf twzp;  // FP32 z twiddles of the column-pair kernel's plan (when it has one)
   AxisPlan px{}, py{}, pz{};
   int twoff[3] = {0, 0, 0};
   // Green transform cache
@@ -334,6 +356,7 @@ static OpView<T> make_view(const dda_target* t, const void* ghat, const void* ai
   v.ky_at = pm + t->Lx;
   v.kz_at = pm + t->Lx + t->Ly;
   v.ypos_at = pm + (t->Lx + t->Ly + t->Lz) + t->Lx;
+  v.twz_pair = t->twzp.as<float2>();
   v.px = t->px; v.py = t->py; v.pz = t->pz;
   auto magic = [](int d) { return ((1ull << 36) + (unsigned long long)d - 1) / (unsigned long long)d; };
   v.div_nx = magic(v.nx); v.div_ny = magic(v.ny); v.div_nz = magic(v.nz); v.div_Lx = magic(v.Lx);
@@ -1367,6 +1390,7 @@ void dda_target_destroy(dda_target* t) {
   if (t->stream) cudaStreamSynchronize(t->stream);
   t->ws.release_all();
   t->comp.release(); t->site.release(); t->tw64.release(); t->tw32.release(); t->twdf.release();
+  t->twzp.release();
   t->perm.release();
   t->g64.release(); t->g32.release(); t->gdf.release(); t->h64.release();
   t->prof.destroy();
@@ -1477,6 +1501,17 @@ dda_status dda_target_create(int nx, int ny, int nz, const uint8_t* occ, const u
     kat.insert(kat.end(), posall.begin(), posall.end());
     t->perm.ensure(sizeof(int) * kat.size());
     CK(cudaMemcpy(t->perm.p, kat.data(), sizeof(int) * kat.size(), cudaMemcpyHostToDevice));
+    // twiddles of the column-pair z kernel's own radix plan (FP32)
+    const std::vector<int> prs = pair_plan_radices(t->Lz);
+    if (!prs.empty()) {
+      std::vector<long double> wr, wi;
+      std::vector<int> ka;
+      make_plan_radices(t->Lz, prs, wr, wi, ka);
+      std::vector<float2> tp(std::max<size_t>(1, wr.size()), make_float2(1, 0));
+      for (size_t i = 0; i < wr.size(); ++i) tp[i] = make_float2((float)wr[i], (float)wi[i]);
+      t->twzp.ensure(sizeof(float2) * tp.size());
+      CK(cudaMemcpy(t->twzp.p, tp.data(), sizeof(float2) * tp.size(), cudaMemcpyHostToDevice));
+    }
   } catch (const CudaFail& f) {
     dda_status s = from_cuda(f);
     dda_target_destroy(t);
@@ -1515,8 +1550,8 @@ int64_t dda_solve_hbm_bytes(const dda_target* t, const dda_solve_params* p) {
 // workspace and its near-field box.
 static int64_t held_bytes(dda_target* t) {
   int64_t b = 0;
-  for (const DevBuf* d : {&t->comp, &t->site, &t->tw64, &t->tw32, &t->twdf, &t->perm, &t->g64,
-                          &t->g32, &t->gdf, &t->h64})
+  for (const DevBuf* d : {&t->comp, &t->site, &t->tw64, &t->tw32, &t->twdf, &t->twzp, &t->perm,
+                          &t->g64, &t->g32, &t->gdf, &t->h64})
     b += (int64_t)d->bytes;
   b += t->ws.bytes();
   if (t->nf) b += held_bytes(t->nf);
@@ -2251,12 +2286,15 @@ dda_status dda_set_schedule(dda_target* t, int precision, const int* in8) {
       zp < 3 * zt || zp > 3 * zt + 8 || zg < 0 || zg > 3)
     return fail(DDA_ERR_INVALID_ARG, "schedule: x lines 1..64, y tile 1..64, z tile 2/4/8/16, "
                                      "z pitch 3*tile..3*tile+8, z staging 0..3");
-  if (zg >= 2 && (f64 || !z_pair_applies(t->pz, t->Lx, zt)))
+  if (zg >= 2 && (f64 || !z_pair_applies(t->Lz, t->Lx, zt) || in8[7] != kZPairThreads))
     return fail(DDA_ERR_INVALID_ARG, "schedule: z staging 2/3 (column-pair z kernel) needs "
-                                     "FP32, an even Lx, a compiled z plan and tile 4, 8 or 16");
+                                     "FP32, an even Lx, Lz of 64, 128, 288 or 512, tile 4 or 8 "
+                                     "and 384 threads");
   for (int i = 5; i < 8; ++i) {
-    // the FP32 z pass of a compiled radix plan takes up to 384 threads
-    const int tmax = (i == 7 && !f64 && z_fixed_applies(t->pz, zt)) ? 384 : 256;
+    // the FP32 z pass of a compiled radix plan (and the column-pair one) takes
+    // up to 384 threads
+    const int tmax =
+        (i == 7 && !f64 && (z_fixed_applies(t->pz, zt) || zg >= 2)) ? 384 : 256;
     if (in8[i] < 32 || in8[i] > tmax || in8[i] % 32)
       return fail(DDA_ERR_INVALID_ARG, "schedule: threads per CTA must be a multiple of 32 in "
                                        "32..256 (FP32 z pass of a compiled plan: ..384)");

@@ -94,8 +94,10 @@ enum { KS_RUN = 0, KS_CONV = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3 };
 // True when the FP32 z pass of this axis plan and z tile runs a compiled-plan
 // kernel (matvec_fixed.cu), which takes up to 384 threads per CTA.
 bool z_fixed_applies(const AxisPlan& P, int tile);
-// The column-pair FP32 z kernel applies: a compiled z plan, Lx even, tile 4, 8 or 16.
-bool z_pair_applies(const AxisPlan& pz, int Lx, int tile);
+// The column-pair FP32 z kernel applies: Lz with a compiled pair plan (64, 128,
+// 288, 512), Lx even, tile 4 or 8; it always runs kZPairThreads threads.
+bool z_pair_applies(int Lz, int Lx, int tile);
+constexpr int kZPairThreads = 384;
 
 // A vector pass that finishes one of the Krylov scalar steps in its last
 // block (instead of a separate one-block kernel): `counter` holds one word per
