@@ -81,31 +81,49 @@ bool z_fixed_applies(const AxisPlan& a, int tile) {
   return ok;
 }
 
-bool z_pair_applies(const AxisPlan& pz, int Lx, int tile) {
-  return (tile == 4 || tile == 8 || tile == 16) && Lx % 2 == 0 && z_fixed_plan(pz);
+// the column-pair z kernel's own plans (radices <= 8; twiddles in op.twz_pair)
+using QP64 = FixedPlan<8, 8>;
+using QP128 = FixedPlan<8, 4, 4>;
+using QP288 = FixedPlan<8, 4, 3, 3>;
+using QP512 = FixedPlan<8, 8, 8>;
+using PairPlans = PlanList<QP64, QP128, QP288, QP512>;
+
+template <class F, class P, class... Ps>
+bool dispatch_length(int L, PlanList<P, Ps...>, F&& f) {
+  if (L == P::L) {
+    f(P{});
+    return true;
+  }
+  if constexpr (sizeof...(Ps) > 0) return dispatch_length(L, PlanList<Ps...>{}, f);
+  else return false;
+}
+
+bool z_pair_applies(int Lz, int Lx, int tile) {
+  return (tile == 4 || tile == 8) && Lx % 2 == 0 &&
+         dispatch_length(Lz, PairPlans{}, [](auto) {});
 }
 
 bool launch_z_fixed(const OpView<float>& op, const MatvecLaunch& L, int R, float2* scratch,
                     const int* active, cudaStream_t st) {
   bool done = false;
   if (L.z_pair) {
-    if (!z_pair_applies(op.pz, op.Lx, L.z_tile)) return false;
-    dispatch_plan(op.pz, ZPlans{}, [&](auto plan) {
+    if (!z_pair_applies(op.Lz, op.Lx, L.z_tile) || !op.twz_pair) return false;
+    dispatch_length(op.Lz, PairPlans{}, [&](auto plan) {
       using P = decltype(plan);
+      constexpr int NT = kZPairThreads;
       const dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly / 2 + 1);
       auto go = [&](auto tile) {
         constexpr int TT = decltype(tile)::value;
         if (L.z_gs)
-          k_fft_z_pairs<TT, P, true><<<gz, L.z_threads, zpair_smem<TT, P, true>(), st>>>(
+          k_fft_z_pairs<TT, P, true, NT><<<gz, NT, zpair_smem<TT, P, true>(), st>>>(
               op, scratch, R, active);
         else
-          k_fft_z_pairs<TT, P, false><<<gz, L.z_threads, zpair_smem<TT, P, false>(), st>>>(
+          k_fft_z_pairs<TT, P, false, NT><<<gz, NT, zpair_smem<TT, P, false>(), st>>>(
               op, scratch, R, active);
         done = true;
       };
       if (L.z_tile == 4) go(IC<4>{});
-      else if (L.z_tile == 8) go(IC<8>{});
-      else go(IC<16>{});
+      else go(IC<8>{});
     });
     return done;
   }
@@ -203,14 +221,13 @@ cudaError_t configure_fixed_kernels() {
   zcfg(P16x8{}); zcfg(P16x4{}); zcfg(P16x8x4{}); zcfg(P8x4x3x3{});
   auto zpcfg = [&](auto plan) {
     using P = decltype(plan);
-    ok(set_smem((const void*)k_fft_z_pairs<4, P, false>));
-    ok(set_smem((const void*)k_fft_z_pairs<8, P, false>));
-    ok(set_smem((const void*)k_fft_z_pairs<16, P, false>));
-    ok(set_smem((const void*)k_fft_z_pairs<4, P, true>));
-    ok(set_smem((const void*)k_fft_z_pairs<8, P, true>));
-    ok(set_smem((const void*)k_fft_z_pairs<16, P, true>));
+    constexpr int NT = kZPairThreads;
+    ok(set_smem((const void*)k_fft_z_pairs<4, P, false, NT>));
+    ok(set_smem((const void*)k_fft_z_pairs<8, P, false, NT>));
+    ok(set_smem((const void*)k_fft_z_pairs<4, P, true, NT>));
+    ok(set_smem((const void*)k_fft_z_pairs<8, P, true, NT>));
   };
-  zpcfg(P16x8{}); zpcfg(P16x4{}); zpcfg(P16x8x4{}); zpcfg(P8x4x3x3{});
+  zpcfg(QP64{}); zpcfg(QP128{}); zpcfg(QP288{}); zpcfg(QP512{});
   auto ycfg = [&](auto plan) {
     using P = decltype(plan);
     for_y_variants([&](auto tile, auto iv) {

@@ -150,10 +150,10 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
           }
     // the column-pair kernel (FP32, compiled z plans)
     if (std::is_same<T, float>::value)
-      for (int tile : {4, 8, 16})
-        for (int gs = 0; gs < 2; ++gs)
-        for (int th : {128, 192, 256}) {
-          if (!z_pair_applies(op.pz, op.Lx, tile)) continue;
+      for (int tile : {4, 8})
+        for (int gs = 0; gs < 2; ++gs) {
+          const int th = kZPairThreads;
+          if (!z_pair_applies(op.Lz, op.Lx, tile)) continue;
           const size_t zs = (size_t)op.Lz * 3 * tile * sizeof(C) +
                             (gs ? (size_t)6 * op.Hz * tile * sizeof(C) : 0);
           if (zs > kMax) continue;

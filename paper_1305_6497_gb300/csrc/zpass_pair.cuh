@@ -1,5 +1,5 @@
-// z pass on column pairs (FP32, a radix plan P of the z axis fixed at compile
-// time).
+// z pass on column pairs (FP32, the kernel's own radix plan P of the z length,
+// radices of at most 8, fixed at compile time, and NT threads per CTA).
 //
 // The same arithmetic as k_fft_z_mul_p -- forward FFT along z, the 3x3
 // complex-symmetric multiply by Ghat, inverse FFT along z, for the three
@@ -17,8 +17,14 @@
 //     forward transform runs (GS = true);
 //   * the last forward stage, the multiply and the first inverse stage are
 //     separate sweeps over shared memory (each conflict-free for this layout).
-// Per column the butterflies, twiddles and the multiply are those of the other
-// z kernels, in the same order, so the results are bit-identical to theirs.
+// The plan P (e.g. 512 = 8 x 8 x 8) need not be the target's z plan: the z
+// transform starts and ends inside this kernel, so only the frequency held at
+// each position (P::k_at, for the multiply) and P's twiddle table (op.twz_pair)
+// matter.  Small radices keep the registers low enough for two CTAs of NT
+// threads per SM, and NT is a multiple of the pair-lines per row so every
+// thread keeps one pair-line for the whole kernel (no index division in the
+// loops).  The arithmetic is the same transform with another factorization,
+// so results agree with the other z kernels to rounding, not bit for bit.
 //
 // grid: (ceil(Lx / TILE), Ly / 2 + 1), any block size.  Needs Lx even (pairs
 // of columns are 16-byte aligned).  Shared memory: Lz * 3 * TILE/2 float4,
@@ -36,12 +42,13 @@ __device__ __forceinline__ void split4(const float4 q, float2& a, float2& b) {
 
 // One in-place stage ST of plan P on NU pair-lines of shared memory, both
 // columns of each pair (forward: DFT then twiddles; inverse: the adjoint).
-template <bool INV, class P, int ST, int NU>
+template <bool INV, class P, int ST, int NU, int NT>
 __device__ __forceinline__ void stage_pair(float4* sd, const float2* __restrict__ tw) {
   constexpr int R = P::radix(ST), B = P::block(ST), S = P::span(ST), NB = P::L / R;
+  static_assert(NT % NU == 0, "a thread keeps one pair-line");
   const float2* __restrict__ tws = tw + P::tw_off(ST);
-  for (int b = threadIdx.x; b < NU * NB; b += blockDim.x) {
-    const int u = b % NU, q = b / NU;
+  const int u = threadIdx.x % NU;
+  for (int q = threadIdx.x / NU; q < NB; q += NT / NU) {
     const int blk = q / S, j = q - blk * S;
     float4* base = sd + (blk * B + j) * NU + u;
     float2 va[R], vb[R];
@@ -77,25 +84,26 @@ __device__ __forceinline__ void stage_pair(float4* sd, const float2* __restrict_
 }
 
 // Stages LO..HI forward (ascending) or inverse (descending).
-template <bool INV, class P, int LO, int HI, int NU>
+template <bool INV, class P, int LO, int HI, int NU, int NT>
 __device__ __forceinline__ void stages_pair(float4* sd, const float2* __restrict__ tw) {
   if constexpr (LO <= HI) {
     if constexpr (!INV) {
-      stage_pair<false, P, LO, NU>(sd, tw);
-      stages_pair<false, P, LO + 1, HI, NU>(sd, tw);
+      stage_pair<false, P, LO, NU, NT>(sd, tw);
+      stages_pair<false, P, LO + 1, HI, NU, NT>(sd, tw);
     } else {
-      stage_pair<true, P, HI, NU>(sd, tw);
-      stages_pair<true, P, LO, HI - 1, NU>(sd, tw);
+      stage_pair<true, P, HI, NU, NT>(sd, tw);
+      stages_pair<true, P, LO, HI - 1, NU, NT>(sd, tw);
     }
   }
 }
 
-template <int TILE, class P, bool GS>
-__global__ void __launch_bounds__(256, 2)
+template <int TILE, class P, bool GS, int NT>
+__global__ void __launch_bounds__(NT, 2)
 k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __restrict__ active) {
   static_assert(TILE % 2 == 0, "column pairs");
   constexpr int L = P::L, NS = P::NS, R0 = P::radix(0), S0 = P::span(0);
   constexpr int NP = TILE / 2, NU = 3 * NP;
+  static_assert(NT % NU == 0 && NT % NP == 0, "a thread keeps one pair-line");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* sd = reinterpret_cast<float4*>(smem_raw);
   float2* gs = reinterpret_cast<float2*>(sd + L * NU);
@@ -107,8 +115,11 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
   const int64_t plane_sz = (int64_t)Ly * Lx;
   const int64_t comp_sz = (int64_t)nz * plane_sz;
   const bool half = 2 * nz <= L;
-  const float2* __restrict__ tw = op.twz;
+  const float2* __restrict__ tw = op.twz_pair;
   const int kxh = Lx >> 1;
+  const int u = threadIdx.x % NU;           // this thread's pair-line ...
+  const int c = u / NP, tp = u - c * NP;    // ... = component c, column pair tp
+  const int tpm = threadIdx.x % NP;         // its column pair in the multiply
   // the rows sharing octant row hy: ky = hy, and ky = Ly - hy unless that is hy
   const int nrow = (hy == 0 || 2 * hy == Ly) ? 1 : 2;
   for (int rr = 0; rr < nrow; ++rr) {
@@ -119,9 +130,7 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
       if (active && !active[r]) continue;
       float2* base = buf + (int64_t)r * 3 * comp_sz + (int64_t)pyy * Lx + col0;
       // ---- first forward stage (radix R0, span S0), read from global memory
-      for (int b = threadIdx.x; b < NU * S0; b += blockDim.x) {
-        const int u = b % NU, j = b / NU;
-        const int c = u / NP, tp = u - c * NP;
+      for (int j = threadIdx.x / NU; j < S0; j += NT / NU) {
         const bool ok = tp < npv;
         const float2* src = base + c * comp_sz + (int64_t)j * plane_sz + 2 * tp;
         float2 va[R0], vb[R0];
@@ -161,15 +170,14 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
           sd[(j + m * S0) * NU + u] = make_float4(va[m].x, va[m].y, vb[m].x, vb[m].y);
       }
       __syncthreads();
-      stages_pair<false, P, 1, NS - 1, NU>(sd, tw);
+      stages_pair<false, P, 1, NS - 1, NU, NT>(sd, tw);
       if (GS) {  // the Ghat tile has landed (a no-op after the first pass)
         cp_async_wait_all();
         __syncthreads();
       }
       // ---- multiply by Ghat at each frequency (all three components)
-      for (int b = threadIdx.x; b < L * NP; b += blockDim.x) {
-        const int tp = b % NP, p = b / NP;
-        if (tp >= npv) continue;
+      for (int p = threadIdx.x / NP; p < L && tpm < npv; p += NT / NP) {
+        const int tp = tpm;
         const int kz = P::k_at(p);
         const bool fz = kz > L / 2;
         const int hz = fz ? L - kz : kz;
@@ -194,11 +202,9 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
         for (int c = 0; c < 3; ++c) row[c * NP] = make_float4(a[c].x, a[c].y, bb[c].x, bb[c].y);
       }
       __syncthreads();
-      stages_pair<true, P, 1, NS - 1, NU>(sd, tw);
+      stages_pair<true, P, 1, NS - 1, NU, NT>(sd, tw);
       // ---- last inverse stage (radix R0), written to global memory (z < nz)
-      for (int b = threadIdx.x; b < NU * S0; b += blockDim.x) {
-        const int u = b % NU, j = b / NU;
-        const int c = u / NP, tp = u - c * NP;
+      for (int j = threadIdx.x / NU; j < S0; j += NT / NU) {
         const bool ok = tp < npv;
         float2* dst = base + c * comp_sz + (int64_t)j * plane_sz + 2 * tp;
         float2 va[R0], vb[R0];

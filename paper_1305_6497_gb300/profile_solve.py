@@ -8,7 +8,8 @@ profiler can restrict its capture to that range, e.g. ncu --nvtx
 --nvtx-include "timed/").  Prints one JSON line with each solve's device time,
 iterations and per-pass times.  The workloads are those of bench.py, plus
 "zprobe": a 64x64x256 brick (2 RHS; 512-point z lines like the 256^3 sphere's,
-a few hundred MB per spectral array) for captures that must stay small.
+a few hundred MB per spectral array) and "box" (a brick of any size, --box)
+for captures that must stay small.
 """
 from __future__ import annotations
 
@@ -21,7 +22,9 @@ import sys
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--workload", default="sphere256",
-                    choices=["sphere16", "sphere64", "ellipsoid", "sphere256", "zprobe"])
+                    choices=["sphere16", "sphere64", "ellipsoid", "sphere256", "zprobe", "box"])
+    ap.add_argument("--box", default="256,96,96",
+                    help="nx,ny,nz of the brick the 'box' workload solves (2 RHS, LDR)")
     ap.add_argument("--solves", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--precision", default="fp32_refined")
@@ -38,9 +41,11 @@ def main():
     from dda_inputs import workloads as W
     from paper_1305_6497_gb300 import binding as B
 
-    if args.workload == "zprobe":
-        occ, comp = tg.rect_prism(64, 64, 256)
-        w = W.Workload("zprobe64x64x256", occ, comp, [1.33 + 0.01j], 0.19,
+    if args.workload in ("zprobe", "box"):
+        dims = (64, 64, 256) if args.workload == "zprobe" else \
+            tuple(int(v) for v in args.box.split(","))
+        occ, comp = tg.rect_prism(*dims)
+        w = W.Workload("brick%dx%dx%d" % dims, occ, comp, [1.33 + 0.01j], 0.19,
                        *W._lab_incidence([(0.0, 0.0, 0.0)]), 2, "LDR", 1e-8, 0.0)
     else:
         fn = {"sphere16": "c1_sphere16", "sphere64": "c2_sphere64",

@@ -96,13 +96,14 @@ def test_compiled_z_pass_takes_384_threads(shape):
 
 @pytest.mark.parametrize("shape", [(11, 18, 32), (12, 18, 64), (20, 7, 256), (10, 9, 144),
                                    (6, 40, 256)])
-def test_column_pair_z_kernel_is_bit_identical(shape):
-    """z staging 2 and 3 select the column-pair z kernel (each CTA: two columns
-    per thread, both rows of an octant row, every right-hand side; Ghat read
-    through L2, or staged once in shared memory): the same
-    butterflies, twiddles and multiply per column as the compiled-plan kernel,
-    so the FP32 product is bit-identical, over 1 and 3 right-hand sides, ragged
-    column tiles and odd box sides; it also matches the oracle."""
+def test_column_pair_z_kernel_matches(shape):
+    """z staging 2 and 3 select the column-pair z kernel (two columns per
+    thread, both rows of an octant row and every right-hand side per CTA, its
+    own radix-8 plan of the z length; Ghat read through L2, or staged once in
+    shared memory): the FP32 product equals the compiled-plan kernel's to FP32
+    rounding (another factorization of the same transform) and the oracle's,
+    over ragged column tiles and odd Ly; batched solves (several right-hand
+    sides, some converging first) give the same Q's."""
     from paper_1305_6497_gb300 import binding as B
     occ, comp = tg.ellipsoid(*shape)
     flat, pos = O.site_positions(occ)
@@ -110,25 +111,22 @@ def test_column_pair_z_kernel_is_bit_identical(shape):
     t = B.Target(occ, comp, [1.5 + 0.1j], method="GKDLDR")
     kh, e = np.array([0.36, 0.48, 0.8]), [0.8, -0.6, 0]
     assert t.grid[0] % 2 == 0
-    for zt in (4, 8, 16):
+    ainv = O.site_alpha_inverse(comp.reshape(-1)[flat], [1.5 + 0.1j], "GKDLDR", 0.4, kh)
+    rows = np.arange(0, len(flat), 7)
+    ref = O.matvec_direct(x, pos, ainv, 0.4, "GKDLDR", rows=rows)
+    for zt in (4, 8):
         base = dict(x_lines=16, y_tile=16, z_tile=zt, z_pitch=3 * zt, x_threads=128,
                     y_threads=128, z_threads=256)
         t.set_schedule(dict(base, z_stage_ghat=0), "fp32")
         y0 = t.matvec(0.4, x, kh, e, "fp32")
-        for th, zg in ((128, 2), (256, 2), (192, 3), (256, 3)):
-            try:
-                t.set_schedule(dict(base, z_stage_ghat=zg, z_threads=th), "fp32")
-            except B.DDAError as ex:   # 16 columns of 512 points with Ghat staged
-                assert "shared memory" in str(ex)
-                continue
+        for zg in (2, 3):
+            t.set_schedule(dict(base, z_stage_ghat=zg, z_threads=384), "fp32")
             assert t.schedule("fp32")["z_stage_ghat"] == zg
             y1 = t.matvec(0.4, x, kh, e, "fp32")
-            assert np.array_equal(y1, y0), (zt, th, zg, np.abs(y1 - y0).max())
-    ainv = O.site_alpha_inverse(comp.reshape(-1)[flat], [1.5 + 0.1j], "GKDLDR", 0.4, kh)
-    rows = np.arange(0, len(flat), 7)
-    ref = O.matvec_direct(x, pos, ainv, 0.4, "GKDLDR", rows=rows)
-    assert np.abs(y1[rows] - ref).max() <= 2e-5 * np.abs(ref).max()
-    # batched solves (several right-hand sides, some converging first) agree
+            assert np.abs(y1 - y0).max() <= 2e-6 * np.abs(y0).max(), (zt, zg)
+            assert np.abs(y1[rows] - ref).max() <= 2e-5 * np.abs(ref).max(), (zt, zg)
+        with pytest.raises(B.DDAError):      # the pair kernel runs 384 threads
+            t.set_schedule(dict(base, z_stage_ghat=2, z_threads=256), "fp32")
     w = W.small_ellipsoid(*shape, m=1.5 + 0.1j, kd=0.4, method="LDR", n_orient=3, seed=9)
     t2 = B.Target(w.occ, w.comp, w.m, method="LDR")
     kw = dict(yhat=w.yhat, npol=2, tol=1e-9, precision="fp32_refined", want_P=True)
@@ -137,18 +135,20 @@ def test_column_pair_z_kernel_is_bit_identical(shape):
     t2.set_schedule(dict(sched, z_stage_ghat=0), "fp32")
     a = t2.solve(w.kd, w.khat, w.e01, **kw)
     for zg in (2, 3):
-        t2.set_schedule(dict(sched, z_stage_ghat=zg), "fp32")
+        t2.set_schedule(dict(sched, z_stage_ghat=zg, z_threads=384), "fp32")
         b = t2.solve(w.kd, w.khat, w.e01, **kw)
-        assert np.array_equal(a["P"], b["P"]) and np.array_equal(a["iters"], b["iters"])
+        assert b["status"] == B.DDA_OK
+        assert np.all(np.abs(b["Qext"] / a["Qext"] - 1) < 1e-7)
+        assert np.abs(b["P"] - a["P"]).max() <= 1e-7 * np.abs(a["P"]).max()
     t.close()
     t2.close()
 
 
 def test_column_pair_z_kernel_needs_a_compiled_plan_and_even_x_length():
     from paper_1305_6497_gb300 import binding as B
-    occ, comp = tg.ellipsoid(13, 10, 11)      # Lx = 25 (odd), Lz = 24: no compiled plan
+    occ, comp = tg.ellipsoid(13, 10, 11)      # Lx = 25 (odd), Lz = 24: no pair plan
     t = B.Target(occ, comp, [1.5 + 0.1j], method="CM")
     with pytest.raises(B.DDAError):
         t.set_schedule(dict(x_lines=16, y_tile=16, z_tile=4, z_pitch=12, z_stage_ghat=2,
-                            x_threads=128, y_threads=128, z_threads=128), "fp32")
+                            x_threads=128, y_threads=128, z_threads=384), "fp32")
     t.close()
