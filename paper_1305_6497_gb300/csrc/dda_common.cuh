@@ -167,7 +167,7 @@ template <typename T> struct OpView {
   const int* kx_at; const int* ky_at; const int* kz_at;  // frequency held at each
                                                           // digit-reversed position
   const int* ypos_at;             // position holding each y frequency (inverse of ky_at)
-  const C* twz_pair;              // z twiddles of the column-pair kernel's plan (FP32), or null
+  const float2* twz_pair;         // z twiddles of the column-pair kernel's plan (FP32), or null
   unsigned long long div_nx, div_ny, div_nz, div_Lx;     // fast_div magics
   AxisPlan px, py, pz;
 };
