@@ -131,7 +131,7 @@ def pass_bytes(box, grid, s):
 def _source_hash():
     h = hashlib.sha256()
     for f in ("matvec_impl.cuh", "fft_core.cuh", "fft_plan.cuh", "matvec_fixed.cu",
-              "dda_common.cuh"):
+              "zpass_pair.cuh", "dda_common.cuh"):
         with open(os.path.join(ROOT, "paper_1305_6497_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
