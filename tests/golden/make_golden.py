@@ -82,7 +82,7 @@ def main(which):
             store(f"ellipsoid_o{i}", solve(w, i, tol=1e-10, operator="fft_lowmem",
                                            workers=workers))
     if "sphere256" in which:
-        store("sphere256", solve(W.c5_sphere256(), 0, tol=1e-10, npol=1,
+        store("sphere256", solve(W.c5_sphere256(), 0, tol=1e-9, npol=1,
                                  operator="fft_lowmem", workers=workers))
 
 
