@@ -284,19 +284,26 @@ const char* dda_last_error(void);
  * Without this call the library uses a fixed rule. */
 dda_status dda_autotune(dda_target* t, double kd, int n_rhs);
 
-/* The schedule in use: out8 = {x lines, y tile, z tile, z row pitch, z stages
- * Ghat in shared memory (0/1), threads per CTA of the x, y and z passes} for
- * DDA_PREC_FP64 or (otherwise) FP32. */
+/* The schedule in use: out8 = {x lines, y tile, z tile, z row pitch, z kind,
+ * threads per CTA of the x, y and z passes} for DDA_PREC_FP64 or (otherwise)
+ * FP32.  z kind: 0 / 1 -- one column tile of one right-hand side per CTA, Ghat
+ * read through L2 / staged in shared memory; 2 / 3 -- the FP32 column-pair
+ * kernel (two columns per thread, both rows of an octant row and every
+ * right-hand side per CTA, its own radix-8 plan; Ghat through L2 / staged);
+ * 6 / 7 -- the same with each pass's column tile moved by TMA tensor copies. */
 dda_status dda_target_schedule(const dda_target* t, int precision, int* out8);
 
 /* Set the schedule of DDA_PREC_FP64 or (otherwise) FP32 explicitly, in the
  * layout dda_target_schedule returns (for instance one saved from an earlier
  * dda_autotune).  Values outside x lines 1..64, y tile 1..64, z tile 2/4/8/16,
- * z pitch 3*tile..3*tile+8, z staging 0/1, threads 32..256 (multiples of 32;
- * up to 384 for the FP32 z pass when the target's z length has a compiled
- * radix plan for that tile), or needing more than 200 KB of shared memory:
- * DDA_ERR_INVALID_ARG.  The schedule changes tiling and launch shape only, not
- * the arithmetic. */
+ * z pitch 3*tile..3*tile+8, z kind 0/1/2/3/6/7, threads 32..256 (multiples of
+ * 32; up to 384 for the FP32 z pass when the target's z length has a compiled
+ * radix plan for that tile; exactly 384 for kinds 2..7, which need FP32, an
+ * even Lx, Lz of 64, 128, 288 or 512 and tile 4 or 8, and for 6/7 nz <= 256),
+ * or needing more than 200 KB of shared memory: DDA_ERR_INVALID_ARG.  Kinds
+ * 0/1 and 2/3 factor the z transform differently (the same transform, results
+ * equal to FP32 rounding); otherwise the schedule changes tiling and launch
+ * shape only, not the arithmetic. */
 dda_status dda_set_schedule(dda_target* t, int precision, const int* in8);
 
 /* Kernels launched by this library since the process started (all threads). */

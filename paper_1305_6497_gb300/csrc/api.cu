@@ -305,6 +305,7 @@ struct dda_target {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   DevBuf comp, site, tw64, tw32, twdf, perm;  // perm: k_at x|y|z, then pos x|y|z
   DevBuf twzp;  // FP32 z twiddles of the column-pair kernel's plan (when it has one)
+  DevBuf zerr;  // one int: a kernel's bounded wait on a copy ran out
   AxisPlan px{}, py{}, pz{};
   int twoff[3] = {0, 0, 0};
   // Green transform cache
@@ -357,6 +358,7 @@ static OpView<T> make_view(const dda_target* t, const void* ghat, const void* ai
   v.kz_at = pm + t->Lx + t->Ly;
   v.ypos_at = pm + (t->Lx + t->Ly + t->Lz) + t->Lx;
   v.twz_pair = t->twzp.as<float2>();
+  v.zerr = t->zerr.as<int>();
   v.px = t->px; v.py = t->py; v.pz = t->pz;
   auto magic = [](int d) { return ((1ull << 36) + (unsigned long long)d - 1) / (unsigned long long)d; };
   v.div_nx = magic(v.nx); v.div_ny = magic(v.ny); v.div_nz = magic(v.nz); v.div_Lx = magic(v.Lx);
@@ -1391,6 +1393,7 @@ void dda_target_destroy(dda_target* t) {
   t->ws.release_all();
   t->comp.release(); t->site.release(); t->tw64.release(); t->tw32.release(); t->twdf.release();
   t->twzp.release();
+  t->zerr.release();
   t->perm.release();
   t->g64.release(); t->g32.release(); t->gdf.release(); t->h64.release();
   t->prof.destroy();
@@ -1501,6 +1504,8 @@ dda_status dda_target_create(int nx, int ny, int nz, const uint8_t* occ, const u
     kat.insert(kat.end(), posall.begin(), posall.end());
     t->perm.ensure(sizeof(int) * kat.size());
     CK(cudaMemcpy(t->perm.p, kat.data(), sizeof(int) * kat.size(), cudaMemcpyHostToDevice));
+    t->zerr.ensure(sizeof(int));
+    CK(cudaMemset(t->zerr.p, 0, sizeof(int)));
     // twiddles of the column-pair z kernel's own radix plan (FP32)
     const std::vector<int> prs = pair_plan_radices(t->Lz);
     if (!prs.empty()) {
@@ -2039,6 +2044,15 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
     }
     if (result_status == DDA_ERR_BREAKDOWN) g_last_error = "BiCGSTAB breakdown on some RHS";
     if (result_status == DDA_ERR_NOCONV) g_last_error = "some RHS did not reach tol";
+    // a pass whose bounded wait on a TMA copy ran out stopped early: the
+    // results are not to be trusted
+    int zerr = 0;
+    CK(cudaMemcpy(&zerr, t->zerr.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (zerr) {
+      CK(cudaMemset(t->zerr.p, 0, sizeof(int)));
+      result_status = DDA_ERR_TIMEOUT;
+      g_last_error = "a z-pass copy (TMA) did not complete within its bounded wait";
+    }
   } catch (const CudaFail& f) {
     return from_cuda(f);
   }
@@ -2113,16 +2127,18 @@ void apply_schedule(const dda_target* t, MatvecLaunch& L, const std::vector<int>
   L.y_smem = (size_t)t->Ly * v[1] * sizeof(C);
   L.z_tile = v[2];
   L.z_ps = v[3];
-  // z staging 2, 3: the column-pair kernel, Ghat through L2 (2) or staged (3)
-  L.z_pair = v[4] >= 2 ? 1 : 0;
-  L.z_gs = v[4] == 1 || v[4] == 3;
+  // z staging 2, 3: the column-pair kernel, Ghat through L2 (2) or staged (3);
+  // +4: its column tiles moved by TMA
+  L.z_pair = v[4] >= 6 ? 2 : v[4] >= 2 ? 1 : 0;
+  L.z_gs = v[4] == 1 || v[4] == 3 || v[4] == 7;
   const int Hz = t->Lz / 2 + 1;
   L.z_smem = (((size_t)t->Lz * L.z_ps * sizeof(C) + 15) & ~(size_t)15) +
              (L.z_gs ? (size_t)6 * Hz * L.z_tile * sizeof(C) : 0);
 }
 
 std::vector<int> schedule_of(const MatvecLaunch& L) {
-  return {L.x_lines, L.y_tile, L.z_tile, L.z_ps, (L.z_pair ? 2 : 0) + (L.z_gs ? 1 : 0),
+  return {L.x_lines, L.y_tile, L.z_tile, L.z_ps,
+          (L.z_pair ? 2 : 0) + (L.z_pair == 2 ? 4 : 0) + (L.z_gs ? 1 : 0),
           L.x_threads, L.y_threads, L.z_threads};
 }
 }  // namespace
@@ -2283,13 +2299,15 @@ dda_status dda_set_schedule(dda_target* t, int precision, const int* in8) {
   const bool f64 = precision == DDA_PREC_FP64;
   const size_t cs = f64 ? sizeof(double2) : sizeof(float2);
   if (xl < 1 || xl > 64 || yt < 1 || yt > 64 || (zt != 2 && zt != 4 && zt != 8 && zt != 16) ||
-      zp < 3 * zt || zp > 3 * zt + 8 || zg < 0 || zg > 3)
+      zp < 3 * zt || zp > 3 * zt + 8 || zg < 0 || zg > 7 || zg == 4 || zg == 5)
     return fail(DDA_ERR_INVALID_ARG, "schedule: x lines 1..64, y tile 1..64, z tile 2/4/8/16, "
-                                     "z pitch 3*tile..3*tile+8, z staging 0..3");
+                                     "z pitch 3*tile..3*tile+8, z staging 0, 1, 2, 3, 6 or 7");
   if (zg >= 2 && (f64 || !z_pair_applies(t->Lz, t->Lx, zt) || in8[7] != kZPairThreads))
-    return fail(DDA_ERR_INVALID_ARG, "schedule: z staging 2/3 (column-pair z kernel) needs "
+    return fail(DDA_ERR_INVALID_ARG, "schedule: z staging 2/3/6/7 (column-pair z kernel) needs "
                                      "FP32, an even Lx, Lz of 64, 128, 288 or 512, tile 4 or 8 "
                                      "and 384 threads");
+  if (zg >= 6 && !z_pair_tma_applies(t->Lz, t->Lx, t->nz, zt))
+    return fail(DDA_ERR_INVALID_ARG, "schedule: z staging 6/7 (TMA tiles) needs nz <= 256");
   for (int i = 5; i < 8; ++i) {
     // the FP32 z pass of a compiled radix plan (and the column-pair one) takes
     // up to 384 threads
@@ -2304,8 +2322,7 @@ dda_status dda_set_schedule(dda_target* t, int precision, const int* in8) {
   // a compiled-plan z kernel uses its own pitch, 3 tile (+1 below 128 B rows)
   const int zpc = (!f64 && z_fixed_applies(t->pz, zt))
                       ? std::max(zp, 3 * zt + (zt * (int)cs < 128 ? 1 : 0)) : zp;
-  const size_t zsm = zg >= 2 ? (size_t)t->Lz * 3 * zt * cs +
-                                   (zg == 3 ? (size_t)6 * (t->Lz / 2 + 1) * zt * cs : 0)
+  const size_t zsm = zg >= 2 ? zpair_smem_bytes(t->Lz, zt, zg == 3 || zg == 7)
                              : (((size_t)t->Lz * zpc * cs + 15) & ~(size_t)15) +
                                    (zg ? (size_t)6 * (t->Lz / 2 + 1) * zt * cs : 0);
   if (xinv > 200 * 1024 || ysm > 200 * 1024 || zsm > 200 * 1024)

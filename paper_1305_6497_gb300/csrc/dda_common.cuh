@@ -168,6 +168,7 @@ template <typename T> struct OpView {
                                                           // digit-reversed position
   const int* ypos_at;             // position holding each y frequency (inverse of ky_at)
   const float2* twz_pair;         // z twiddles of the column-pair kernel's plan (FP32), or null
+  int* zerr;                      // set to 1 by a kernel whose bounded wait on a copy ran out
   unsigned long long div_nx, div_ny, div_nz, div_Lx;     // fast_div magics
   AxisPlan px, py, pz;
 };

@@ -17,7 +17,7 @@ struct MatvecLaunch {
   int y_tile, y_threads; size_t y_smem;
   int z_tile, z_ps, z_threads; size_t z_smem;
   bool z_gs;   // Ghat tile staged in shared memory
-  int z_pair;  // FP32 compiled plans: the column-pair z kernel (k_fft_z_pairs)
+  int z_pair;  // FP32: the column-pair z kernel (k_fft_z_pairs); 2: with TMA tiles
 };
 
 template <typename T> MatvecLaunch plan_matvec(const OpView<T>& op);
@@ -98,6 +98,11 @@ bool z_fixed_applies(const AxisPlan& P, int tile);
 // 288, 512), Lx even, tile 4 or 8; it always runs kZPairThreads threads.
 bool z_pair_applies(int Lz, int Lx, int tile);
 constexpr int kZPairThreads = 384;
+// Dynamic shared memory of the column-pair z kernel (with the Ghat tile if gs).
+size_t zpair_smem_bytes(int Lz, int tile, bool gs);
+// The column-pair kernel's TMA variant applies as well: nz <= 256 (a box
+// dimension), 2 nz <= Lz, and a driver that encodes tensor maps.
+bool z_pair_tma_applies(int Lz, int Lx, int nz, int tile);
 
 // A vector pass that finishes one of the Krylov scalar steps in its last
 // block (instead of a separate one-block kernel): `counter` holds one word per

@@ -4,6 +4,7 @@
 // 288 = 8x4x3x3 (z).  The variants live in their own translation unit so the
 // build compiles them in parallel with the generic kernels; any other plan,
 // tile or precision takes the generic kernels.
+#include <cstring>
 #include <type_traits>
 
 #include "matvec_impl.cuh"
@@ -103,6 +104,51 @@ bool z_pair_applies(int Lz, int Lx, int tile) {
          dispatch_length(Lz, PairPlans{}, [](auto) {});
 }
 
+size_t zpair_smem_bytes(int Lz, int tile, bool gs) {
+  return (size_t)Lz * 3 * (tile / 2) * sizeof(float4) +
+         (gs ? (size_t)tile * zpair_gstride(Lz / 2 + 1) * sizeof(float2) : 0);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library links the runtime only); resolved once.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+bool z_pair_tma_applies(int Lz, int Lx, int nz, int tile) {
+  return z_pair_applies(Lz, Lx, tile) && nz <= 256 && 2 * nz <= Lz && encode_fn() != nullptr;
+}
+
+bool encode_zpair_map(CUtensorMap* map, const float2* scratch, int Lx, int Ly, int nz, int R,
+                      int tile) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || ((uintptr_t)scratch & 15) || Lx % 2) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)Lx, (cuuint64_t)Ly, (cuuint64_t)nz, (cuuint64_t)3 * R};
+  const cuuint64_t strides[3] = {(cuuint64_t)Lx * 8, (cuuint64_t)Ly * Lx * 8,
+                                 (cuuint64_t)nz * Ly * Lx * 8};
+  const cuuint32_t box[4] = {(cuuint32_t)tile, 1, (cuuint32_t)nz, 3};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<float2*>(scratch), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool launch_z_fixed(const OpView<float>& op, const MatvecLaunch& L, int R, float2* scratch,
                     const int* active, cudaStream_t st) {
   bool done = false;
@@ -112,14 +158,27 @@ bool launch_z_fixed(const OpView<float>& op, const MatvecLaunch& L, int R, float
       using P = decltype(plan);
       constexpr int NT = kZPairThreads;
       const dim3 gz((op.Lx + L.z_tile - 1) / L.z_tile, op.Ly / 2 + 1);
+      CUtensorMap map;
+      std::memset(&map, 0, sizeof map);
+      const bool tma = L.z_pair == 2 && z_pair_tma_applies(op.Lz, op.Lx, op.nz, L.z_tile) &&
+                       encode_zpair_map(&map, scratch, op.Lx, op.Ly, op.nz, R, L.z_tile);
       auto go = [&](auto tile) {
         constexpr int TT = decltype(tile)::value;
-        if (L.z_gs)
-          k_fft_z_pairs<TT, P, true, NT><<<gz, NT, zpair_smem<TT, P, true>(), st>>>(
-              op, scratch, R, active);
-        else
-          k_fft_z_pairs<TT, P, false, NT><<<gz, NT, zpair_smem<TT, P, false>(), st>>>(
-              op, scratch, R, active);
+        if (tma) {
+          if (L.z_gs)
+            k_fft_z_pairs<TT, P, true, NT, true><<<gz, NT, zpair_smem<TT, P, true>(), st>>>(
+                op, scratch, R, active, map);
+          else
+            k_fft_z_pairs<TT, P, false, NT, true><<<gz, NT, zpair_smem<TT, P, false>(), st>>>(
+                op, scratch, R, active, map);
+        } else {
+          if (L.z_gs)
+            k_fft_z_pairs<TT, P, true, NT, false><<<gz, NT, zpair_smem<TT, P, true>(), st>>>(
+                op, scratch, R, active, map);
+          else
+            k_fft_z_pairs<TT, P, false, NT, false><<<gz, NT, zpair_smem<TT, P, false>(), st>>>(
+                op, scratch, R, active, map);
+        }
         done = true;
       };
       if (L.z_tile == 4) go(IC<4>{});
@@ -222,10 +281,14 @@ cudaError_t configure_fixed_kernels() {
   auto zpcfg = [&](auto plan) {
     using P = decltype(plan);
     constexpr int NT = kZPairThreads;
-    ok(set_smem((const void*)k_fft_z_pairs<4, P, false, NT>));
-    ok(set_smem((const void*)k_fft_z_pairs<8, P, false, NT>));
-    ok(set_smem((const void*)k_fft_z_pairs<4, P, true, NT>));
-    ok(set_smem((const void*)k_fft_z_pairs<8, P, true, NT>));
+    ok(set_smem((const void*)k_fft_z_pairs<4, P, false, NT, false>));
+    ok(set_smem((const void*)k_fft_z_pairs<8, P, false, NT, false>));
+    ok(set_smem((const void*)k_fft_z_pairs<4, P, true, NT, false>));
+    ok(set_smem((const void*)k_fft_z_pairs<8, P, true, NT, false>));
+    ok(set_smem((const void*)k_fft_z_pairs<4, P, false, NT, true>));
+    ok(set_smem((const void*)k_fft_z_pairs<8, P, false, NT, true>));
+    ok(set_smem((const void*)k_fft_z_pairs<4, P, true, NT, true>));
+    ok(set_smem((const void*)k_fft_z_pairs<8, P, true, NT, true>));
   };
   zpcfg(QP64{}); zpcfg(QP128{}); zpcfg(QP288{}); zpcfg(QP512{});
   auto ycfg = [&](auto plan) {

@@ -154,14 +154,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_fwd(OpVie
   else fft_smem_p<C, false, P>(s, nlines, div_nl, ps, op.twx, half);
   const int64_t plane_sz = (int64_t)op.Ly * Lx;
   C* dst = buf + (int64_t)r * 3 * op.nz * plane_sz;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < nlines * Lx; e += blockDim.x) {
-    const int line = LP ? e / LP : fast_div(e, op.div_Lx), p = e - line * Lx;
+  // one line at a time: the row's plane and y are worked out once per line
+  const int nrow = min(nlines, rows - row0);
+  for (int line = 0; line < nrow; ++line) {
     const int row = row0 + line;
-    if (row < rows) {
-      const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
-      dst[plane * plane_sz + (int64_t)y * Lx + p] = s[p * ps + line];
-    }
+    const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
+    C* drow = dst + plane * plane_sz + (int64_t)y * Lx;
+#pragma unroll 4
+    for (int p = threadIdx.x; p < Lx; p += blockDim.x) drow[p] = s[p * ps + line];
   }
 }
 
@@ -819,15 +819,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
     cp_async<(int)sizeof(IO)>(&sx[e], &xin[g0 + e]);
     if (MODE == XOUT_RV) cp_async<(int)sizeof(IO)>(&sh[e], &rhat[g0 + e]);
   }
-  // all of the tile's loads in flight at once (asynchronous copies)
-  for (int e = threadIdx.x; e < nlines * Lx; e += blockDim.x) {
-    const int line = LP ? e / LP : fast_div(e, op.div_Lx), p = e - line * Lx;
+  // all of the tile's loads in flight at once (asynchronous copies); the row's
+  // plane and y are worked out once per line.  Each line's site information
+  // for the epilogue (composition row, polarization component) goes to a
+  // small table (at most 64 lines per CTA).
+  __shared__ int line_site[64], line_comp[64];
+  for (int line = 0; line < nlines; ++line) {
     const int row = row0 + line;
     if (row < rows) {
       const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
-      cp_async<(int)sizeof(C)>(&s[p * ps + line], &src[plane * plane_sz + (int64_t)y * Lx + p]);
+      const C* srow = src + plane * plane_sz + (int64_t)y * Lx;
+      for (int p = threadIdx.x; p < Lx; p += blockDim.x)
+        cp_async<(int)sizeof(C)>(&s[p * ps + line], &srow[p]);
+      if (threadIdx.x == 0) {
+        // row = (c nz + z) ny + y  ->  sites (z ny + y) nx + p
+        const int c = fast_div(plane, op.div_nz);
+        line_site[line] = ((plane - c * op.nz) * op.ny + y) * nx;
+        line_comp[line] = c;
+      }
     } else {
-      s[p * ps + line] = mk<C>(0, 0);
+      for (int p = threadIdx.x; p < Lx; p += blockDim.x) s[p * ps + line] = mk<C>(0, 0);
     }
   }
   cp_async_commit();
@@ -853,14 +864,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
       cms[u] = 0;
       if (e < nin && MODE != XOUT_FIELD) {
         const int line = fast_div(e, op.div_nx), p = e - line * nx;
-        const int row = row0 + line;
-        // row = (c nz + z) ny + y  ->  site (z ny + y) nx + p; the alpha^{-1}
-        // entry of composition cm on axis c is 3 cm + c (0: vacant)
-        const int plane = fast_div(row, op.div_ny), y = row - plane * op.ny;
-        const int c = fast_div(plane, op.div_nz);
-        const int z = plane - c * op.nz;
-        const int cm = op.comp[((int64_t)z * op.ny + y) * nx + p];
-        cms[u] = cm ? 3 * cm + c : 0;
+        // the alpha^{-1} entry of composition cm on axis c is 3 cm + c (0: vacant)
+        const int cm = op.comp[line_site[line] + p];
+        cms[u] = cm ? 3 * cm + line_comp[line] : 0;
       }
     }
 #pragma unroll

@@ -151,15 +151,16 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
     // the column-pair kernel (FP32, compiled z plans)
     if (std::is_same<T, float>::value)
       for (int tile : {4, 8})
-        for (int gs = 0; gs < 2; ++gs) {
+        for (int gs = 0; gs < 2; ++gs)
+        for (int tma = 0; tma < 2; ++tma) {
           const int th = kZPairThreads;
           if (!z_pair_applies(op.Lz, op.Lx, tile)) continue;
-          const size_t zs = (size_t)op.Lz * 3 * tile * sizeof(C) +
-                            (gs ? (size_t)6 * op.Hz * tile * sizeof(C) : 0);
+          if (tma && !z_pair_tma_applies(op.Lz, op.Lx, op.nz, tile)) continue;
+          const size_t zs = zpair_smem_bytes(op.Lz, tile, gs != 0);
           if (zs > kMax) continue;
           MatvecLaunch c = best;
           fill_z<T>(op, c, tile, 0, gs != 0);
-          c.z_pair = 1;
+          c.z_pair = tma ? 2 : 1;
           c.z_smem = zs;
           c.z_threads = th;
           const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);

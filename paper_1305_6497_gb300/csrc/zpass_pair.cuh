@@ -16,7 +16,14 @@
 //     false), or staged once in shared memory with cp.async while the first
 //     forward transform runs (GS = true);
 //   * the last forward stage, the multiply and the first inverse stage are
-//     separate sweeps over shared memory (each conflict-free for this layout).
+//     separate sweeps over shared memory; the multiply visits positions in a
+//     skewed order and the Ghat tile's columns are padded so that its 16-byte
+//     accesses avoid bank conflicts;
+//   * optionally (TMA) each pass's column tile is loaded and stored by the
+//     tensor-memory accelerator: one cp.async.bulk.tensor box per pass, landing
+//     in (and leaving from) the upper half of the transform's shared memory,
+//     with an mbarrier wait bounded in time (a kernel whose copy never arrives
+//     sets op.zerr and returns).
 // The plan P (e.g. 512 = 8 x 8 x 8) need not be the target's z plan: the z
 // transform starts and ends inside this kernel, so only the frequency held at
 // each position (P::k_at, for the multiply) and P's twiddle table (op.twz_pair)
@@ -26,14 +33,80 @@
 // loops).  The arithmetic is the same transform with another factorization,
 // so results agree with the other z kernels to rounding, not bit for bit.
 //
-// grid: (ceil(Lx / TILE), Ly / 2 + 1), any block size.  Needs Lx even (pairs
-// of columns are 16-byte aligned).  Shared memory: Lz * 3 * TILE/2 float4,
-// plus (GS) the Ghat tile, (Lz/2 + 1) * TILE * 6 float2.
+// grid: (ceil(Lx / TILE), Ly / 2 + 1), NT threads.  Needs Lx even (pairs of
+// columns are 16-byte aligned) and, for TMA, nz <= 256.  Shared memory: Lz * 3 *
+// TILE/2 float4, plus (GS) the Ghat tile, TILE * zpair_gstride(Lz/2 + 1) float2.
 #pragma once
+
+#include <cuda.h>  // CUtensorMap
 
 #include "matvec_impl.cuh"
 
 namespace dda {
+
+// ---- tensor-memory-access (TMA) copies and mbarriers, inline PTX ----------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// global -> shared copy of one box of a 4-D tensor map, completing on bar
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_addr(bar))
+      : "memory");
+}
+// shared -> global copy of one box (elements outside the tensor are dropped)
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0,
+                                             int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::
+          "l"(reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// wait until the committed bulk stores have read their shared memory
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// wait until the committed bulk stores have completed
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// Bounded wait on an mbarrier phase: false after 2^22 polls (each poll may
+// suspend the thread for a while in hardware), i.e. well over a second.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
 
 __device__ __forceinline__ void split4(const float4 q, float2& a, float2& b) {
   a = make_float2(q.x, q.y);
@@ -83,6 +156,59 @@ __device__ __forceinline__ void stage_pair(float4* sd, const float2* __restrict_
   __syncthreads();
 }
 
+// The multiply visits the positions of a transform in a skewed order: item v
+// (0 <= v < L) takes the last digit m_last = v mod R_last, the middle digits from
+// the middle of v and the first digit m_0 = (m_last + top of v) mod R_0, so that
+// neighbouring items differ both in the position's last digit (its shared-memory
+// row, rows are consecutive) and in the frequency's first digit (its Ghat row);
+// with either natural order the other would repeat across a quarter-warp and
+// the 16-byte accesses would collide on the same banks.  Returns the position
+// p and the frequency k held there.
+template <class P>
+__device__ __forceinline__ void skew_item(int v, int& p, int& k) {
+  constexpr int NS = P::NS, R0 = P::radix(0), RL = P::radix(NS - 1);
+  const int a = v % RL;
+  int rest = v / RL;
+  int pos = a * P::span(NS - 1), frq = a * P::nprod(NS - 1);
+#pragma unroll
+  for (int t = NS - 2; t >= 1; --t) {
+    const int m = rest % P::radix(t);
+    rest /= P::radix(t);
+    pos += m * P::span(t);
+    frq += m * P::nprod(t);
+  }
+  const int m0 = (a + rest) % R0;
+  p = pos + m0 * P::span(0);
+  k = frq + m0;
+}
+
+// Ghat tile of a pair-kernel CTA in shared memory: column t's rows hz at
+// gs[t * stride + 6 hz] (float2), the column stride padded so that the columns
+// 2 apart (the same instruction's other column pair) land 64 bytes apart
+// modulo the 128-byte bank cycle.
+__host__ __device__ constexpr int zpair_gstride(int Hz) {
+  return ((Hz * 48 + 63) / 64 * 64 + 32) / 8;  // in float2
+}
+
+template <int TILE>
+__device__ __forceinline__ void ghat_tile_pairs_async(const OpView<float>& op, float2* gs,
+                                                      int col0, int ncol, int hy) {
+  const int stride = zpair_gstride(op.Hz);
+  const int n = op.Hz * TILE * 3;  // 16-byte chunks: 3 per point
+  const int64_t plane = (int64_t)op.Hy * op.Hx;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int ch = e % 3, pt = e / 3;
+    const int hz = pt % op.Hz, t = pt / op.Hz;
+    if (t < ncol) {
+      const int kx = op.kx_at[col0 + t];
+      const int hx = kx > (op.Lx >> 1) ? op.Lx - kx : kx;
+      const float2* src = op.ghat + 6 * (hz * plane + (int64_t)hy * op.Hx + hx) + 2 * ch;
+      cp_async<16>(gs + t * stride + 6 * hz + 2 * ch, src);
+    }
+  }
+  cp_async_commit();
+}
+
 // Stages LO..HI forward (ascending) or inverse (descending).
 template <bool INV, class P, int LO, int HI, int NU, int NT>
 __device__ __forceinline__ void stages_pair(float4* sd, const float2* __restrict__ tw) {
@@ -97,21 +223,25 @@ __device__ __forceinline__ void stages_pair(float4* sd, const float2* __restrict
   }
 }
 
-template <int TILE, class P, bool GS, int NT>
+template <int TILE, class P, bool GS, int NT, bool TMA>
 __global__ void __launch_bounds__(NT, 2)
-k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __restrict__ active) {
+k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __restrict__ active,
+              const __grid_constant__ CUtensorMap tmap) {
   static_assert(TILE % 2 == 0, "column pairs");
   constexpr int L = P::L, NS = P::NS, R0 = P::radix(0), S0 = P::span(0);
   constexpr int NP = TILE / 2, NU = 3 * NP;
   static_assert(NT % NU == 0 && NT % NP == 0, "a thread keeps one pair-line");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* sd = reinterpret_cast<float4*>(smem_raw);
+  static_assert(((L / 2) * NU * 16) % 128 == 0, "TMA staging rows 128-byte aligned");
+  // (128-byte aligned: the TMA staging rows start at a multiple of 128 bytes)
+  extern __shared__ __align__(128) unsigned char zpair_smem_raw[];
+  float4* sd = reinterpret_cast<float4*>(zpair_smem_raw);
   float2* gs = reinterpret_cast<float2*>(sd + L * NU);
   const int Lx = op.Lx, Ly = op.Ly, nz = op.nz;
   const int hy = blockIdx.y;
   const int col0 = blockIdx.x * TILE;
   const int npv = min(TILE, Lx - col0) >> 1;  // pairs inside the grid (Lx even)
-  if (GS) ghat_tile_async<float, TILE>(op, gs, col0, 2 * npv, hy);
+  if (GS) ghat_tile_pairs_async<TILE>(op, gs, col0, 2 * npv, hy);
+  const int gstride = zpair_gstride(op.Hz);
   const int64_t plane_sz = (int64_t)Ly * Lx;
   const int64_t comp_sz = (int64_t)nz * plane_sz;
   const bool half = 2 * nz <= L;
@@ -120,6 +250,20 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
   const int u = threadIdx.x % NU;           // this thread's pair-line ...
   const int c = u / NP, tp = u - c * NP;    // ... = component c, column pair tp
   const int tpm = threadIdx.x % NP;         // its column pair in the multiply
+  // TMA: each pass's input tile lands in the upper half of sd (rows >= L/2, free
+  // until the first stage writes them: the inputs are the nz <= L/2 lower rows)
+  // as [c][z][t]; the output tile leaves from there the same way.
+  __shared__ __align__(8) uint64_t bar;
+  float2* stg = reinterpret_cast<float2*>(sd + (L / 2) * NU);
+  unsigned phase = 0;
+  if (TMA) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+  }
+  constexpr int NJ = (S0 + NT / NU - 1) / (NT / NU);  // first-stage items per thread
   // the rows sharing octant row hy: ky = hy, and ky = Ly - hy unless that is hy
   const int nrow = (hy == 0 || 2 * hy == Ly) ? 1 : 2;
   for (int rr = 0; rr < nrow; ++rr) {
@@ -129,31 +273,49 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
     for (int r = 0; r < R; ++r) {
       if (active && !active[r]) continue;
       float2* base = buf + (int64_t)r * 3 * comp_sz + (int64_t)pyy * Lx + col0;
+      if (TMA) {
+        if (threadIdx.x == 0) {
+          fence_proxy_async();  // sd's earlier generic accesses before the async write
+          mbar_arrive_expect_tx(&bar, (unsigned)(3 * nz * TILE * sizeof(float2)));
+          tma_load_4d(stg, &tmap, &bar, col0, pyy, 0, 3 * r);
+        }
+        const bool ok = mbar_wait_bounded(&bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {  // the copy never completed: report and stop
+          if (threadIdx.x == 0 && op.zerr) atomicExch(op.zerr, 1);
+          return;
+        }
+      }
       // ---- first forward stage (radix R0, span S0), read from global memory
-      for (int j = threadIdx.x / NU; j < S0; j += NT / NU) {
+      // (or, with TMA, from the staged tile; its outputs then wait for every
+      // thread's reads before overwriting the staging rows)
+      float4 keep[TMA ? NJ * R0 : 1];
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj) {
+        const int j = threadIdx.x / NU + jj * (NT / NU);
+        if (j >= S0) break;
         const bool ok = tp < npv;
         const float2* src = base + c * comp_sz + (int64_t)j * plane_sz + 2 * tp;
         float2 va[R0], vb[R0];
-        if (R0 % 2 == 0 && half) {
+        const int nin = (R0 % 2 == 0 && half) ? R0 / 2 : R0;
 #pragma unroll
-          for (int i = 0; i < R0 / 2; ++i) {
-            const float4 q = (ok && j + i * S0 < nz)
-                                 ? *reinterpret_cast<const float4*>(src + (int64_t)i * S0 * plane_sz)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-            split4(q, va[i], vb[i]);
+        for (int i = 0; i < R0; ++i) {
+          if (i >= nin) break;
+          const int z = j + i * S0;
+          float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (TMA) {
+            if (z < nz) q = *reinterpret_cast<const float4*>(stg + (c * nz + z) * TILE + 2 * tp);
+          } else if (ok && z < nz) {
+            q = *reinterpret_cast<const float4*>(src + (int64_t)i * S0 * plane_sz);
           }
+          split4(q, va[i], vb[i]);
+        }
+        if (R0 % 2 == 0 && half) {
           if constexpr (R0 % 2 == 0) {
             dft_half<R0, false, true, false>(va);
             dft_half<R0, false, true, false>(vb);
           }
         } else {
-#pragma unroll
-          for (int i = 0; i < R0; ++i) {
-            const float4 q = (ok && j + i * S0 < nz)
-                                 ? *reinterpret_cast<const float4*>(src + (int64_t)i * S0 * plane_sz)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-            split4(q, va[i], vb[i]);
-          }
           dft<R0, false>(va);
           dft<R0, false>(vb);
         }
@@ -166,8 +328,21 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
           }
         }
 #pragma unroll
-        for (int m = 0; m < R0; ++m)
-          sd[(j + m * S0) * NU + u] = make_float4(va[m].x, va[m].y, vb[m].x, vb[m].y);
+        for (int m = 0; m < R0; ++m) {
+          const float4 o = make_float4(va[m].x, va[m].y, vb[m].x, vb[m].y);
+          if (TMA) keep[jj * R0 + m] = o;
+          else sd[(j + m * S0) * NU + u] = o;
+        }
+      }
+      if (TMA) {
+        __syncthreads();  // every staged input has been read
+#pragma unroll
+        for (int jj = 0; jj < NJ; ++jj) {
+          const int j = threadIdx.x / NU + jj * (NT / NU);
+          if (j >= S0) break;
+#pragma unroll
+          for (int m = 0; m < R0; ++m) sd[(j + m * S0) * NU + u] = keep[jj * R0 + m];
+        }
       }
       __syncthreads();
       stages_pair<false, P, 1, NS - 1, NU, NT>(sd, tw);
@@ -175,23 +350,25 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
         cp_async_wait_all();
         __syncthreads();
       }
-      // ---- multiply by Ghat at each frequency (all three components)
-      for (int p = threadIdx.x / NP; p < L && tpm < npv; p += NT / NP) {
-        const int tp = tpm;
-        const int kz = P::k_at(p);
+      // ---- multiply by Ghat at each frequency (all three components), the
+      // positions in the skewed order of skew_item
+      for (int v = threadIdx.x / NP; v < L && tpm < npv; v += NT / NP) {
+        const int tp2 = tpm;
+        int p, kz;
+        skew_item<P>(v, p, kz);
         const bool fz = kz > L / 2;
         const int hz = fz ? L - kz : kz;
-        float4* row = sd + p * NU + tp;
+        float4* row = sd + p * NU + tp2;
         float2 a[3], bb[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) split4(row[c * NP], a[c], bb[c]);
+        for (int cc = 0; cc < 3; ++cc) split4(row[cc * NP], a[cc], bb[cc]);
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          const int kx = op.kx_at[col0 + 2 * tp + e];
+          const int kx = op.kx_at[col0 + 2 * tp2 + e];
           const bool fx = kx > kxh;
           float2 g[6];
           if (GS) {
-            G6<float>::load_smem(gs + 6 * (hz * TILE + 2 * tp + e), g);
+            G6<float>::load_smem(gs + (2 * tp2 + e) * gstride + 6 * hz, g);
           } else {
             const int hx = fx ? Lx - kx : kx;
             G6<float>::load(op.ghat + 6 * (((int64_t)hz * op.Hy + hy) * op.Hx + hx), g);
@@ -199,12 +376,19 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
           spectral_mul<float, false>(g, fx, fy, fz, e ? bb : a, 1);
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) row[c * NP] = make_float4(a[c].x, a[c].y, bb[c].x, bb[c].y);
+        for (int cc = 0; cc < 3; ++cc)
+          row[cc * NP] = make_float4(a[cc].x, a[cc].y, bb[cc].x, bb[cc].y);
       }
       __syncthreads();
       stages_pair<true, P, 1, NS - 1, NU, NT>(sd, tw);
-      // ---- last inverse stage (radix R0), written to global memory (z < nz)
-      for (int j = threadIdx.x / NU; j < S0; j += NT / NU) {
+      // ---- last inverse stage (radix R0), written to global memory (z < nz);
+      // with TMA the outputs go to the staging rows once every thread has
+      // read its inputs, and one tensor store writes the tile
+      float4 outk[TMA ? NJ * R0 : 1];
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj) {
+        const int j = threadIdx.x / NU + jj * (NT / NU);
+        if (j >= S0) break;
         const bool ok = tp < npv;
         float2* dst = base + c * comp_sz + (int64_t)j * plane_sz + 2 * tp;
         float2 va[R0], vb[R0];
@@ -218,35 +402,65 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
             vb[m] = cmulc(w, vb[m]);
           }
         }
-        if (R0 % 2 == 0 && half) {
+        const bool hout = R0 % 2 == 0 && half;
+        if (hout) {
           if constexpr (R0 % 2 == 0) {
             dft_half<R0, true, false, true>(va);
             dft_half<R0, true, false, true>(vb);
           }
-#pragma unroll
-          for (int i = 0; i < R0 / 2; ++i)
-            if (ok && j + i * S0 < nz)
-              *reinterpret_cast<float4*>(dst + (int64_t)i * S0 * plane_sz) =
-                  make_float4(va[i].x, va[i].y, vb[i].x, vb[i].y);
         } else {
           dft<R0, true>(va);
           dft<R0, true>(vb);
+        }
 #pragma unroll
-          for (int i = 0; i < R0; ++i)
-            if (ok && j + i * S0 < nz)
-              *reinterpret_cast<float4*>(dst + (int64_t)i * S0 * plane_sz) =
-                  make_float4(va[i].x, va[i].y, vb[i].x, vb[i].y);
+        for (int i = 0; i < R0; ++i) {
+          if (hout && i >= R0 / 2) break;
+          const float4 o = make_float4(va[i].x, va[i].y, vb[i].x, vb[i].y);
+          if (TMA) outk[jj * R0 + i] = o;
+          else if (ok && j + i * S0 < nz)
+            *reinterpret_cast<float4*>(dst + (int64_t)i * S0 * plane_sz) = o;
+        }
+      }
+      if (TMA) {
+        __syncthreads();  // every input of the last stage has been read
+#pragma unroll
+        for (int jj = 0; jj < NJ; ++jj) {
+          const int j = threadIdx.x / NU + jj * (NT / NU);
+          if (j >= S0) break;
+          // (with the pruned stage only i < R0/2 were formed; the others have
+          // z >= R0/2 * S0 = L/2 >= nz)
+#pragma unroll
+          for (int i = 0; i < R0; ++i) {
+            const int z = j + i * S0;
+            if (z < nz)
+              *reinterpret_cast<float4*>(stg + (c * nz + z) * TILE + 2 * tp) = outk[jj * R0 + i];
+          }
+        }
+        fence_proxy_async();  // the generic writes, before the async store reads them
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          tma_store_4d(&tmap, stg, col0, pyy, 0, 3 * r);
+          bulk_commit();
+          bulk_wait_read();  // the staging rows may be overwritten from here on
         }
       }
       __syncthreads();  // the next pass overwrites sd
     }
   }
   if (GS) cp_async_wait_all();  // no copy outlives the CTA (every RHS may be frozen)
+  if (TMA && threadIdx.x == 0) bulk_wait_all();
 }
+
+// 4-D tensor map of the spectral scratch [R][3][nz][Ly][Lx] (8-byte complex
+// FP32 elements) with a box of TILE columns x 1 row x nz planes x 3 components,
+// for the TMA variant; false when the driver call is unavailable or refuses
+// (the caller then keeps the plain loads).
+bool encode_zpair_map(CUtensorMap* map, const float2* scratch, int Lx, int Ly, int nz, int R,
+                      int tile);
 
 template <int TILE, class P, bool GS> constexpr size_t zpair_smem() {
   return (size_t)P::L * 3 * (TILE / 2) * sizeof(float4) +
-         (GS ? (size_t)(P::L / 2 + 1) * TILE * 6 * sizeof(float2) : 0);
+         (GS ? (size_t)TILE * zpair_gstride(P::L / 2 + 1) * sizeof(float2) : 0);
 }
 
 }  // namespace dda

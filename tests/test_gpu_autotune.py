@@ -100,10 +100,12 @@ def test_column_pair_z_kernel_matches(shape):
     """z staging 2 and 3 select the column-pair z kernel (two columns per
     thread, both rows of an octant row and every right-hand side per CTA, its
     own radix-8 plan of the z length; Ghat read through L2, or staged once in
-    shared memory): the FP32 product equals the compiled-plan kernel's to FP32
-    rounding (another factorization of the same transform) and the oracle's,
-    over ragged column tiles and odd Ly; batched solves (several right-hand
-    sides, some converging first) give the same Q's."""
+    shared memory), 6 and 7 the same with each pass's column tile loaded and
+    stored by TMA (bit-identical to 2 and 3): the FP32 product equals the
+    compiled-plan kernel's to FP32 rounding (another factorization of the same
+    transform) and the oracle's, over ragged column tiles and odd Ly; batched
+    solves (several right-hand sides, some converging first) give the same
+    Q's."""
     from paper_1305_6497_gb300 import binding as B
     occ, comp = tg.ellipsoid(*shape)
     flat, pos = O.site_positions(occ)
@@ -119,12 +121,16 @@ def test_column_pair_z_kernel_matches(shape):
                     y_threads=128, z_threads=256)
         t.set_schedule(dict(base, z_stage_ghat=0), "fp32")
         y0 = t.matvec(0.4, x, kh, e, "fp32")
-        for zg in (2, 3):
+        prev = {}
+        for zg in (2, 3, 6, 7):
             t.set_schedule(dict(base, z_stage_ghat=zg, z_threads=384), "fp32")
             assert t.schedule("fp32")["z_stage_ghat"] == zg
             y1 = t.matvec(0.4, x, kh, e, "fp32")
             assert np.abs(y1 - y0).max() <= 2e-6 * np.abs(y0).max(), (zt, zg)
             assert np.abs(y1[rows] - ref).max() <= 2e-5 * np.abs(ref).max(), (zt, zg)
+            if zg >= 6:   # TMA tiles: the same arithmetic as plain loads and stores
+                assert np.array_equal(y1, prev[zg - 4]), (zt, zg)
+            prev[zg] = y1
         with pytest.raises(B.DDAError):      # the pair kernel runs 384 threads
             t.set_schedule(dict(base, z_stage_ghat=2, z_threads=256), "fp32")
     w = W.small_ellipsoid(*shape, m=1.5 + 0.1j, kd=0.4, method="LDR", n_orient=3, seed=9)
@@ -134,7 +140,7 @@ def test_column_pair_z_kernel_matches(shape):
                  z_threads=256)
     t2.set_schedule(dict(sched, z_stage_ghat=0), "fp32")
     a = t2.solve(w.kd, w.khat, w.e01, **kw)
-    for zg in (2, 3):
+    for zg in (2, 3, 6, 7):
         t2.set_schedule(dict(sched, z_stage_ghat=zg, z_threads=384), "fp32")
         b = t2.solve(w.kd, w.khat, w.e01, **kw)
         assert b["status"] == B.DDA_OK
