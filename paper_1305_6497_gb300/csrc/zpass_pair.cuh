@@ -282,7 +282,11 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
         const bool ok = mbar_wait_bounded(&bar, phase);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {  // the copy never completed: report and stop
-          if (threadIdx.x == 0 && op.zerr) atomicExch(op.zerr, 1);
+          if (threadIdx.x == 0) {
+            if (op.zerr) atomicExch(op.zerr, 1);
+            bulk_wait_all();  // the stores already issued finish before the exit
+          }
+          if (GS) cp_async_wait_all();
           return;
         }
       }

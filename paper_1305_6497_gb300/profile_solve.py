@@ -30,7 +30,7 @@ def main():
     ap.add_argument("--precision", default="fp32_refined")
     ap.add_argument("--solver", default="bicgstab")
     ap.add_argument("--z-schedule", default="",
-                    help="tile,staging,threads: override the tuned FP32 z pass (staging 0/1/2)")
+                    help="tile,kind,threads: override the tuned FP32 z pass (kind 0/1/2/3/6/7)")
     args = ap.parse_args()
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
