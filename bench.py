@@ -138,8 +138,9 @@ def _source_hash():
 
 
 def _ncu_traffic(kernel, workload):
-    """Per-RHS DRAM traffic of `kernel` from the committed ncu summary, or None
-    if it was taken on a different version of the kernel sources."""
+    """DRAM bytes per launch of `kernel` (all right-hand sides active) from the
+    committed ncu summary, or None if it was taken on a different version of
+    the kernel sources."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -147,9 +148,9 @@ def _ncu_traffic(kernel, workload):
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and not line.startswith("#"):
-            k, w, sha, per_rhs = parts[:4]
+            k, w, sha, per_launch = parts[:4]
             if k == kernel and w == workload and sha == src:
-                return float(per_rhs)
+                return float(per_launch)
     return None
 
 
@@ -435,7 +436,11 @@ def run_gpu(args, rank, world, local_rank):
     alg = per_rhs[dom] * fp32_rhs_mv + per_launch.get(dom, 0) * ncall
     achieved = alg / (tms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic_rhs = _ncu_traffic(dom, wl)
+    traffic_launch = _ncu_traffic(dom, wl)
+    # the z pass runs the column-pair kernel for z kinds 2..7, else the
+    # one-column-tile kernels
+    zk = schedule["fp32"]["z_stage_ghat"]
+    kname = {"z_mul": "k_fft_z_pairs" if zk >= 2 else "k_fft_z_mul"}.get(dom, f"k_fft_{dom}")
     share = {f"{p}": round(kern_ms[("fp32", p)] / sum(step_ms), 4) for p in B.PASSES}
     share.update({f"{p}_fp64": round(kern_ms[("fp64", p)] / sum(step_ms), 4)
                   for p in B.PASSES})
@@ -478,11 +483,13 @@ def run_gpu(args, rank, world, local_rank):
         "solver": args.solver,
         "other_solvers": solver_cmp or None,
         "setup_ms": setup["t_setup_ms"],
-        "roofline": {"bound": "hbm", "kernel": f"k_fft_{dom} (fp32)",
+        "roofline": {"bound": "hbm", "kernel": f"{kname} (fp32)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_rhs": per_rhs[dom],
-                     "traffic": None if traffic_rhs is None else traffic_rhs,
+                     "algorithmic_bytes_per_launch": alg / ncall,
+                     "launches": ncall,
+                     "traffic": traffic_launch,
                      "share_of_step": share},
         "cpu_baseline": cpu,
         "e2e": {"value": N * e2e_iters / (statistics.mean(e2e_ms) / 1e3), "unit": UNIT,

@@ -639,10 +639,12 @@ static void bicgstab(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, 
   CK(launch_state_init(R, nblk, part, ks, act, tol, max_iter, st));
   // the scalar steps alpha, omega, rho run in the last block of the pass that
   // produces their sums (block counters start at zero and are re-armed there)
-  w.fold.ensure(sizeof(unsigned) * R);
+  w.fold.ensure(fold_bytes(R));
   unsigned* cnt = w.fold.as<unsigned>();
-  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * R, st));
-  FoldArgs fa{ks, act, cnt, FOLD_ALPHA}, fo{ks, act, cnt, FOLD_OMEGA}, fr{ks, act, cnt, FOLD_RHO};
+  double* gsum = reinterpret_cast<double*>(w.fold.as<char>() + fold_gsum_offset(R));
+  CK(cudaMemsetAsync(cnt, 0, fold_gsum_offset(R), st));
+  FoldArgs fa{ks, act, cnt, FOLD_ALPHA, gsum}, fo{ks, act, cnt, FOLD_OMEGA, gsum},
+      fr{ks, act, cnt, FOLD_RHO, gsum};
   std::vector<int> hact(R);
   CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -775,10 +777,11 @@ static void qmr(dda_target* t, const OpView<T>& op, const MatvecLaunch& L, int R
   const int nblk_mv = matvec_partial_blocks<T>(op, L);
   // sigma/alpha and the rotation step run in the last block of the pass that
   // produces their sums
-  w.fold.ensure(sizeof(unsigned) * R);
+  w.fold.ensure(fold_bytes(R));
   unsigned* cnt = w.fold.as<unsigned>();
-  CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * R, st));
-  const FoldArgs fs{ks, act, cnt, FOLD_QSIGMA}, fq{ks, act, cnt, FOLD_QMR};
+  double* gsum = reinterpret_cast<double*>(w.fold.as<char>() + fold_gsum_offset(R));
+  CK(cudaMemsetAsync(cnt, 0, fold_gsum_offset(R), st));
+  const FoldArgs fs{ks, act, cnt, FOLD_QSIGMA, gsum}, fq{ks, act, cnt, FOLD_QMR, gsum};
   auto enqueue_block = [&](int nq) {
     for (int k = 0; k < nq; ++k) {
       // pending d/x update, q <- r + beta q; t = A q; q^T t; alpha
@@ -1299,6 +1302,7 @@ static int64_t workspace_bytes(const dda_target* t, int R, dda_precision prec, i
   const int fblk = std::min(reduce_blocks(t->nbox), 304);
   b += std::max((int64_t)8 * R * nblk, (int64_t)12 * (ndir + 1) * fblk) * 8;
   b += (int64_t)R * (sizeof(KState) + 64) + (int64_t)R * (t->nx + t->ny + t->nz + 8) * 16;
+  b += (int64_t)fold_bytes(R);  // scalar-step counters and group sums
   b += (int64_t)(ndir + 1) * (t->nx + t->ny + t->nz) * 16 + t->N * (int64_t)R * 48;
   return b;
 }

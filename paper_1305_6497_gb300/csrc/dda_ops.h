@@ -105,16 +105,32 @@ size_t zpair_smem_bytes(int Lz, int tile, bool gs);
 bool z_pair_tma_applies(int Lz, int Lx, int nz, int tile);
 
 // A vector pass that finishes one of the Krylov scalar steps in its last
-// block (instead of a separate one-block kernel): `counter` holds one word per
-// RHS, zero between passes, counting the blocks that have written partials.
+// block (instead of a separate one-block kernel).  The blocks of an RHS are
+// counted in two levels, so that no counter takes more than a few hundred
+// tickets per pass and no block sums more than ~1024 partials: groups of at
+// least 64 consecutive blocks (at most kFoldGroups groups), the last block of
+// a group sums the group's partials into `gsum`, and the last group to finish
+// sums the group sums and runs the step.  `counter` holds per RHS one word for
+// the groups and kFoldGroups words for the blocks ([R][1 + kFoldGroups], zero
+// between passes; the finishing blocks re-arm them); `gsum` [R][kFoldGroups][4].
 enum { FOLD_NONE = 0, FOLD_ALPHA = 1, FOLD_OMEGA = 2, FOLD_RHO = 3, FOLD_QSIGMA = 4,
        FOLD_QMR = 5 };
+constexpr int kFoldGroups = 1024;
 struct FoldArgs {
   KState* ks = nullptr;
   int* active = nullptr;
   unsigned* counter = nullptr;
   int step = FOLD_NONE;
+  double* gsum = nullptr;
 };
+// bytes of the counters and group sums of R right-hand sides (counters first,
+// the sums at fold_gsum_offset)
+inline size_t fold_gsum_offset(int R) {
+  return ((sizeof(unsigned) * (size_t)R * (1 + kFoldGroups)) + 255) & ~(size_t)255;
+}
+inline size_t fold_bytes(int R) {
+  return fold_gsum_offset(R) + sizeof(double) * 4 * (size_t)R * kFoldGroups;
+}
 
 // Matvecs fused with BiCGSTAB steps (same five passes as launch_matvec):
 //  launch_matvec_p: p <- r + beta (p - omega v); v = A p; partials of <rhat, v>

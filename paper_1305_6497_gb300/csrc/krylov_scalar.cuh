@@ -115,43 +115,69 @@ __device__ inline void step_qmr(const double* tot, KState& k, int* active_r) {
 }
 
 // Called by every thread of every block of a row after the block's NV partials
-// are written (by thread 0).  The block that completes the row last sums the
-// row's partials in a fixed order (block 0, 1, ...; FP64) and runs the scalar
-// step; it also re-arms the counter.  The result does not depend on which
-// block comes last.
+// are written (by thread 0).  Two levels of tickets (see FoldArgs): the last
+// block of each group sums the group's partials in block order, the last group
+// sums the group sums in group order (FP64) and runs the scalar step; each
+// finisher re-arms its counter.  The result does not depend on which blocks
+// finish last.
 template <int NV>
 __device__ void fold_scalar_step(const double* partials, const FoldArgs& f) {
   __shared__ int last;
+  const int r = blockIdx.y;
+  const int nb = gridDim.x;
+  const int G = max(64, (nb + kFoldGroups - 1) / kFoldGroups);
+  const int ng = (nb + G - 1) / G;
+  const int g = blockIdx.x / G;
+  const int gsz = min(G, nb - g * G);
+  unsigned* cnt = f.counter + (int64_t)r * (1 + kFoldGroups);
+  double* gs = f.gsum + (int64_t)r * kFoldGroups * 4;
   if (threadIdx.x == 0) {
     // thread 0 wrote the block's partials: make them visible before its ticket
-    // (the other threads wrote nothing the last block reads, and a fence in
+    // (the other threads wrote nothing the finisher reads, and a fence in
     // every thread would hold each block until all of its stores drained)
     __threadfence();
-    const unsigned ticket = atomicAdd(&f.counter[blockIdx.y], 1u);
-    last = ticket == gridDim.x - 1;
+    const unsigned ticket = atomicAdd(&cnt[1 + g], 1u);
+    last = ticket == (unsigned)gsz - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double acc[NV];
+  double acc[NV], tot[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-  const double* p = partials + (int64_t)blockIdx.y * gridDim.x * NV;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+  const double* p = partials + ((int64_t)r * nb + (int64_t)g * G) * NV;
+  for (int b = threadIdx.x; b < gsz; b += blockDim.x) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] += __ldcg(p + (int64_t)b * NV + i);
   }
-  double tot[NV];
   block_sum<NV>(acc, tot);
   if (threadIdx.x == 0) {
-    KState& k = f.ks[blockIdx.y];
-    int* act = f.active + blockIdx.y;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) gs[4 * g + i] = tot[i];
+    cnt[1 + g] = 0;
+    __threadfence();
+    const unsigned ticket = atomicAdd(&cnt[0], 1u);
+    last = ticket == (unsigned)ng - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int q = threadIdx.x; q < ng; q += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += __ldcg(gs + 4 * q + i);
+  }
+  block_sum<NV>(acc, tot);
+  if (threadIdx.x == 0) {
+    KState& k = f.ks[r];
+    int* act = f.active + r;
     if (f.step == FOLD_ALPHA) step_alpha(tot, k, act);
     else if (f.step == FOLD_OMEGA) step_omega(tot, k);
     else if (f.step == FOLD_RHO) step_rho(tot, k, act);
     else if (f.step == FOLD_QSIGMA) step_qmr_sigma(tot, k, act);
     else if (f.step == FOLD_QMR) step_qmr(tot, k, act);
-    f.counter[blockIdx.y] = 0;
+    cnt[0] = 0;
   }
 }
 

@@ -105,8 +105,8 @@ bool z_pair_applies(int Lz, int Lx, int tile) {
 }
 
 size_t zpair_smem_bytes(int Lz, int tile, bool gs) {
-  return (size_t)Lz * 3 * (tile / 2) * sizeof(float4) +
-         (gs ? (size_t)tile * zpair_gstride(Lz / 2 + 1) * sizeof(float2) : 0);
+  return (size_t)zpair_row(Lz, Lz, tile) * sizeof(float4) +
+         (gs ? (size_t)tile * zpair_gstride(Lz / 2 + 1, tile) * sizeof(float2) : 0);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (the

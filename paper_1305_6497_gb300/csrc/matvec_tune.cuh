@@ -38,7 +38,7 @@ template <typename T>
 static float time_pass(const OpView<T>& op, const MatvecLaunch& L, int pass, int R,
                        const cplx_t<T>* x, cplx_t<T>* y, cplx_t<T>* scratch, cudaStream_t st,
                        cudaEvent_t e0, cudaEvent_t e1, int reps, const KState* ks,
-                       double* part) {
+                       double* part, FoldArgs fold) {
   auto launch = [&]() {
     switch (pass) {
       case 0: {
@@ -49,8 +49,8 @@ static float time_pass(const OpView<T>& op, const MatvecLaunch& L, int pass, int
       case 1: launch_y_pass<T, false>(op, L, R, scratch, nullptr, st); break;
       case 2: launch_z_pass<T, false>(op, L, R, scratch, nullptr, st); break;
       case 3: launch_y_pass<T, true>(op, L, R, scratch, nullptr, st); break;
-      default:
-        launch_x_inv_pass<T, XOUT_RV>(op, L, R, scratch, x, y, nullptr, x, part, st);
+      default:  // with the scalar step its sums feed, as in the solves
+        launch_x_inv_pass<T, XOUT_RV>(op, L, R, scratch, x, y, nullptr, x, part, st, fold);
     }
   };
   launch();  // warm-up
@@ -74,17 +74,27 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
   if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
   // a zero Krylov state (alpha = 0) and partial sums for the fused x passes,
   // sized for the smallest line count tried (2 lines per CTA)
+  // (and the tuner's own counters, group sums and active flags for the scalar
+  // step the inverse x pass finishes; the step writes only these buffers)
   KState* ks = nullptr;
   double* part = nullptr;
+  char* fb = nullptr;
+  int* act = nullptr;
   const size_t nks = sizeof(KState) * (size_t)R;
   const size_t npart = sizeof(double) * 2 * (size_t)R * (3 * (size_t)op.nz * op.ny / 2 + 1);
   e = cudaMalloc(&ks, nks);
   if (e == cudaSuccess) e = cudaMalloc(&part, npart);
+  if (e == cudaSuccess) e = cudaMalloc(&fb, fold_bytes(R));
+  if (e == cudaSuccess) e = cudaMalloc(&act, sizeof(int) * (size_t)R);
   if (e == cudaSuccess) e = cudaMemsetAsync(ks, 0, nks, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fb, 0, fold_gsum_offset(R), st);
   if (e != cudaSuccess) {
-    cudaFree(ks); cudaFree(part); cudaEventDestroy(e0); cudaEventDestroy(e1);
+    cudaFree(ks); cudaFree(part); cudaFree(fb); cudaFree(act);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
     return e;
   }
+  const FoldArgs fold{ks, act, reinterpret_cast<unsigned*>(fb), FOLD_ALPHA,
+                      reinterpret_cast<double*>(fb + fold_gsum_offset(R))};
   const int reps = 6;
   const size_t kMax = 200 * 1024;
   MatvecLaunch best = L;
@@ -93,37 +103,37 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
   // without one wait at the stage's barrier.
   // x passes (forward and inverse together)
   {
-    float bt = time_pass<T>(op, best, 0, R, x, y, scratch, st, e0, e1, reps, ks, part) +
-               time_pass<T>(op, best, 4, R, x, y, scratch, st, e0, e1, reps, ks, part);
+    float bt = time_pass<T>(op, best, 0, R, x, y, scratch, st, e0, e1, reps, ks, part, fold) +
+               time_pass<T>(op, best, 4, R, x, y, scratch, st, e0, e1, reps, ks, part, fold);
     for (int nl : {2, 4, 8, 16, 32, 64})
       for (int th : {64, 96, 128, 192, 256}) {
         MatvecLaunch c = best;
         fill_x<T>(op, c, nl);
         c.x_threads = th;
         if (c.xinv_smem > kMax || nl > 3 * op.nz * op.ny) continue;
-        const float tt = time_pass<T>(op, c, 0, R, x, y, scratch, st, e0, e1, reps, ks, part) +
-                         time_pass<T>(op, c, 4, R, x, y, scratch, st, e0, e1, reps, ks, part);
+        const float tt = time_pass<T>(op, c, 0, R, x, y, scratch, st, e0, e1, reps, ks, part, fold) +
+                         time_pass<T>(op, c, 4, R, x, y, scratch, st, e0, e1, reps, ks, part, fold);
         if (tt < bt) { bt = tt; best = c; }
       }
   }
   // y passes
   {
-    float bt = time_pass<T>(op, best, 1, R, x, y, scratch, st, e0, e1, reps, ks, part) +
-               time_pass<T>(op, best, 3, R, x, y, scratch, st, e0, e1, reps, ks, part);
+    float bt = time_pass<T>(op, best, 1, R, x, y, scratch, st, e0, e1, reps, ks, part, fold) +
+               time_pass<T>(op, best, 3, R, x, y, scratch, st, e0, e1, reps, ks, part, fold);
     for (int tile : {2, 4, 8, 16, 32})
       for (int th : {64, 96, 128, 192, 256}) {
         MatvecLaunch c = best;
         fill_y<T>(op, c, tile);
         c.y_threads = th;
         if (c.y_smem > kMax) continue;
-        const float tt = time_pass<T>(op, c, 1, R, x, y, scratch, st, e0, e1, reps, ks, part) +
-                         time_pass<T>(op, c, 3, R, x, y, scratch, st, e0, e1, reps, ks, part);
+        const float tt = time_pass<T>(op, c, 1, R, x, y, scratch, st, e0, e1, reps, ks, part, fold) +
+                         time_pass<T>(op, c, 3, R, x, y, scratch, st, e0, e1, reps, ks, part, fold);
         if (tt < bt) { bt = tt; best = c; }
       }
   }
   // z pass
   {
-    float bt = time_pass<T>(op, best, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);
+    float bt = time_pass<T>(op, best, 2, R, x, y, scratch, st, e0, e1, reps, ks, part, fold);
     for (int tile : {2, 4, 8, 16})
       for (int gs = 0; gs < 2; ++gs)
         for (int pad = 0; pad < 4; ++pad)
@@ -145,7 +155,7 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
                                 (gs ? (size_t)6 * op.Hz * tile * 8 : 0);
               if (zc > kMax) continue;
             }
-            const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);
+            const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part, fold);
             if (tt < bt) { bt = tt; best = c; }
           }
     // the column-pair kernel (FP32, compiled z plans)
@@ -163,7 +173,7 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
           c.z_pair = tma ? 2 : 1;
           c.z_smem = zs;
           c.z_threads = th;
-          const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part);
+          const float tt = time_pass<T>(op, c, 2, R, x, y, scratch, st, e0, e1, reps, ks, part, fold);
           if (tt < bt) { bt = tt; best = c; }
         }
   }
@@ -171,6 +181,8 @@ cudaError_t autotune_matvec(const OpView<T>& op, MatvecLaunch& L, int R, const c
   cudaStreamSynchronize(st);
   cudaFree(ks);
   cudaFree(part);
+  cudaFree(fb);
+  cudaFree(act);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   L = best;

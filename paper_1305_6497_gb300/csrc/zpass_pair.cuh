@@ -34,8 +34,9 @@
 // so results agree with the other z kernels to rounding, not bit for bit.
 //
 // grid: (ceil(Lx / TILE), Ly / 2 + 1), NT threads.  Needs Lx even (pairs of
-// columns are 16-byte aligned) and, for TMA, nz <= 256.  Shared memory: Lz * 3 *
-// TILE/2 float4, plus (GS) the Ghat tile, TILE * zpair_gstride(Lz/2 + 1) float2.
+// columns are 16-byte aligned) and, for TMA, nz <= 256.  Shared memory: the
+// padded rows, zpair_row(Lz) float4, plus (GS) the Ghat tile,
+// TILE * zpair_gstride(Lz/2 + 1, TILE) float2.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap
@@ -113,20 +114,49 @@ __device__ __forceinline__ void split4(const float4 q, float2& a, float2& b) {
   b = make_float2(q.z, q.w);
 }
 
+// Rows of the transform in shared memory: position pos of the NU = 3 TILE/2
+// pair-lines starts at float4 index pos * NU + (pos / D) * K, i.e. K float4
+// are skipped after every D positions (none where D = 0).  D and K are chosen
+// per plan and tile so that every stage's 16-byte accesses, the multiply's and
+// the staged tile's fall in distinct bank slots per quarter-warp (a model of
+// the bank mapping over all of the kernel's access patterns; the plans of
+// lengths 64 and 288 keep unpadded rows, where no padding helped).
+__host__ __device__ constexpr int zpair_pad_div(int L, int tile) {
+  return L == 512 ? (tile == 4 ? 8 : 2) : L == 128 ? (tile == 4 ? 4 : 2) : 0;
+}
+__host__ __device__ constexpr int zpair_pad_k(int L, int tile) {
+  return L == 512 ? (tile == 4 ? 6 : 1) : L == 128 ? (tile == 4 ? 6 : 2) : 0;
+}
+__host__ __device__ constexpr int zpair_row(int pos, int L, int tile) {
+  return pos * (3 * tile / 2) +
+         (zpair_pad_div(L, tile) ? pos / zpair_pad_div(L, tile) * zpair_pad_k(L, tile) : 0);
+}
+
+// Offset (float4) of element i of a butterfly of span S from its first
+// element, in the padded rows of zpair_row: a multiple of the padding period D
+// apart (D | S), or inside one period (S = 1, D | block), so it is a constant.
+template <int L, int TILE, int S>
+__device__ __forceinline__ constexpr int zpair_step(int i) {
+  constexpr int D = zpair_pad_div(L, TILE), K = zpair_pad_k(L, TILE), NU = 3 * TILE / 2;
+  return i * S * NU + (D == 0 ? 0 : S % D == 0 ? i * (S / D) * K : (i / D) * K);
+}
+
 // One in-place stage ST of plan P on NU pair-lines of shared memory, both
 // columns of each pair (forward: DFT then twiddles; inverse: the adjoint).
-template <bool INV, class P, int ST, int NU, int NT>
+template <bool INV, class P, int ST, int TILE, int NT>
 __device__ __forceinline__ void stage_pair(float4* sd, const float2* __restrict__ tw) {
   constexpr int R = P::radix(ST), B = P::block(ST), S = P::span(ST), NB = P::L / R;
+  constexpr int NU = 3 * TILE / 2, D = zpair_pad_div(P::L, TILE);
   static_assert(NT % NU == 0, "a thread keeps one pair-line");
+  static_assert(D == 0 || S % D == 0 || (S == 1 && B % D == 0), "padding period");
   const float2* __restrict__ tws = tw + P::tw_off(ST);
   const int u = threadIdx.x % NU;
   for (int q = threadIdx.x / NU; q < NB; q += NT / NU) {
     const int blk = q / S, j = q - blk * S;
-    float4* base = sd + (blk * B + j) * NU + u;
+    float4* base = sd + zpair_row(blk * B + j, P::L, TILE) + u;
     float2 va[R], vb[R];
 #pragma unroll
-    for (int i = 0; i < R; ++i) split4(base[i * S * NU], va[i], vb[i]);
+    for (int i = 0; i < R; ++i) split4(base[zpair_step<P::L, TILE, S>(i)], va[i], vb[i]);
     if constexpr (!INV) {
       dft<R, false>(va);
       dft<R, false>(vb);
@@ -151,7 +181,8 @@ __device__ __forceinline__ void stage_pair(float4* sd, const float2* __restrict_
       dft<R, true>(vb);
     }
 #pragma unroll
-    for (int i = 0; i < R; ++i) base[i * S * NU] = make_float4(va[i].x, va[i].y, vb[i].x, vb[i].y);
+    for (int i = 0; i < R; ++i)
+      base[zpair_step<P::L, TILE, S>(i)] = make_float4(va[i].x, va[i].y, vb[i].x, vb[i].y);
   }
   __syncthreads();
 }
@@ -184,16 +215,17 @@ __device__ __forceinline__ void skew_item(int v, int& p, int& k) {
 
 // Ghat tile of a pair-kernel CTA in shared memory: column t's rows hz at
 // gs[t * stride + 6 hz] (float2), the column stride padded so that the columns
-// 2 apart (the same instruction's other column pair) land 64 bytes apart
-// modulo the 128-byte bank cycle.
-__host__ __device__ constexpr int zpair_gstride(int Hz) {
-  return ((Hz * 48 + 63) / 64 * 64 + 32) / 8;  // in float2
+// one instruction reads (2 apart: 2 columns for TILE 4, 4 for TILE 8) start in
+// different 16-byte slots of the 128-byte bank cycle (64 / 32 bytes apart).
+__host__ __device__ constexpr int zpair_gstride(int Hz, int tile) {
+  return (Hz * 6 + 7) / 8 * 8 + (tile == 4 ? 4 : 2);  // in float2
 }
+
 
 template <int TILE>
 __device__ __forceinline__ void ghat_tile_pairs_async(const OpView<float>& op, float2* gs,
                                                       int col0, int ncol, int hy) {
-  const int stride = zpair_gstride(op.Hz);
+  const int stride = zpair_gstride(op.Hz, TILE);
   const int n = op.Hz * TILE * 3;  // 16-byte chunks: 3 per point
   const int64_t plane = (int64_t)op.Hy * op.Hx;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
@@ -210,17 +242,33 @@ __device__ __forceinline__ void ghat_tile_pairs_async(const OpView<float>& op, f
 }
 
 // Stages LO..HI forward (ascending) or inverse (descending).
-template <bool INV, class P, int LO, int HI, int NU, int NT>
+template <bool INV, class P, int LO, int HI, int TILE, int NT>
 __device__ __forceinline__ void stages_pair(float4* sd, const float2* __restrict__ tw) {
   if constexpr (LO <= HI) {
     if constexpr (!INV) {
-      stage_pair<false, P, LO, NU, NT>(sd, tw);
-      stages_pair<false, P, LO + 1, HI, NU, NT>(sd, tw);
+      stage_pair<false, P, LO, TILE, NT>(sd, tw);
+      stages_pair<false, P, LO + 1, HI, TILE, NT>(sd, tw);
     } else {
-      stage_pair<true, P, HI, NU, NT>(sd, tw);
-      stages_pair<true, P, LO, HI - 1, NU, NT>(sd, tw);
+      stage_pair<true, P, HI, TILE, NT>(sd, tw);
+      stages_pair<true, P, LO, HI - 1, TILE, NT>(sd, tw);
     }
   }
+}
+
+// The first forward and the last inverse stage give each thread one
+// (position j, component c, column pair tp): tp fastest, then 8 / NP
+// consecutive positions, then the component, so that a quarter-warp's 16-byte
+// accesses to the staged tile ([c][z][column]) and to the transform rows fall
+// in distinct bank slots.
+template <int TILE>
+__device__ __forceinline__ void zpair_first_map(int tid, int& j, int& c, int& tp) {
+  constexpr int NP = TILE / 2, JL = 8 / NP;
+  tp = tid % NP;
+  int r = tid / NP;
+  const int jl = r % JL;
+  r /= JL;
+  c = r % 3;
+  j = (r / 3) * JL + jl;
 }
 
 template <int TILE, class P, bool GS, int NT, bool TMA>
@@ -231,30 +279,32 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
   constexpr int L = P::L, NS = P::NS, R0 = P::radix(0), S0 = P::span(0);
   constexpr int NP = TILE / 2, NU = 3 * NP;
   static_assert(NT % NU == 0 && NT % NP == 0, "a thread keeps one pair-line");
-  static_assert(((L / 2) * NU * 16) % 128 == 0, "TMA staging rows 128-byte aligned");
-  // (128-byte aligned: the TMA staging rows start at a multiple of 128 bytes)
+  constexpr int PD = zpair_pad_div(L, TILE);
+  static_assert((zpair_row(L / 2, L, TILE) * 16) % 128 == 0, "TMA staging 128-byte aligned");
+  static_assert(PD == 0 || S0 % PD == 0, "first-stage span a multiple of the padding period");
   extern __shared__ __align__(128) unsigned char zpair_smem_raw[];
   float4* sd = reinterpret_cast<float4*>(zpair_smem_raw);
-  float2* gs = reinterpret_cast<float2*>(sd + L * NU);
+  float2* gs = reinterpret_cast<float2*>(sd + zpair_row(L, L, TILE));
   const int Lx = op.Lx, Ly = op.Ly, nz = op.nz;
   const int hy = blockIdx.y;
   const int col0 = blockIdx.x * TILE;
   const int npv = min(TILE, Lx - col0) >> 1;  // pairs inside the grid (Lx even)
   if (GS) ghat_tile_pairs_async<TILE>(op, gs, col0, 2 * npv, hy);
-  const int gstride = zpair_gstride(op.Hz);
+  const int gstride = zpair_gstride(op.Hz, TILE);
   const int64_t plane_sz = (int64_t)Ly * Lx;
   const int64_t comp_sz = (int64_t)nz * plane_sz;
   const bool half = 2 * nz <= L;
   const float2* __restrict__ tw = op.twz_pair;
   const int kxh = Lx >> 1;
-  const int u = threadIdx.x % NU;           // this thread's pair-line ...
-  const int c = u / NP, tp = u - c * NP;    // ... = component c, column pair tp
-  const int tpm = threadIdx.x % NP;         // its column pair in the multiply
+  int jf, c, tp;  // first/last stage: position, component, column pair
+  zpair_first_map<TILE>(threadIdx.x, jf, c, tp);
+  const int u = c * NP + tp;                // the pair-line
+  const int tpm = threadIdx.x % NP;         // the column pair in the multiply
   // TMA: each pass's input tile lands in the upper half of sd (rows >= L/2, free
   // until the first stage writes them: the inputs are the nz <= L/2 lower rows)
   // as [c][z][t]; the output tile leaves from there the same way.
   __shared__ __align__(8) uint64_t bar;
-  float2* stg = reinterpret_cast<float2*>(sd + (L / 2) * NU);
+  float2* stg = reinterpret_cast<float2*>(sd + zpair_row(L / 2, L, TILE));
   unsigned phase = 0;
   if (TMA) {
     if (threadIdx.x == 0) {
@@ -296,7 +346,7 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
       float4 keep[TMA ? NJ * R0 : 1];
 #pragma unroll
       for (int jj = 0; jj < NJ; ++jj) {
-        const int j = threadIdx.x / NU + jj * (NT / NU);
+        const int j = jf + jj * (NT / NU);
         if (j >= S0) break;
         const bool ok = tp < npv;
         const float2* src = base + c * comp_sz + (int64_t)j * plane_sz + 2 * tp;
@@ -335,21 +385,22 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
         for (int m = 0; m < R0; ++m) {
           const float4 o = make_float4(va[m].x, va[m].y, vb[m].x, vb[m].y);
           if (TMA) keep[jj * R0 + m] = o;
-          else sd[(j + m * S0) * NU + u] = o;
+          else sd[zpair_row(j, L, TILE) + zpair_step<L, TILE, S0>(m) + u] = o;
         }
       }
       if (TMA) {
         __syncthreads();  // every staged input has been read
 #pragma unroll
         for (int jj = 0; jj < NJ; ++jj) {
-          const int j = threadIdx.x / NU + jj * (NT / NU);
+          const int j = jf + jj * (NT / NU);
           if (j >= S0) break;
 #pragma unroll
-          for (int m = 0; m < R0; ++m) sd[(j + m * S0) * NU + u] = keep[jj * R0 + m];
+          for (int m = 0; m < R0; ++m)
+            sd[zpair_row(j, L, TILE) + zpair_step<L, TILE, S0>(m) + u] = keep[jj * R0 + m];
         }
       }
       __syncthreads();
-      stages_pair<false, P, 1, NS - 1, NU, NT>(sd, tw);
+      stages_pair<false, P, 1, NS - 1, TILE, NT>(sd, tw);
       if (GS) {  // the Ghat tile has landed (a no-op after the first pass)
         cp_async_wait_all();
         __syncthreads();
@@ -362,7 +413,7 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
         skew_item<P>(v, p, kz);
         const bool fz = kz > L / 2;
         const int hz = fz ? L - kz : kz;
-        float4* row = sd + p * NU + tp2;
+        float4* row = sd + zpair_row(p, L, TILE) + tp2;
         float2 a[3], bb[3];
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) split4(row[cc * NP], a[cc], bb[cc]);
@@ -384,20 +435,21 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
           row[cc * NP] = make_float4(a[cc].x, a[cc].y, bb[cc].x, bb[cc].y);
       }
       __syncthreads();
-      stages_pair<true, P, 1, NS - 1, NU, NT>(sd, tw);
+      stages_pair<true, P, 1, NS - 1, TILE, NT>(sd, tw);
       // ---- last inverse stage (radix R0), written to global memory (z < nz);
       // with TMA the outputs go to the staging rows once every thread has
       // read its inputs, and one tensor store writes the tile
       float4 outk[TMA ? NJ * R0 : 1];
 #pragma unroll
       for (int jj = 0; jj < NJ; ++jj) {
-        const int j = threadIdx.x / NU + jj * (NT / NU);
+        const int j = jf + jj * (NT / NU);
         if (j >= S0) break;
         const bool ok = tp < npv;
         float2* dst = base + c * comp_sz + (int64_t)j * plane_sz + 2 * tp;
         float2 va[R0], vb[R0];
 #pragma unroll
-        for (int m = 0; m < R0; ++m) split4(sd[(j + m * S0) * NU + u], va[m], vb[m]);
+        for (int m = 0; m < R0; ++m)
+          split4(sd[zpair_row(j, L, TILE) + zpair_step<L, TILE, S0>(m) + u], va[m], vb[m]);
         if (j > 0) {
 #pragma unroll
           for (int m = 1; m < R0; ++m) {
@@ -429,7 +481,7 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
         __syncthreads();  // every input of the last stage has been read
 #pragma unroll
         for (int jj = 0; jj < NJ; ++jj) {
-          const int j = threadIdx.x / NU + jj * (NT / NU);
+          const int j = jf + jj * (NT / NU);
           if (j >= S0) break;
           // (with the pruned stage only i < R0/2 were formed; the others have
           // z >= R0/2 * S0 = L/2 >= nz)
@@ -463,8 +515,8 @@ bool encode_zpair_map(CUtensorMap* map, const float2* scratch, int Lx, int Ly, i
                       int tile);
 
 template <int TILE, class P, bool GS> constexpr size_t zpair_smem() {
-  return (size_t)P::L * 3 * (TILE / 2) * sizeof(float4) +
-         (GS ? (size_t)TILE * zpair_gstride(P::L / 2 + 1) * sizeof(float2) : 0);
+  return (size_t)zpair_row(P::L, P::L, TILE) * sizeof(float4) +
+         (GS ? (size_t)TILE * zpair_gstride(P::L / 2 + 1, TILE) * sizeof(float2) : 0);
 }
 
 }  // namespace dda
