@@ -2126,7 +2126,7 @@ void apply_schedule(const dda_target* t, MatvecLaunch& L, const std::vector<int>
   L.z_threads = v[7];
   L.x_lines = v[0];
   L.x_smem = (size_t)t->Lx * (v[0] + 1) * sizeof(C);
-  L.xinv_smem = L.x_smem + (size_t)2 * v[0] * t->nx * sizeof(C);
+  L.xinv_smem = x_inv_smem_bytes(t->Lx, v[0], t->nx, sizeof(C));
   L.y_tile = v[1];
   L.y_smem = (size_t)t->Ly * v[1] * sizeof(C);
   L.z_tile = v[2];

@@ -12,6 +12,14 @@ namespace dda {
 void note_launch();
 long long launch_count();
 
+// Shared memory of the inverse x pass with nl lines: the lines (Lx x (nl+1)
+// complex), the x and rhat chunks (nl nx complex each) and the sites'
+// composition bytes (nl nx, rounded up to 16).
+inline size_t x_inv_smem_bytes(int Lx, int nl, int nx, size_t csize) {
+  return (size_t)Lx * (nl + 1) * csize + (size_t)2 * nl * nx * csize +
+         (((size_t)nl * nx + 15) & ~(size_t)15);
+}
+
 struct MatvecLaunch {
   int x_lines, x_threads; size_t x_smem, xinv_smem;
   int y_tile, y_threads; size_t y_smem;

@@ -813,17 +813,28 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   static_assert(sizeof(IO) == sizeof(C), "box and FFT elements must have one size");
   IO* sx = reinterpret_cast<IO*>(s + (size_t)Lx * ps);
   IO* sh = sx + (size_t)nlines * nx;
+  // the composition bytes of the CTA's sites (lines of nx bytes)
+  unsigned char* scm = reinterpret_cast<unsigned char*>(sh + (size_t)nlines * nx);
   const int nin = min(nlines, rows - row0) * nx;
   const int64_t g0 = ((int64_t)r * rows + row0) * nx;
   for (int e = threadIdx.x; e < nin; e += blockDim.x) {
     cp_async<(int)sizeof(IO)>(&sx[e], &xin[g0 + e]);
     if (MODE == XOUT_RV) cp_async<(int)sizeof(IO)>(&sh[e], &rhat[g0 + e]);
   }
-  // all of the tile's loads in flight at once (asynchronous copies); the row's
+  // the epilogue's alpha^{-1} entries (3 per composition), when few
+  constexpr int kAiSmem = 24;
+  __shared__ C sai[kAiSmem];
+  const bool ai_smem = op.ncomp1 * 3 <= kAiSmem;
+  const C* ai = op.ainv + (int64_t)r * op.ncomp1 * 3;
+  if (MODE != XOUT_FIELD && ai_smem)
+    for (int i = threadIdx.x; i < op.ncomp1 * 3; i += blockDim.x) sai[i] = ai[i];
+  // all of the tile's loads in flight at once (asynchronous copies, the
+  // composition bytes in 4-byte pieces when lines are whole words); the row's
   // plane and y are worked out once per line.  Each line's site information
   // for the epilogue (composition row, polarization component) goes to a
   // small table (at most 64 lines per CTA).
   __shared__ int line_site[64], line_comp[64];
+  const bool cm_words = (nx & 3) == 0;
   for (int line = 0; line < nlines; ++line) {
     const int row = row0 + line;
     if (row < rows) {
@@ -831,10 +842,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
       const C* srow = src + plane * plane_sz + (int64_t)y * Lx;
       for (int p = threadIdx.x; p < Lx; p += blockDim.x)
         cp_async<(int)sizeof(C)>(&s[p * ps + line], &srow[p]);
+      // row = (c nz + z) ny + y  ->  sites (z ny + y) nx + p
+      const int c = fast_div(plane, op.div_nz);
+      const int site = ((plane - c * op.nz) * op.ny + y) * nx;
+      if (MODE != XOUT_FIELD) {
+        if (cm_words) {
+          for (int p = 4 * threadIdx.x; p < nx; p += 4 * blockDim.x)
+            cp_async<4>(&scm[line * nx + p], &op.comp[site + p]);
+        } else {
+          for (int p = threadIdx.x; p < nx; p += blockDim.x) scm[line * nx + p] = op.comp[site + p];
+        }
+      }
       if (threadIdx.x == 0) {
-        // row = (c nz + z) ny + y  ->  sites (z ny + y) nx + p
-        const int c = fast_div(plane, op.div_nz);
-        line_site[line] = ((plane - c * op.nz) * op.ny + y) * nx;
+        line_site[line] = site;
         line_comp[line] = c;
       }
     } else {
@@ -847,7 +867,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   // only positions < nx <= Lx/2 are used below
   if constexpr (std::is_void<P>::value) fft_smem<C, true>(s, nlines, ps, op.px, op.twx, 2 * nx <= Lx);
   else fft_smem_p<C, true, P>(s, nlines, div_nl, ps, op.twx, 2 * nx <= Lx);
-  const C* ai = op.ainv + (int64_t)r * op.ncomp1 * 3;
+  const C* aiv = ai_smem ? sai : ai;
   IO* yr = yout + g0;
   // (df64 passes only run the plain epilogue; their accumulator type is unused)
   ChunkAcc<std::conditional_t<std::is_same<T, df64>::value, double, T>, 4> acc;
@@ -857,28 +877,21 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fft_x_inv(OpVie
   // element's store)
   constexpr int U = 4;
   for (int e0 = threadIdx.x; e0 < nin; e0 += U * blockDim.x) {
-    int cms[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * blockDim.x;
-      cms[u] = 0;
-      if (e < nin && MODE != XOUT_FIELD) {
-        const int line = fast_div(e, op.div_nx), p = e - line * nx;
-        // the alpha^{-1} entry of composition cm on axis c is 3 cm + c (0: vacant)
-        const int cm = op.comp[line_site[line] + p];
-        cms[u] = cm ? 3 * cm + line_comp[line] : 0;
-      }
-    }
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int e = e0 + u * blockDim.x;
     if (e >= nin) break;
     const int line = fast_div(e, op.div_nx), p = e - line * nx;
-    const int cm = cms[u];
+    // the alpha^{-1} entry of composition cm on axis c is 3 cm + c (0: vacant)
+    int cm = 0;
+    if (MODE != XOUT_FIELD) {
+      cm = scm[e];
+      cm = cm ? 3 * cm + line_comp[line] : 0;
+    }
     C out = mk<C>(0, 0);
     const C xv = from_io<C>(sx[e]);
     if (MODE == XOUT_FIELD) out = s[p * ps + line];
-    else if (cm) out = csub(cmul(ai[cm], xv), s[p * ps + line]);
+    else if (cm) out = csub(cmul(aiv[cm], xv), s[p * ps + line]);
     yr[e] = to_io<IO>(out);
     {
       if constexpr (MODE == XOUT_RV) {
@@ -960,7 +973,7 @@ MatvecLaunch plan_matvec(const OpView<T>& op) {
   L.x_lines = nl;
   L.x_threads = 256;
   L.x_smem = (size_t)op.Lx * (nl + 1) * sizeof(C);
-  L.xinv_smem = L.x_smem + (size_t)2 * nl * op.nx * sizeof(C);  // + x and rhat chunks
+  L.xinv_smem = x_inv_smem_bytes(op.Lx, nl, op.nx, sizeof(C));  // + x, rhat, composition
   // y pass: a tile of 128 B of columns (16 FP32 / 8 FP64 complex), 256 threads
   int ty = 128 / (int)sizeof(C);
   while (ty > 2 && (size_t)ty * op.Ly * sizeof(C) > 64 * 1024) ty >>= 1;

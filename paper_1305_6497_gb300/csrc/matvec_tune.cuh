@@ -14,7 +14,7 @@ static void fill_x(const OpView<T>& op, MatvecLaunch& L, int nl) {
   using C = cplx_t<T>;
   L.x_lines = nl;
   L.x_smem = (size_t)op.Lx * (nl + 1) * sizeof(C);
-  L.xinv_smem = L.x_smem + (size_t)2 * nl * op.nx * sizeof(C);
+  L.xinv_smem = x_inv_smem_bytes(op.Lx, nl, op.nx, sizeof(C));
 }
 template <typename T>
 static void fill_y(const OpView<T>& op, MatvecLaunch& L, int tile) {

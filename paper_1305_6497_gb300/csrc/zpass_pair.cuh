@@ -295,11 +295,21 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
   const int64_t comp_sz = (int64_t)nz * plane_sz;
   const bool half = 2 * nz <= L;
   const float2* __restrict__ tw = op.twz_pair;
-  const int kxh = Lx >> 1;
   int jf, c, tp;  // first/last stage: position, component, column pair
   zpair_first_map<TILE>(threadIdx.x, jf, c, tp);
   const int u = c * NP + tp;                // the pair-line
   const int tpm = threadIdx.x % NP;         // the column pair in the multiply
+  // the multiply's two columns: frequency kx (octant column hx, flipped or not)
+  int hxm[2] = {0, 0};
+  bool fxm[2] = {false, false};
+  if (tpm < npv) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int kx = op.kx_at[col0 + 2 * tpm + e];
+      fxm[e] = kx > (Lx >> 1);
+      hxm[e] = fxm[e] ? Lx - kx : kx;
+    }
+  }
   // TMA: each pass's input tile lands in the upper half of sd (rows >= L/2, free
   // until the first stage writes them: the inputs are the nz <= L/2 lower rows)
   // as [c][z][t]; the output tile leaves from there the same way.
@@ -419,16 +429,13 @@ k_fft_z_pairs(OpView<float> op, float2* __restrict__ buf, int R, const int* __re
         for (int cc = 0; cc < 3; ++cc) split4(row[cc * NP], a[cc], bb[cc]);
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          const int kx = op.kx_at[col0 + 2 * tp2 + e];
-          const bool fx = kx > kxh;
           float2 g[6];
           if (GS) {
             G6<float>::load_smem(gs + (2 * tp2 + e) * gstride + 6 * hz, g);
           } else {
-            const int hx = fx ? Lx - kx : kx;
-            G6<float>::load(op.ghat + 6 * (((int64_t)hz * op.Hy + hy) * op.Hx + hx), g);
+            G6<float>::load(op.ghat + 6 * (((int64_t)hz * op.Hy + hy) * op.Hx + hxm[e]), g);
           }
-          spectral_mul<float, false>(g, fx, fy, fz, e ? bb : a, 1);
+          spectral_mul<float, false>(g, fxm[e], fy, fz, e ? bb : a, 1);
         }
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc)
