@@ -206,9 +206,11 @@ typedef struct {
   double tol;            /* stop when ||E - A P|| / ||E|| <= tol (FP64)          */
   int max_iter;          /* cap on Krylov iterations per RHS (all sweeps)       */
   dda_precision precision;
-  double inner_tol;      /* FP32_REFINED inner tolerance; <= 0: adaptive, each
-                            sweep reduces the residual by what the target still
-                            needs, max(tol/(2 * current rel. residual), 1e-5)   */
+  double inner_tol;      /* FP32_REFINED inner tolerance.  > 0: that tolerance
+                            in every sweep; 0: adaptive, each sweep reduces the
+                            residual by what the target still needs,
+                            max(tol/(2 * current rel. residual), 1e-5); < 0: the
+                            same with the floor -inner_tol in place of 1e-5   */
   int n_dirs;            /* scattering directions besides forward (>= 0)        */
   const double* dirs;    /* [n_dirs][2] (theta_s, phi_s) radians in the Lab Frame
                             (x_LF = khat, y_LF = yhat): n = x cos(theta) +

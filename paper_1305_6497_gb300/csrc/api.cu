@@ -1840,8 +1840,9 @@ dda_status dda_solve(dda_target* t, const dda_solve_params* p, dda_solve_result*
       // FP64 iterative refinement around FP32 BiCGSTAB
       // inner tolerance: the caller's, or adaptive -- reduce the residual only as far
       // as the outer target needs (half of tol / current relative residual), but no
-      // further than FP32 arithmetic can carry the inner solve (1e-5)
-      const double kInnerFloor = 1e-5;
+      // further than FP32 arithmetic can carry the inner solve (by default 1e-5; a
+      // negative inner_tol sets another floor)
+      const double kInnerFloor = p->inner_tol < 0 ? -p->inner_tol : 1e-5;
       Vecs<float> V{w.b32.as<float2>(), w.x32.as<float2>(), w.r32.as<float2>(),
                     w.rh32.as<float2>(), w.p32.as<float2>(), w.v32.as<float2>(),
                     w.s32.as<float2>(), w.t32.as<float2>(), w.scr32.as<float2>()};
