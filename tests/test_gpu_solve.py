@@ -536,3 +536,41 @@ def test_device_loop_equals_host_checked_blocks(B, solver, precision):
         assert np.array_equal(c["P"], d["P"]) and np.array_equal(c["iters"], d["iters"])
         assert np.all(c["iters"] <= 10 + (1 if solver == "bicgstab2" else 0))
     t.close()
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_fp32_bicgstab_iterates_within_the_fp32_error_bound(B, k):
+    """The FP32 Krylov solve -- FP32 vectors and FFT passes, inner products
+    summed in FP32 within each thread (chunks of 8) and block (shuffle tree)
+    and in FP64 across blocks -- follows the oracle's FP64 BiCGSTAB: after k
+    iterations (from the same zero start and shadow vector) the GPU iterate
+    differs from the oracle's by a relative amount set by FP32 rounding.  The
+    inner products alone stay within (m/8 + 15) 2^-24 of sum |terms| for m
+    terms per thread (a few 1e-7 here), a product through five FFT passes of
+    length <= 64 within ~1e-6; through the k-th iterate these compound to a few
+    1e-6 per iteration, so the bound asserted is 2e-5 k.  A reduction that lost
+    a block or a chunk would move alpha and omega by ~1/(number of blocks), at
+    the percent level on this size (~40 k vector elements, dozens of blocks per
+    pass).  The FP64 solve meets the FP64 bar on the same iterates."""
+    w = W.small_ellipsoid(20, 24, 28, m=1.5 + 0.1j, kd=0.3, method="LDR")
+    flat, pos = O.site_positions(w.occ)
+    e1, _ = O.polarization_pair(w.khat[0], w.e01[0])
+    ainv = O.site_alpha_inverse(w.comp.reshape(-1)[flat], w.m, w.method, w.kd, w.khat[0], e1)
+    E = O.incident_field(pos, w.kd, w.khat[0], e1).reshape(-1)
+    ainv_box = np.zeros(w.occ.size, np.complex128)
+    ainv_box[flat] = ainv
+    op = O.FFTOperator(w.occ, ainv_box.reshape(w.occ.shape), w.kd, w.method)
+
+    def mv(v):
+        return O.box_to_sites(op(O.sites_to_box(v.reshape(-1, 3), flat, w.occ.shape)),
+                              flat).reshape(-1)
+    xo, it, _ = O.bicgstab(mv, E, tol=0.0, maxiter=k)
+    assert it == k
+    t = B.Target(w.occ, w.comp, w.m, method="LDR")
+    for precision, bound in (("fp64", 1e-9), ("fp32", 2e-5 * k)):
+        g = t.solve(w.kd, w.khat, w.e01, yhat=w.yhat, npol=1, tol=1e-14, max_iter=k,
+                    precision=precision)
+        assert g["iters"][0] == k
+        rel = np.linalg.norm(g["P"][0].reshape(-1) - xo) / np.linalg.norm(xo)
+        assert rel < bound, (precision, k, rel)
+    t.close()
