@@ -113,17 +113,19 @@ size_t zpair_smem_bytes(int Lz, int tile, bool gs);
 bool z_pair_tma_applies(int Lz, int Lx, int nz, int tile);
 
 // A vector pass that finishes one of the Krylov scalar steps in its last
-// block (instead of a separate one-block kernel).  The blocks of an RHS are
-// counted in two levels, so that no counter takes more than a few hundred
-// tickets per pass and no block sums more than ~1024 partials: groups of at
-// least 64 consecutive blocks (at most kFoldGroups groups), the last block of
-// a group sums the group's partials into `gsum`, and the last group to finish
-// sums the group sums and runs the step.  `counter` holds per RHS one word for
+// block (instead of a separate one-block kernel).  Up to kFoldSingle blocks
+// per RHS, the last block to finish sums all partials and runs the step.
+// Beyond that the blocks are counted in two levels, so that no counter takes
+// more than a few hundred tickets per pass and no block sums more than ~1024
+// partials: groups of at least 64 consecutive blocks (at most kFoldGroups
+// groups), the last block of a group sums the group's partials into `gsum`,
+// and the last group to finish sums the group sums and runs the step.  `counter` holds per RHS one word for
 // the groups and kFoldGroups words for the blocks ([R][1 + kFoldGroups], zero
 // between passes; the finishing blocks re-arm them); `gsum` [R][kFoldGroups][4].
 enum { FOLD_NONE = 0, FOLD_ALPHA = 1, FOLD_OMEGA = 2, FOLD_RHO = 3, FOLD_QSIGMA = 4,
        FOLD_QMR = 5 };
 constexpr int kFoldGroups = 1024;
+constexpr int kFoldSingle = 2048;  // up to this many blocks: one level
 struct FoldArgs {
   KState* ks = nullptr;
   int* active = nullptr;

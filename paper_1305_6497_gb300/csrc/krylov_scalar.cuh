@@ -125,7 +125,9 @@ __device__ void fold_scalar_step(const double* partials, const FoldArgs& f) {
   __shared__ int last;
   const int r = blockIdx.y;
   const int nb = gridDim.x;
-  const int G = max(64, (nb + kFoldGroups - 1) / kFoldGroups);
+  // one group (the plain last-block scheme) while the last block's sum over all
+  // partials stays short; groups of >= 64 blocks beyond that
+  const int G = nb <= kFoldSingle ? nb : max(64, (nb + kFoldGroups - 1) / kFoldGroups);
   const int ng = (nb + G - 1) / G;
   const int g = blockIdx.x / G;
   const int gsz = min(G, nb - g * G);
@@ -151,25 +153,28 @@ __device__ void fold_scalar_step(const double* partials, const FoldArgs& f) {
     for (int i = 0; i < NV; ++i) acc[i] += __ldcg(p + (int64_t)b * NV + i);
   }
   block_sum<NV>(acc, tot);
-  if (threadIdx.x == 0) {
+  if (ng > 1) {
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) gs[4 * g + i] = tot[i];
-    cnt[1 + g] = 0;
+      for (int i = 0; i < NV; ++i) gs[4 * g + i] = tot[i];
+      cnt[1 + g] = 0;
+      __threadfence();
+      const unsigned ticket = atomicAdd(&cnt[0], 1u);
+      last = ticket == (unsigned)ng - 1;
+    }
+    __syncthreads();
+    if (!last) return;
     __threadfence();
-    const unsigned ticket = atomicAdd(&cnt[0], 1u);
-    last = ticket == (unsigned)ng - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-  for (int q = threadIdx.x; q < ng; q += blockDim.x) {
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int q = threadIdx.x; q < ng; q += blockDim.x) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] += __ldcg(gs + 4 * q + i);
+      for (int i = 0; i < NV; ++i) acc[i] += __ldcg(gs + 4 * q + i);
+    }
+    block_sum<NV>(acc, tot);
   }
-  block_sum<NV>(acc, tot);
   if (threadIdx.x == 0) {
+    if (ng == 1) cnt[1] = 0;
     KState& k = f.ks[r];
     int* act = f.active + r;
     if (f.step == FOLD_ALPHA) step_alpha(tot, k, act);
@@ -177,7 +182,7 @@ __device__ void fold_scalar_step(const double* partials, const FoldArgs& f) {
     else if (f.step == FOLD_RHO) step_rho(tot, k, act);
     else if (f.step == FOLD_QSIGMA) step_qmr_sigma(tot, k, act);
     else if (f.step == FOLD_QMR) step_qmr(tot, k, act);
-    cnt[0] = 0;
+    if (ng > 1) cnt[0] = 0;
   }
 }
 
