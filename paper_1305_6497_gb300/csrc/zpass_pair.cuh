@@ -7,18 +7,19 @@
 // instructions per point and for reuse of Ghat:
 //   * a thread always works on two neighbouring columns at once: shared memory
 //     holds a pair as one float4 (16-byte loads and stores, every twiddle
-//     loaded once for both columns, half the index arithmetic), and rows are
-//     stored without padding so that consecutive threads touch consecutive
-//     16-byte words;
+//     loaded once for both columns, half the index arithmetic);
 //   * a CTA owns TILE columns at one octant row hy and runs both rows that
 //     share it (ky = hy and ky = Ly - hy) for every right-hand side, so every
 //     pass of the CTA reads the same Ghat rows: from L2 after the first (GS =
 //     false), or staged once in shared memory with cp.async while the first
 //     forward transform runs (GS = true);
 //   * the last forward stage, the multiply and the first inverse stage are
-//     separate sweeps over shared memory; the multiply visits positions in a
-//     skewed order and the Ghat tile's columns are padded so that its 16-byte
-//     accesses avoid bank conflicts;
+//     separate sweeps over shared memory.  The layout keeps every 16-byte
+//     access free of bank conflicts (for the 512-point plan; nearly so for
+//     the others): transform rows padded per plan and tile (zpair_row), the
+//     first and last stages' thread map (zpair_first_map), the multiply's
+//     skewed position order (skew_item) and the Ghat tile's column stride
+//     (zpair_gstride);
 //   * optionally (TMA) each pass's column tile is loaded and stored by the
 //     tensor-memory accelerator: one cp.async.bulk.tensor box per pass, landing
 //     in (and leaving from) the upper half of the transform's shared memory,
